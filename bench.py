@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""Benchmark: paths/s of the iterated stochastic Magnus solver at a fixed L2 error.
+
+Workload: the time-dependent Langevin SPDE on a 128 x 128 grid over [-6, 6]^2,
+a(t) = 1 + 0.5 sin 2 pi t, sigma(t) = 0.5 (1 + 0.3 cos 2 pi t), Gaussian
+u0 = N((0.5, 0), diag(0.5, 1)), 4096 Philox paths per GPU, 2^14 fine Brownian
+increments on [0, 1], Magnus order 3 with float stencil/Taylor arithmetic and
+double-precision functionals, weights, norm bound and (s, m).
+
+Fixed-error protocol: before timing, the number of Magnus steps K is the
+cheapest of 8/16/32/64 whose mean relative L2 error (Err, whole grid) against
+the double-precision order-3 solution with 1024 steps stays <= 1e-3 on a
+subset of paths (that reference path is itself checked against the CPU
+oracle by the test suite).
+
+One timed step = one full solve of the batch (Brownian functionals, Magnus
+weights and Taylor parameters, iterated Taylor action), inputs resident on the
+device.  Prints one JSON line.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import LANGEVIN_TRIG_128  # noqa: E402
+
+ORDER = 3
+K_CANDIDATES = (8, 16, 32, 64)
+ERR_TARGET = 1e-3
+REF_K = 1024
+REF_PATHS = 128
+COMPARATOR_PATHS = 512
+FLOPS_PER_POINT = 32      # 15 stencil multiply-adds + Taylor scale and accumulate
+METRIC = "paths/s to T at fixed L2 err (Magnus FP32/FP64/surrogate vs EM); HBM GB/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    p.add_argument("--paths", type=int, default=LANGEVIN_TRIG_128.paths)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-comparators", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=0, help="paths in the CPU-oracle sample (0 = auto)")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def _oracle_paths(args):
+    w, order, K, paths = args
+    from oracle import magnus
+    from oracle.discretization import LangevinOperators
+    ops = LangevinOperators(w)
+    for p in paths:
+        magnus.solve_path(w, order, K, p, ops)
+    return len(paths)
+
+
+def time_oracle(w, order, K, npaths, cores):
+    """Wall-clock paths/s of the oracle on `npaths` paths spread over `cores` processes."""
+    chunks = [list(range(c, npaths, cores)) for c in range(cores)]
+    chunks = [c for c in chunks if c]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(chunks)) as pool:
+        pool.map(_oracle_paths, [(w, order, K, [0])] * len(chunks))      # imports, warm caches
+        t0 = time.perf_counter()
+        done = sum(pool.map(_oracle_paths, [(w, order, K, c) for c in chunks]))
+        dt = time.perf_counter() - t0
+    return done / dt, dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            t = [x.strip() for x in line.split(",")]
+            if len(t) < 9:
+                continue
+            try:
+                rows.append((float(t[1]), float(t[2]), t[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def engine_profile():
+    """ncu DRAM traffic of the engine kernel from the committed profile summary,
+    valid only if the engine source is unchanged since it was taken."""
+    src = os.path.join(ROOT, "paper_2207_09776_b300", "csrc", "engine.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    prof = os.path.join(ROOT, "profiles", "magnus_engine_d128_f32.txt")
+    if not os.path.exists(prof):
+        return None, h
+    vals = {}
+    for line in open(prof):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("engine_source_sha256_16") != h:
+        return None, h
+    try:
+        return float(vals["dram_bytes_per_launch_full_workload"]), h
+    except (KeyError, ValueError):
+        return None, h
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+# ------------------------------------------------------------------ our implementation
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    import paper_2207_09776_b300 as msk
+    from paper_2207_09776_b300 import build as mbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mbuild.build()
+    msk.load_library()
+
+    P = a.paths
+    w = LANGEVIN_TRIG_128.with_(paths=P, path_offset=rank * P)
+    solver = msk.Solver(w, device=local)
+    ctx = solver.ctx
+    stream = torch.cuda.current_stream()
+
+    # ---- fixed-error protocol (untimed) -------------------------------------------
+    wref = w.with_(paths=REF_PATHS)
+    msk.msk_set_seed(ctx, w.seed, w.path_offset, w.n_fine, w.T)
+    ref = solver.magnus(ORDER, REF_K, paths=REF_PATHS, precision=msk.MSK_F64)
+    sweep = {}
+    chosen = None
+    for K in K_CANDIDATES:
+        u = solver.magnus(ORDER, K, paths=REF_PATHS, precision=msk.MSK_F32)
+        _, em = solver.error(u, msk.MSK_F32, ref=ref, ref_precision=msk.MSK_F64)
+        sweep[K] = float(em.cpu()[0])
+        if chosen is None and sweep[K] <= ERR_TARGET:
+            chosen = K
+    if chosen is None:
+        chosen = K_CANDIDATES[-1]
+    K = chosen
+    del wref
+
+    # ---- buffers of one step ------------------------------------------------------------
+    F = torch.empty(P * K * msk.MSK_NF, dtype=torch.float64, device=dev)
+    Wt = torch.empty(P * K * msk.MSK_NWT, dtype=torch.float64, device=dev)
+    out = torch.empty(P * w.d * w.d, dtype=torch.float32, device=dev)
+    st = torch.zeros(P, dtype=torch.int32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+
+    def step(i=None):
+        msk.msk_brownian_functionals(ctx, K, P, F, stream)
+        msk.msk_omega_weights(ctx, ORDER, K, P, msk.MSK_F32, F, Wt, stream)
+        if i is not None:
+            ev[i][0].record(stream)
+        msk.msk_magnus_from_weights(ctx, K, P, msk.MSK_F32, Wt, out, st, stream)
+        if i is not None:
+            ev[i][1].record(stream)
+
+    for _ in range(max(a.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    msk.msk_work_counter(ctx, reset=True, stream=stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(a.steps):
+        step(i)
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    engine_ms = sum(s.elapsed_time(e) for s, e in ev) / a.steps
+    matvecs = msk.msk_work_counter(ctx, reset=True, stream=stream)
+    status_bits = int(st.cpu().numpy().max())
+
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    ms_per_step = elapsed_ms / a.steps
+    value = world * P * a.steps / (elapsed_ms / 1e3)
+
+    # ---- end to end through the public call with host buffers -------------------------
+    u0_host = torch.empty(w.d * w.d, dtype=torch.float64).pin_memory()
+    u0_dev = torch.empty(w.d * w.d, dtype=torch.float64, device=dev)
+    import numpy as _np
+    xs = w.ax + (w.bx - w.ax) / (w.d + 1) * _np.arange(1, w.d + 1)
+    X, V = _np.meshgrid(xs, xs, indexing="xy")
+    mx, mv = w.u0_mean
+    cxx, cxv, cvv = w.u0_cov
+    det = cxx * cvv - cxv * cxv
+    q = (cvv * (X - mx) ** 2 - 2 * cxv * (X - mx) * (V - mv) + cxx * (V - mv) ** 2) / det
+    u0_host.copy_(torch.from_numpy((_np.exp(-0.5 * q) / (2 * math.pi * math.sqrt(det))).ravel()))
+    out_host = torch.empty(P * w.d * w.d, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        u0_dev.copy_(u0_host, non_blocking=True)
+        msk.msk_set_initial(ctx, u0_dev, stream)
+        msk.msk_solve_magnus(ctx, ORDER, K, P, msk.MSK_F32, out, st, stream)
+        out_host.copy_(out, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    n_e2e = max(3, a.steps // 2)
+    for _ in range(n_e2e):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / n_e2e
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # ---- comparators (untimed by the main loop; events) --------------------------------
+    comparators = {}
+    if not a.no_comparators:
+        Pc = min(COMPARATOR_PATHS, P)
+        refc = ref[: min(Pc, REF_PATHS)]
+        def timed(fn):
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            fn()
+            torch.cuda.synchronize()
+            s0.record(stream)
+            r = fn()
+            s1.record(stream)
+            torch.cuda.synchronize()
+            return r, s0.elapsed_time(s1)
+        n = refc.shape[0]
+        for Kc in K_CANDIDATES:
+            u64, ms64 = timed(lambda: solver.magnus(ORDER, Kc, paths=Pc, precision=msk.MSK_F64))
+            _, e64 = solver.error(u64[:n].contiguous(), msk.MSK_F64, ref=refc, ref_precision=msk.MSK_F64)
+            comparators.setdefault("magnus_fp64", {})[f"K{Kc}"] = {
+                "paths_per_s": Pc / (ms64 / 1e3), "err": float(e64.cpu()[0])}
+        for ne in (2048, 16384):
+            uem, msem = timed(lambda: solver.euler(ne, paths=Pc, precision=msk.MSK_F32))
+            _, eem = solver.error(uem[:n].contiguous(), msk.MSK_F32, ref=refc, ref_precision=msk.MSK_F64)
+            comparators.setdefault("euler_fp32", {})[f"N{ne}"] = {
+                "paths_per_s": Pc / (msem / 1e3), "err": float(eem.cpu()[0])}
+        comparators["magnus_fp32_sweep_err"] = {f"K{k}": v for k, v in sweep.items()}
+
+    # ---- roofline of the engine kernel ------------------------------------------------------
+    peaks, peak_src = measured_peaks()
+    sm_mhz_peak = float(peaks.get("sm_max_mhz", 2032.0))
+    fp32_peak = 148 * 128 * 2 * sm_mhz_peak * 1e6 / 1e12            # TFLOP/s, CUDA-core FMA
+    flops_launch = matvecs / a.steps * w.d * w.d * FLOPS_PER_POINT
+    achieved = flops_launch / (engine_ms / 1e3) / 1e12
+    traffic, src_hash = engine_profile()
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": traffic,
+            "kernel": "engine_kernel<float,128,1,512>", "engine_ms": engine_ms,
+            "matvecs_per_launch": matvecs / a.steps,
+            "peak_note": f"FP32 FMA peak 148 SMs x 128 lanes x 2 x {sm_mhz_peak:.0f} MHz ({peak_src} clock)"}
+
+    # ---- CPU oracle baseline -------------------------------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cores = host_cores()
+        npaths = a.cpu_sample or max(cores, 4 * cores)
+        v, secs = time_oracle(w.with_(paths=npaths), ORDER, K, npaths, cores)
+        cpu = {"value": v, "unit": "paths/s", "cores": cores, "kind": "oracle",
+               "sample": f"{npaths} paths of the same workload (FP64 oracle, order {ORDER}, K={K}), {secs:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "d": w.d, "paths_per_gpu": P, "order": ORDER, "magnus_steps": K,
+                   "n_fine": w.n_fine, "err_target": ERR_TARGET, "err_measured": sweep[K],
+                   "reference": f"FP64 order-3 Magnus with {REF_K} steps on {REF_PATHS} paths",
+                   "precision": "float stencil/Taylor, double functionals/weights/norm/(s,m)",
+                   "l2": "output 268 MB/step > 126 MB L2; Brownian paths regenerated in-kernel each step",
+                   "parallelism": f"replicas x{world} (path ranges)"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * P / (e2e_ms / 1e3), "unit": "paths/s",
+                "h2d_bytes_per_step": u0_host.numel() * 8, "d2h_bytes_per_step": out_host.numel() * 4},
+        "clocks": clk,
+        "gpu_launches": 3 * a.steps,
+        "path_status_max": status_bits,
+        "comparators": comparators,
+    }
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm (CPU oracle)
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    K = K_CANDIDATES[0]
+    cores = host_cores()
+    npaths = a.cpu_sample or 2 * cores
+    w = LANGEVIN_TRIG_128.with_(paths=npaths)
+    for _ in range(max(a.warmup, 0)):
+        time_oracle(w, ORDER, K, min(npaths, cores), cores)
+    times = []
+    for _ in range(a.steps):
+        v, secs = time_oracle(w, ORDER, K, npaths, cores)
+        times.append(secs)
+    total = sum(times)
+    value = npaths * a.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "d": w.d, "order": ORDER, "magnus_steps": K, "n_fine": w.n_fine,
+                       "sample_paths_per_step": npaths},
+            "cpu_baseline": {"value": value, "unit": "paths/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{npaths} paths per step of the same workload"},
+            "e2e": {"value": value, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * msk.h — C ABI of the B300 stochastic Magnus solver for the kinetic Langevin SPDE
+ *
+ *   du = ( a(t)/2 d_vv u + kappa v d_x u ) dt + sigma(t) d_v u dW          (Eq. spde)
+ *
+ * discretised in space by central finite differences with zero Dirichlet
+ * boundary (Section 2, "Computation of A and B") into the linear matrix SDE
+ * dU = B U dt + A U dW (Eq. SPDEvec), and integrated over many Brownian paths
+ * at once by the iterated Ito-stochastic Magnus scheme of orders 1..3
+ * (Eq. MagnusFormulas; Section 2, "Iterated Magnus expansion"), with the
+ * Euler-Maruyama scheme (Eq. EulerMaruyama) as comparator.
+ *
+ * Conventions for every entry point
+ *  - Every call returns msk_status and never throws, exits or prints.
+ *  - The library owns the context, its operator tables and its scratch
+ *    buffers.  The caller owns every buffer passed in ("_dev" = device
+ *    memory of the context's device, "_host" = host memory) and the CUDA
+ *    stream; work is enqueued on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream) and the call returns without synchronising unless
+ *    stated.  The library never frees caller memory.
+ *  - Solution arrays are [path][v][x] with x fastest (the paper's vec
+ *    ordering, vec index i + n_x j), element type double for MSK_F64 and
+ *    float for MSK_F32.
+ *  - A failed call returns non-MSK_OK and leaves a message for
+ *    msk_last_error(ctx); per-path numerical trouble (non-finite values,
+ *    Taylor scaling cap, blow-up) is reported in the optional per-path
+ *    status words and does not fail the call.
+ *  - Sizes: 32 <= n_x = n_v <= 512, n_x a multiple of 32 and one of
+ *    32, 64, 128, 256, 512; paths >= 0 (0 is a no-op); steps >= 1 dividing
+ *    n_fine.  Violations return MSK_ERR_ARG before any device work.
+ */
+#ifndef MSK_H
+#define MSK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct msk_ctx msk_ctx;
+
+typedef enum {
+  MSK_OK = 0,
+  MSK_ERR_ARG = 1,          /* invalid argument (checked before any device work) */
+  MSK_ERR_CUDA = 2,         /* a CUDA runtime call failed (message in msk_last_error) */
+  MSK_ERR_OOM = 3,          /* device allocation failed */
+  MSK_ERR_TIMEOUT = 4,      /* reserved: a bounded device wait ran out */
+  MSK_ERR_NONFINITE = 5,    /* non-finite scalar argument */
+  MSK_ERR_UNSUPPORTED = 6   /* valid request this build does not implement */
+} msk_status;
+
+enum { MSK_COEF_CONST = 0, MSK_COEF_TRIG = 1 };
+enum { MSK_F64 = 0, MSK_F32 = 1 };
+enum { MSK_REF_EXPLICIT = 0, MSK_REF_BUFFER = 1 };
+
+/* per-path status bits */
+#define MSK_PATH_NONFINITE 1u   /* a non-finite value reached the solution */
+#define MSK_PATH_SCALE_CAP 2u   /* Taylor scaling count hit its cap (result inaccurate) */
+#define MSK_PATH_BLOWUP 4u      /* max|u_T| > 10 max|u_0| (Magnus explosion, Section 3.1) */
+
+/* Brownian functionals per (path, step), see msk_brownian_functionals */
+#define MSK_NF 8
+enum { MSK_F_DW = 0, MSK_F_I1, MSK_F_I2, MSK_F_I3, MSK_F_OM, MSK_F_JOM, MSK_F_G1, MSK_F_G2 };
+
+/* Basis operators of the Magnus logarithm (Kronecker factors: v-matrix (x) x-matrix),
+ * with Bx = kappa diag(v) (x) D^x, Bvv = D^vv (x) I, A0 = D^v (x) I. */
+#define MSK_NOPS 13
+enum {
+  MSK_OP_BX = 0, MSK_OP_BVV, MSK_OP_A0, MSK_OP_A0A0, MSK_OP_BX_A0, MSK_OP_BVV_A0,
+  MSK_OP_BX_BVV, MSK_OP_BXA0_A0, MSK_OP_BVVA0_A0, MSK_OP_BXA0_BX, MSK_OP_BXA0_BVV,
+  MSK_OP_BVVA0_BX, MSK_OP_BVVA0_BVV
+};
+
+/* Per (path, step) record written by msk_omega_weights (doubles):
+ * [0, MSK_NOPS) operator weights, then shift mu, norm bound, scaling s, degree m. */
+#define MSK_NWT 20
+enum { MSK_WT_MU = 16, MSK_WT_NORM = 17, MSK_WT_S = 18, MSK_WT_M = 19 };
+
+/* Interior grid n_x x n_v on [ax,bx] x [av,bv]; Delta = (b - a)/(n + 1)
+ * (Eq. xGrid, vGrid).  This build requires nx == nv. */
+typedef struct {
+  int32_t nx, nv;
+  double ax, bx, av, bv;
+} msk_grid;
+
+/* Langevin coefficients: f^x = drift_sign * v, g^vv = a(t), sigma^v = sigma(t)
+ * (Eq. coeffsLangevinConst has drift_sign = -1 and constant a, sigma).
+ * MSK_COEF_CONST: a = a0, sigma = s0.
+ * MSK_COEF_TRIG:  a(t) = a0 + a1 sin(2 pi t), sigma(t) = s0 (1 + s1 cos(2 pi t)). */
+typedef struct {
+  int32_t drift_sign;
+  int32_t kind;
+  double a0, a1, s0, s1;
+} msk_coeffs;
+
+/* Gaussian initial datum u0(z) = scale * N(z; mean, cov) (Eq. initialdatum is
+ * mean 0, cov I, scale 2 pi). */
+typedef struct {
+  double mean_x, mean_v, cov_xx, cov_xv, cov_vv, scale;
+} msk_gaussian;
+
+/* Create a context on CUDA device `device`: builds the grid, the finite
+ * difference operators and the thirteen basis-operator band tables on the
+ * device (Section 2, "Computation of A and B"; commutators of
+ * Eq. MagnusFormulas).  Defaults: drift +1, a = 1, sigma = 0.5, standard
+ * Gaussian density, seed 0, n_fine 10000, T 1.  *out is NULL on failure. */
+msk_status msk_create(msk_ctx** out, const msk_grid* grid, int device);
+
+/* Release the context and every library-owned device buffer.  NULL is a no-op.
+ * Must not be called while work using the context is in flight. */
+void msk_destroy(msk_ctx* ctx);
+
+/* Last error message of the context ("" if none); a static string for ctx NULL. */
+const char* msk_last_error(const msk_ctx* ctx);
+
+/* Set the coefficient profile (see msk_coeffs).  Non-finite values -> MSK_ERR_NONFINITE. */
+msk_status msk_set_coefficients(msk_ctx* ctx, const msk_coeffs* coeffs);
+
+/* Set a Gaussian initial datum; evaluated on the interior grid on the device. */
+msk_status msk_set_initial_gaussian(msk_ctx* ctx, const msk_gaussian* g);
+
+/* Copy a caller-owned initial datum u0_dev ([v][x], double, device) into the context. */
+msk_status msk_set_initial(msk_ctx* ctx, const double* u0_dev, void* stream);
+
+/* Brownian stream: Philox4x32-10 key = seed, path p of a call uses global index
+ * path_offset + p; n_fine increments of variance T/n_fine on [0, T] (the
+ * fine "Lebesgue" grid of Section 3, "Error and notations"). */
+msk_status msk_set_seed(msk_ctx* ctx, uint64_t seed, uint64_t path_offset, int64_t n_fine,
+                        double T);
+
+/* Raw Philox4x32-10 words of the Brownian stream: out_dev[4 q + r] = word r of
+ * counter (first_pair + q, path lo, path hi, tag), key (seed lo, seed hi),
+ * q = 0..npairs-1.  Integer work; used to check bit-exactness. */
+msk_status msk_philox_words(uint64_t seed, uint64_t path, uint32_t tag, int64_t first_pair,
+                            int64_t npairs, uint32_t* out_dev, void* stream);
+
+/* S3: per-step Brownian functionals on the fine grid (Section 3,
+ * "Implementation": Lebesgue integrals by Riemann sums), read as exact
+ * integrals of the piecewise-linear interpolant of W:
+ *   F_dev[(p * steps + n) * MSK_NF + f], f = DW, I1 = int W~, I2 = int W~^2,
+ *   I3 = int s W~, OM = int sigma dW, JOM = int omega~, G1, G2 (time-dependent
+ *   weights, see msk_omega_weights), with W~ the Brownian motion restarted at
+ *   the step start.  F_dev: caller-owned double[paths * steps * MSK_NF]. */
+msk_status msk_brownian_functionals(msk_ctx* ctx, int steps, int64_t paths, double* F_dev,
+                                    void* stream);
+
+/* Brownian increments over `steps` equal steps: dW_dev[p * steps + n] (double). */
+msk_status msk_brownian_increments(msk_ctx* ctx, int steps, int64_t paths, double* dW_dev,
+                                   void* stream);
+
+/* S4 + S5a: Magnus weights of the order-`order` logarithm (Eq. MagnusFormulas;
+ * for MSK_COEF_TRIG the time-dependent order-2 extension of the Appendix's
+ * Picard step), the trace shift mu = trace(Omega)/n, an infinity-norm bound of
+ * Omega - mu I and the Taylor scaling/degree pair (s, m) chosen by the
+ * backward-error bound of Al-Mohy & Higham (2011) at unit roundoff of
+ * `precision`.  F_dev from msk_brownian_functionals; Wt_dev: caller-owned
+ * double[paths * steps * MSK_NWT]. */
+msk_status msk_omega_weights(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
+                             const double* F_dev, double* Wt_dev, void* stream);
+
+/* One application out = Omega u of Omega = sum_k w_k Op_k, weights_dev
+ * [paths][MSK_NOPS] (double), u_dev/out_dev [paths][v][x] double.  Exposes the
+ * widened-stencil operator tables for parity checks. */
+msk_status msk_apply_omega(msk_ctx* ctx, const double* weights_dev, int64_t paths,
+                           const double* u_dev, double* out_dev, void* stream);
+
+/* S5b + S6: iterated Magnus solve (Section 2, "Iterated Magnus expansion"):
+ * `steps` equal sub-intervals of [0, T], on each U <- exp(Omega_n) U by the
+ * scaled truncated Taylor action with early termination.  precision MSK_F64:
+ * all arithmetic in double; MSK_F32: stencil/Taylor arithmetic in float with
+ * the Brownian functionals, weights, norm bound and (s, m) in double.
+ * u_out_dev: [paths][v][x] of double (MSK_F64) or float (MSK_F32).
+ * path_status_dev: optional uint32[paths] of MSK_PATH_* bits (may be NULL).
+ * Scratch (functionals and weights) is library-owned and grows on demand. */
+msk_status msk_solve_magnus(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
+                            void* u_out_dev, uint32_t* path_status_dev, void* stream);
+
+/* S5b + S6 only: the iterated Magnus solve from precomputed per-(path, step)
+ * records Wt_dev (layout of msk_omega_weights, double[paths * steps * MSK_NWT],
+ * caller-owned).  msk_solve_magnus = msk_brownian_functionals +
+ * msk_omega_weights + this call, with library-owned scratch. */
+msk_status msk_magnus_from_weights(msk_ctx* ctx, int steps, int64_t paths, int precision,
+                                   const double* Wt_dev, void* u_out_dev,
+                                   uint32_t* path_status_dev, void* stream);
+
+/* Work counter: number of whole-grid stencil applications (Taylor terms and
+ * Euler steps, summed over paths) performed by the engine since the last
+ * reset, read after synchronising `stream`.  reset != 0 zeroes it afterwards. */
+msk_status msk_work_counter(msk_ctx* ctx, uint64_t* matvecs_host, int reset, void* stream);
+
+/* S7: Euler-Maruyama (Eq. EulerMaruyama) with `steps` equal steps, a(t),
+ * sigma(t) at the left end of each step, dW the sum of the fine increments. */
+msk_status msk_solve_euler(msk_ctx* ctx, int steps, int64_t paths, int precision,
+                           void* u_out_dev, uint32_t* path_status_dev, void* stream);
+
+/* S9: closed-form solution for the Gaussian initial datum, per path,
+ * u_T = c0 N(M_T m0 + c_T, M_T S0 M_T^T + C_T) (Section 3.1's fundamental
+ * solution integrated against the Gaussian datum), u_out_dev [paths][v][x] double. */
+msk_status msk_explicit_solution(msk_ctx* ctx, int64_t paths, double* u_out_dev, void* stream);
+
+/* S8: per-path relative Frobenius error over the central 2^-kappa part
+ * (Eq. meanErr: Err; index range [lo, lo + floor(d/2^kappa)),
+ * lo = floor(d/2 - d/2^(kappa+1))).  ref_kind MSK_REF_EXPLICIT evaluates the
+ * closed form on the fly (ref_dev ignored); MSK_REF_BUFFER reads ref_dev
+ * ([paths][v][x], element type ref_precision).  err_per_path_dev: double[paths];
+ * err_mean_dev: optional double[1] = mean over paths (Err). */
+msk_status msk_error(msk_ctx* ctx, const void* u_dev, int u_precision, int64_t paths,
+                     int ref_kind, const void* ref_dev, int ref_precision, int kappa,
+                     double* err_per_path_dev, double* err_mean_dev, void* stream);
+
+/* Per-path moments of a solution: mom_dev[6 p + r] = mass, mean x, mean v,
+ * cov xx, cov xv, cov vv (double). */
+msk_status msk_moments(msk_ctx* ctx, const void* u_dev, int precision, int64_t paths,
+                       double* mom_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSK_H */

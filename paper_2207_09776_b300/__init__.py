@@ -1,0 +1,333 @@
+"""Python binding of libmsk, the B300 stochastic Magnus solver (C ABI in include/msk.h).
+
+Argument marshalling only: every numerical step runs in the CUDA kernels of
+libmsk.so.  Device buffers are torch tensors on the context's CUDA device;
+work is enqueued on the current torch stream unless a stream is given.
+Loading fails loudly if the library has not been built (there is no CPU
+fallback).
+
+The functions carry the C names (msk_create, msk_solve_magnus, ...); the
+`Solver` class bundles a context with tensor allocation for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmsk.so")
+
+MSK_OK, MSK_ERR_ARG, MSK_ERR_CUDA, MSK_ERR_OOM, MSK_ERR_TIMEOUT, MSK_ERR_NONFINITE, MSK_ERR_UNSUPPORTED = range(7)
+MSK_COEF_CONST, MSK_COEF_TRIG = 0, 1
+MSK_F64, MSK_F32 = 0, 1
+MSK_REF_EXPLICIT, MSK_REF_BUFFER = 0, 1
+MSK_PATH_NONFINITE, MSK_PATH_SCALE_CAP, MSK_PATH_BLOWUP = 1, 2, 4
+MSK_NF, MSK_NOPS, MSK_NWT = 8, 13, 20
+MSK_F_DW, MSK_F_I1, MSK_F_I2, MSK_F_I3, MSK_F_OM, MSK_F_JOM, MSK_F_G1, MSK_F_G2 = range(8)
+MSK_WT_MU, MSK_WT_NORM, MSK_WT_S, MSK_WT_M = 16, 17, 18, 19
+OP_NAMES = ("Bx", "Bvv", "A0", "A0A0", "[Bx,A0]", "[Bvv,A0]", "[Bx,Bvv]", "[[Bx,A0],A0]",
+            "[[Bvv,A0],A0]", "[[Bx,A0],Bx]", "[[Bx,A0],Bvv]", "[[Bvv,A0],Bx]", "[[Bvv,A0],Bvv]")
+STATUS_NAMES = {0: "MSK_OK", 1: "MSK_ERR_ARG", 2: "MSK_ERR_CUDA", 3: "MSK_ERR_OOM",
+                4: "MSK_ERR_TIMEOUT", 5: "MSK_ERR_NONFINITE", 6: "MSK_ERR_UNSUPPORTED"}
+
+
+class msk_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("nv", ctypes.c_int32), ("ax", ctypes.c_double),
+                ("bx", ctypes.c_double), ("av", ctypes.c_double), ("bv", ctypes.c_double)]
+
+
+class msk_coeffs(ctypes.Structure):
+    _fields_ = [("drift_sign", ctypes.c_int32), ("kind", ctypes.c_int32), ("a0", ctypes.c_double),
+                ("a1", ctypes.c_double), ("s0", ctypes.c_double), ("s1", ctypes.c_double)]
+
+
+class msk_gaussian(ctypes.Structure):
+    _fields_ = [("mean_x", ctypes.c_double), ("mean_v", ctypes.c_double), ("cov_xx", ctypes.c_double),
+                ("cov_xv", ctypes.c_double), ("cov_vv", ctypes.c_double), ("scale", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_U64 = ctypes.c_uint64
+_INT = ctypes.c_int
+_DBL = ctypes.c_double
+
+# name -> (restype, argtypes); mirrors include/msk.h
+SIGNATURES = {
+    "msk_create": (_INT, [ctypes.POINTER(_P), ctypes.POINTER(msk_grid), _INT]),
+    "msk_destroy": (None, [_P]),
+    "msk_last_error": (ctypes.c_char_p, [_P]),
+    "msk_set_coefficients": (_INT, [_P, ctypes.POINTER(msk_coeffs)]),
+    "msk_set_initial_gaussian": (_INT, [_P, ctypes.POINTER(msk_gaussian)]),
+    "msk_set_initial": (_INT, [_P, _P, _P]),
+    "msk_set_seed": (_INT, [_P, _U64, _U64, _I64, _DBL]),
+    "msk_philox_words": (_INT, [_U64, _U64, ctypes.c_uint32, _I64, _I64, _P, _P]),
+    "msk_brownian_functionals": (_INT, [_P, _INT, _I64, _P, _P]),
+    "msk_brownian_increments": (_INT, [_P, _INT, _I64, _P, _P]),
+    "msk_omega_weights": (_INT, [_P, _INT, _INT, _I64, _INT, _P, _P, _P]),
+    "msk_apply_omega": (_INT, [_P, _P, _I64, _P, _P, _P]),
+    "msk_solve_magnus": (_INT, [_P, _INT, _INT, _I64, _INT, _P, _P, _P]),
+    "msk_solve_euler": (_INT, [_P, _INT, _I64, _INT, _P, _P, _P]),
+    "msk_magnus_from_weights": (_INT, [_P, _INT, _I64, _INT, _P, _P, _P, _P]),
+    "msk_work_counter": (_INT, [_P, ctypes.POINTER(ctypes.c_uint64), _INT, _P]),
+    "msk_explicit_solution": (_INT, [_P, _I64, _P, _P]),
+    "msk_error": (_INT, [_P, _P, _INT, _I64, _INT, _P, _INT, _INT, _P, _P, _P]),
+    "msk_moments": (_INT, [_P, _P, _INT, _I64, _P, _P]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmsk.so and declare its C signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libmsk.so not built at {path}; run paper_2207_09776_b300/build.py")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class MskError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st: int, ctx=None):
+    if st != MSK_OK:
+        msg = load_library().msk_last_error(ctx).decode() if ctx else ""
+        raise MskError(st, msg)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device buffers must be contiguous CUDA tensors")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dtype(precision):
+    import torch
+    return torch.float64 if precision == MSK_F64 else torch.float32
+
+
+def _need(t, n, dtype, name):
+    if t.dtype != dtype or t.numel() < n:
+        raise ValueError(f"{name}: need {n} elements of {dtype}, got {t.numel()} of {t.dtype}")
+
+
+# ---- thin wrappers with the C names --------------------------------------------------
+
+def msk_create(nx: int, nv: int, ax: float, bx: float, av: float, bv: float, device: int = 0):
+    h = _P()
+    g = msk_grid(nx, nv, ax, bx, av, bv)
+    _check(load_library().msk_create(ctypes.byref(h), ctypes.byref(g), device))
+    return h
+
+
+def msk_destroy(ctx):
+    load_library().msk_destroy(ctx)
+
+
+def msk_last_error(ctx) -> str:
+    return load_library().msk_last_error(ctx).decode()
+
+
+def msk_set_coefficients(ctx, drift_sign, kind, a0, a1, s0, s1):
+    _check(load_library().msk_set_coefficients(ctx, ctypes.byref(msk_coeffs(drift_sign, kind, a0, a1, s0, s1))), ctx)
+
+
+def msk_set_initial_gaussian(ctx, mean, cov, scale=1.0):
+    g = msk_gaussian(mean[0], mean[1], cov[0], cov[1], cov[2], scale)
+    _check(load_library().msk_set_initial_gaussian(ctx, ctypes.byref(g)), ctx)
+
+
+def msk_set_initial(ctx, u0, stream=None):
+    import torch
+    _need(u0, 1, torch.float64, "u0")
+    _check(load_library().msk_set_initial(ctx, _ptr(u0), _stream(stream)), ctx)
+
+
+def msk_set_seed(ctx, seed, path_offset, n_fine, T):
+    _check(load_library().msk_set_seed(ctx, seed, path_offset, n_fine, T), ctx)
+
+
+def msk_philox_words(seed, path, tag, first_pair, npairs, out, stream=None):
+    import torch
+    _need(out, 4 * npairs, torch.int32, "out")
+    _check(load_library().msk_philox_words(seed, path, tag, first_pair, npairs, _ptr(out), _stream(stream)))
+
+
+def msk_brownian_functionals(ctx, steps, paths, F, stream=None):
+    import torch
+    _need(F, paths * steps * MSK_NF, torch.float64, "F")
+    _check(load_library().msk_brownian_functionals(ctx, steps, paths, _ptr(F), _stream(stream)), ctx)
+
+
+def msk_brownian_increments(ctx, steps, paths, dW, stream=None):
+    import torch
+    _need(dW, paths * steps, torch.float64, "dW")
+    _check(load_library().msk_brownian_increments(ctx, steps, paths, _ptr(dW), _stream(stream)), ctx)
+
+
+def msk_omega_weights(ctx, order, steps, paths, precision, F, Wt, stream=None):
+    import torch
+    _need(F, paths * steps * MSK_NF, torch.float64, "F")
+    _need(Wt, paths * steps * MSK_NWT, torch.float64, "Wt")
+    _check(load_library().msk_omega_weights(ctx, order, steps, paths, precision, _ptr(F), _ptr(Wt),
+                                            _stream(stream)), ctx)
+
+
+def msk_apply_omega(ctx, weights, paths, u, out, stream=None):
+    _check(load_library().msk_apply_omega(ctx, _ptr(weights), paths, _ptr(u), _ptr(out), _stream(stream)), ctx)
+
+
+def msk_solve_magnus(ctx, order, steps, paths, precision, u_out, status=None, stream=None):
+    _need(u_out, 1, _dtype(precision), "u_out")
+    _check(load_library().msk_solve_magnus(ctx, order, steps, paths, precision, _ptr(u_out), _ptr(status),
+                                           _stream(stream)), ctx)
+
+
+def msk_magnus_from_weights(ctx, steps, paths, precision, Wt, u_out, status=None, stream=None):
+    import torch
+    _need(Wt, paths * steps * MSK_NWT, torch.float64, "Wt")
+    _need(u_out, 1, _dtype(precision), "u_out")
+    _check(load_library().msk_magnus_from_weights(ctx, steps, paths, precision, _ptr(Wt), _ptr(u_out),
+                                                  _ptr(status), _stream(stream)), ctx)
+
+
+def msk_work_counter(ctx, reset=False, stream=None) -> int:
+    v = ctypes.c_uint64(0)
+    _check(load_library().msk_work_counter(ctx, ctypes.byref(v), int(bool(reset)), _stream(stream)), ctx)
+    return int(v.value)
+
+
+def msk_solve_euler(ctx, steps, paths, precision, u_out, status=None, stream=None):
+    _need(u_out, 1, _dtype(precision), "u_out")
+    _check(load_library().msk_solve_euler(ctx, steps, paths, precision, _ptr(u_out), _ptr(status),
+                                          _stream(stream)), ctx)
+
+
+def msk_explicit_solution(ctx, paths, u_out, stream=None):
+    import torch
+    _need(u_out, 1, torch.float64, "u_out")
+    _check(load_library().msk_explicit_solution(ctx, paths, _ptr(u_out), _stream(stream)), ctx)
+
+
+def msk_error(ctx, u, u_precision, paths, ref_kind, ref, ref_precision, kappa, err_per_path, err_mean=None,
+              stream=None):
+    _check(load_library().msk_error(ctx, _ptr(u), u_precision, paths, ref_kind, _ptr(ref), ref_precision, kappa,
+                                    _ptr(err_per_path), _ptr(err_mean), _stream(stream)), ctx)
+
+
+def msk_moments(ctx, u, precision, paths, mom, stream=None):
+    _check(load_library().msk_moments(ctx, _ptr(u), precision, paths, _ptr(mom), _stream(stream)), ctx)
+
+
+# ---- convenience ---------------------------------------------------------------------
+
+class Solver:
+    """A context configured from a workload description (see workloads.Workload)."""
+
+    def __init__(self, w, device: int = 0):
+        import torch
+        self.w = w
+        self.device = torch.device("cuda", device)
+        self.ctx = msk_create(w.d, w.d, w.ax, w.bx, w.av, w.bv, device)
+        msk_set_coefficients(self.ctx, w.drift_sign, w.kind, w.a0, w.a1, w.s0, w.s1)
+        msk_set_initial_gaussian(self.ctx, w.u0_mean, w.u0_cov, w.u0_scale)
+        msk_set_seed(self.ctx, w.seed, w.path_offset, w.n_fine, w.T)
+
+    def close(self):
+        if self.ctx:
+            msk_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _empty(self, n, dtype):
+        import torch
+        return torch.empty(n, dtype=dtype, device=self.device)
+
+    def state(self, paths, precision=MSK_F64):
+        return self._empty(paths * self.w.d * self.w.d, _dtype(precision)).view(paths, self.w.d, self.w.d)
+
+    def magnus(self, order, steps, paths=None, precision=MSK_F64, status=False, out=None):
+        import torch
+        paths = self.w.paths if paths is None else paths
+        u = self.state(paths, precision) if out is None else out
+        st = torch.zeros(max(paths, 1), dtype=torch.int32, device=self.device) if status else None
+        msk_solve_magnus(self.ctx, order, steps, paths, precision, u, st)
+        return (u, st) if status else u
+
+    def euler(self, steps, paths=None, precision=MSK_F64, status=False):
+        import torch
+        paths = self.w.paths if paths is None else paths
+        u = self.state(paths, precision)
+        st = torch.zeros(max(paths, 1), dtype=torch.int32, device=self.device) if status else None
+        msk_solve_euler(self.ctx, steps, paths, precision, u, st)
+        return (u, st) if status else u
+
+    def explicit(self, paths=None):
+        paths = self.w.paths if paths is None else paths
+        u = self.state(paths, MSK_F64)
+        msk_explicit_solution(self.ctx, paths, u)
+        return u
+
+    def functionals(self, steps, paths=None):
+        import torch
+        paths = self.w.paths if paths is None else paths
+        F = self._empty(paths * steps * MSK_NF, torch.float64)
+        msk_brownian_functionals(self.ctx, steps, paths, F)
+        return F.view(paths, steps, MSK_NF)
+
+    def increments(self, steps, paths=None):
+        import torch
+        paths = self.w.paths if paths is None else paths
+        dW = self._empty(paths * steps, torch.float64)
+        msk_brownian_increments(self.ctx, steps, paths, dW)
+        return dW.view(paths, steps)
+
+    def weights(self, order, steps, paths=None, precision=MSK_F64):
+        import torch
+        paths = self.w.paths if paths is None else paths
+        F = self.functionals(steps, paths)
+        Wt = self._empty(paths * steps * MSK_NWT, torch.float64)
+        msk_omega_weights(self.ctx, order, steps, paths, precision, F, Wt)
+        return Wt.view(paths, steps, MSK_NWT)
+
+    def error(self, u, precision, ref=None, ref_precision=MSK_F64, kappa=0):
+        import torch
+        paths = u.shape[0]
+        e = self._empty(max(paths, 1), torch.float64)
+        m = self._empty(1, torch.float64)
+        kind = MSK_REF_EXPLICIT if ref is None else MSK_REF_BUFFER
+        msk_error(self.ctx, u, precision, paths, kind, ref, ref_precision, kappa, e, m)
+        return e[:paths], m
+
+    def moments(self, u, precision):
+        import torch
+        paths = u.shape[0]
+        mom = self._empty(max(paths, 1) * 6, torch.float64)
+        msk_moments(self.ctx, u, precision, paths, mom)
+        return mom[: paths * 6].view(paths, 6)

@@ -1,0 +1,87 @@
+// Internal declarations shared by the CUDA translation units of libmsk.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/msk.h"
+
+// x-factor class of a basis operator V (x) X: X = I, D^x or (D^x)^2.
+enum { XC_I = 0, XC_DX = 1, XC_DXX = 2 };
+
+// Band half-width of the v-factor tables: offsets -2..2 are stored.
+#define MSK_BAND 5
+
+struct msk_ctx {
+  int device = 0;
+  int d = 0;                 // n_x = n_v
+  double ax = 0, bx = 0, av = 0, bv = 0, dx = 0, dv = 0;
+  msk_coeffs coef{};
+  msk_gaussian u0g{};
+  uint64_t seed = 0, path_offset = 0;
+  int64_t n_fine = 10000;
+  double T = 1.0;
+  double* u0 = nullptr;       // [d][d] (v-major, x fastest), device
+  double* band = nullptr;     // [MSK_NOPS][d][MSK_BAND], device
+  double* aux = nullptr;      // [MSK_NOPS] operator traces, then C_T (3), then u0 max (1)
+  unsigned long long* work = nullptr;   // engine work counter (stencil applications)
+  double host_trace[MSK_NOPS] = {0};
+  double host_u0max = 0;
+  double cT[3] = {0, 0, 0};   // deterministic covariance of the closed form
+  void* scratch = nullptr;    // library-owned scratch (functionals + weights)
+  size_t scratch_bytes = 0;
+  int num_sms = 0;
+  std::string err;
+};
+
+// x-class of each basis operator (same order as the MSK_OP_* enum).
+static const int kOpXClass[MSK_NOPS] = {
+    XC_DX,  // Bx        = kappa diag(v) (x) D^x
+    XC_I,   // Bvv       = D^vv (x) I
+    XC_I,   // A0        = D^v (x) I
+    XC_I,   // A0^2
+    XC_DX,  // [Bx,A0]
+    XC_I,   // [Bvv,A0]
+    XC_DX,  // [Bx,Bvv]
+    XC_DX,  // [[Bx,A0],A0]
+    XC_I,   // [[Bvv,A0],A0]
+    XC_DXX, // [[Bx,A0],Bx]
+    XC_DX,  // [[Bx,A0],Bvv]
+    XC_DX,  // [[Bvv,A0],Bx]
+    XC_I,   // [[Bvv,A0],Bvv]
+};
+
+// Status helpers (host).
+msk_status msk_fail(msk_ctx* ctx, msk_status st, const std::string& msg);
+msk_status msk_cuda(msk_ctx* ctx, cudaError_t e, const char* what);
+msk_status msk_ensure_scratch(msk_ctx* ctx, size_t bytes);
+bool msk_supported_d(int d);
+
+// Launchers implemented in the .cu files (all asynchronous on `stream`).
+msk_status launch_band_tables(msk_ctx* ctx, cudaStream_t stream);
+msk_status launch_gaussian_u0(msk_ctx* ctx, cudaStream_t stream);
+msk_status launch_brownian(msk_ctx* ctx, int steps, int64_t paths, double* out, bool increments_only,
+                           cudaStream_t stream);
+msk_status launch_omega(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
+                        const double* F, double* Wt, cudaStream_t stream);
+msk_status launch_engine(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
+                         const double* Wt, const double* dW, void* out, uint32_t* status,
+                         cudaStream_t stream);
+
+// Device-side coefficient profiles.
+struct CoefDev {
+  int kind;
+  double a0, a1, s0, s1;
+};
+
+__host__ __device__ inline CoefDev coef_dev(const msk_coeffs& c) {
+  CoefDev r;
+  r.kind = c.kind;
+  r.a0 = c.a0;
+  r.s0 = c.s0;
+  r.a1 = c.kind == MSK_COEF_TRIG ? c.a1 : 0.0;
+  r.s1 = c.kind == MSK_COEF_TRIG ? c.s1 : 0.0;
+  return r;
+}

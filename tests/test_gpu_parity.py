@@ -1,0 +1,265 @@
+"""GPU parity: every step of the CUDA path against the CPU oracle on the same
+seeded Philox paths (FP64 <= 1e-10 and FP32 <= 1e-4 relative L2, integer work
+bit-exact)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import paper_2207_09776_b300 as msk  # noqa: E402
+from oracle import brownian, errors, euler as oeuler, explicit, magnus as omagnus, philox  # noqa: E402
+from oracle import discretization as disc  # noqa: E402
+from workloads import COEF_TRIG, LANGEVIN_32, LANGEVIN_TRIG_128  # noqa: E402
+
+TOL64 = 1e-10
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2207_09776_b300 import build
+    build.build()
+    msk.load_library()
+
+
+def rel_l2(got, ref):
+    got = np.asarray(got, dtype=np.float64).reshape(len(ref), -1)
+    ref = np.asarray(ref, dtype=np.float64).reshape(len(ref), -1)
+    return np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+def solver(w):
+    return msk.Solver(w, device=0)
+
+
+# ---------------------------------------------------------------- integer work (bit-exact)
+
+@pytest.mark.parametrize("seed,path", [(0, 0), (20220719, 7), (2 ** 63 + 12345, (1 << 32) + 5)])
+def test_philox_words_bit_exact(seed, path):
+    n = 1000
+    out = torch.empty(4 * n, dtype=torch.int32, device="cuda")
+    msk.msk_philox_words(seed, path, 0, 17, n, out)
+    got = out.cpu().numpy().view(np.uint32).reshape(n, 4)
+    ref = philox.brownian_words(seed, path, np.arange(17, 17 + n))
+    for r in range(4):
+        np.testing.assert_array_equal(got[:, r], np.asarray(ref[r], dtype=np.uint32))
+
+
+# ---------------------------------------------------------------- Brownian functionals
+
+@pytest.mark.parametrize("w,K", [(LANGEVIN_32.with_(paths=6), 1), (LANGEVIN_32.with_(paths=5), 8),
+                                 (LANGEVIN_TRIG_128.with_(paths=4, n_fine=2048), 16),
+                                 (LANGEVIN_32.with_(paths=3, path_offset=(1 << 32) - 1, n_fine=999), 3)])
+def test_brownian_functionals(w, K):
+    s = solver(w)
+    F = s.functionals(K).cpu().numpy()
+    keys = ("dW", "I1", "I2", "I3", "om", "Jom", "G1", "G2")
+    for p in range(w.paths):
+        ref = brownian.step_functionals(w, p, K)
+        for q, k in enumerate(keys):
+            np.testing.assert_allclose(F[p, :, q], ref[k], rtol=1e-11, atol=1e-13, err_msg=k)
+    dW = s.increments(K).cpu().numpy()
+    for p in range(w.paths):
+        np.testing.assert_allclose(dW[p], brownian.coarse_increments(w, p, K), rtol=1e-11, atol=1e-13)
+    s.close()
+
+
+# ---------------------------------------------------------------- widened-stencil operator
+
+@pytest.mark.parametrize("w,order,K", [(LANGEVIN_32.with_(paths=3), 3, 1),
+                                       (LANGEVIN_32.with_(paths=3, drift_sign=-1, d=64), 2, 4),
+                                       (LANGEVIN_TRIG_128.with_(paths=2, d=32, n_fine=256), 3, 4)])
+def test_omega_matvec_matches_the_oracle_matrix(w, order, K):
+    s = solver(w)
+    Wt = s.weights(order, K)
+    rng = np.random.default_rng(5)
+    u = rng.normal(size=(w.paths, w.d, w.d))
+    ut = torch.tensor(u, device="cuda")
+    for n in range(K):
+        wts = Wt[:, n, :msk.MSK_NOPS].contiguous()
+        out = torch.empty_like(ut)
+        msk.msk_apply_omega(s.ctx, wts, w.paths, ut, out)
+        got = out.cpu().numpy()
+        for p in range(w.paths):
+            Y = omagnus.omega_matrix(w, order, K, p, n)
+            ref = (Y @ u[p].ravel()).reshape(w.d, w.d)
+            scale = np.abs(ref).max()
+            np.testing.assert_allclose(got[p], ref, rtol=0, atol=1e-12 * scale)
+    s.close()
+
+
+def test_taylor_parameters_are_sane():
+    w = LANGEVIN_TRIG_128.with_(paths=8, n_fine=1024)
+    s = solver(w)
+    for prec in (msk.MSK_F64, msk.MSK_F32):
+        Wt = s.weights(3, 8, precision=prec).cpu().numpy()
+        sv, mv, nrm = Wt[..., msk.MSK_WT_S], Wt[..., msk.MSK_WT_M], Wt[..., msk.MSK_WT_NORM]
+        assert np.all(sv >= 1) and np.all(mv >= 1) and np.all(np.isfinite(nrm))
+        theta = nrm / sv                      # per sub-step norm must be admissible
+        assert np.all(theta <= 10.0)
+    s.close()
+
+
+# ---------------------------------------------------------------- full solves
+
+def _oracle_magnus(w, order, K, paths):
+    return omagnus.solve(w, order, K, paths)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_magnus_fp64_small_config_all_paths(order):
+    """d = 32, 100 paths, one step to T = 1 (orders 1, 2, 3)."""
+    w = LANGEVIN_32
+    s = solver(w)
+    u, st = s.magnus(order, 1, precision=msk.MSK_F64, status=True)
+    got = u.cpu().numpy()
+    ref = _oracle_magnus(w, order, 1, list(range(w.paths)))
+    err = rel_l2(got, ref)
+    assert err.max() <= TOL64, err.max()
+    s.close()
+
+
+@pytest.mark.parametrize("w,order,K,paths", [
+    (LANGEVIN_32.with_(paths=7), 2, 10, 7),
+    (LANGEVIN_32.with_(paths=5, drift_sign=-1, a0=1.1, s0=10 ** -0.5), 3, 4, 5),
+    (LANGEVIN_TRIG_128.with_(d=64, paths=3, n_fine=1024), 3, 8, 3),
+    (LANGEVIN_TRIG_128.with_(paths=2, n_fine=1024), 2, 8, 2),
+])
+def test_magnus_fp64_parity(w, order, K, paths):
+    s = solver(w)
+    got = s.magnus(order, K, paths=paths, precision=msk.MSK_F64).cpu().numpy()
+    ref = _oracle_magnus(w, order, K, list(range(paths)))
+    err = rel_l2(got, ref)
+    assert err.max() <= TOL64, err
+    s.close()
+
+
+@pytest.mark.parametrize("w,order,K,paths", [
+    (LANGEVIN_32.with_(paths=20), 2, 1, 20),
+    (LANGEVIN_TRIG_128.with_(d=64, paths=3, n_fine=1024), 3, 8, 3),
+    (LANGEVIN_TRIG_128.with_(paths=2, n_fine=1024), 3, 8, 2),
+])
+def test_magnus_fp32_parity(w, order, K, paths):
+    s = solver(w)
+    u, st = s.magnus(order, K, paths=paths, precision=msk.MSK_F32, status=True)
+    ref = _oracle_magnus(w, order, K, list(range(paths)))
+    err = rel_l2(u.cpu().numpy(), ref)
+    assert err.max() <= TOL32, err
+    assert int(st.cpu().numpy()[:paths].max()) == 0
+    s.close()
+
+
+def test_fp64_and_fp32_agree_on_many_paths():
+    """Ragged path count (not a multiple of the resident-CTA count), the FP32
+    path against the (oracle-checked) FP64 path."""
+    w = LANGEVIN_TRIG_128.with_(d=64, paths=301, n_fine=1024)
+    s = solver(w)
+    u64 = s.magnus(2, 8, precision=msk.MSK_F64)
+    u32 = s.magnus(2, 8, precision=msk.MSK_F32)
+    err = rel_l2(u32.cpu().numpy(), u64.cpu().numpy())
+    assert err.max() <= TOL32
+    # sampled paths against the oracle
+    for p in (0, 150, 300):
+        ref = omagnus.solve_path(w, 2, 8, p)
+        assert rel_l2(u64[p:p + 1].cpu().numpy(), ref[None])[0] <= TOL64
+    s.close()
+
+
+def test_euler_parity():
+    w = LANGEVIN_32.with_(paths=6)
+    s = solver(w)
+    got = s.euler(1000, precision=msk.MSK_F64).cpu().numpy()
+    ref = oeuler.solve(w, 1000, list(range(w.paths)))
+    assert rel_l2(got, ref).max() <= TOL64
+    got32 = s.euler(1000, precision=msk.MSK_F32).cpu().numpy()
+    assert rel_l2(got32, ref).max() <= TOL32
+    s.close()
+
+
+def test_euler_timedep_parity():
+    w = LANGEVIN_TRIG_128.with_(d=32, paths=3, n_fine=2048, ax=-5.0, bx=5.0, av=-5.0, bv=5.0)
+    s = solver(w)
+    got = s.euler(2048, precision=msk.MSK_F64).cpu().numpy()
+    ref = oeuler.solve(w, 2048, list(range(w.paths)))
+    assert rel_l2(got, ref).max() <= TOL64
+    s.close()
+
+
+# ---------------------------------------------------------------- closed form, norms, moments
+
+@pytest.mark.parametrize("w", [LANGEVIN_32.with_(paths=5),
+                               LANGEVIN_TRIG_128.with_(paths=3, d=64, n_fine=2048),
+                               LANGEVIN_32.with_(paths=2, drift_sign=-1, u0_mean=(0.3, -0.4),
+                                                 u0_cov=(0.7, 0.2, 1.2), u0_scale=2 * np.pi)])
+def test_explicit_solution_and_error_norms(w):
+    s = solver(w)
+    ex = s.explicit()
+    ref = explicit.solutions(w)
+    np.testing.assert_allclose(ex.cpu().numpy(), ref, rtol=1e-9, atol=1e-13 * np.abs(ref).max())
+    u = s.magnus(2, 1 if w.n_fine % 2 else 2, precision=msk.MSK_F64)
+    for kappa in (0, 1):
+        e, m = s.error(u, msk.MSK_F64, kappa=kappa)
+        oe = errors.rel_err_per_path(u.cpu().numpy(), ref, kappa)
+        np.testing.assert_allclose(e.cpu().numpy(), oe, rtol=1e-8)
+        assert float(m.cpu()[0]) == pytest.approx(errors.Err(u.cpu().numpy(), ref, kappa), rel=1e-8)
+        e2, _ = s.error(u, msk.MSK_F64, ref=ex, kappa=kappa)
+        np.testing.assert_allclose(e2.cpu().numpy(), oe, rtol=1e-8)
+    mom = s.moments(u, msk.MSK_F64).cpu().numpy()
+    xs, dx = disc.grid(w.d, w.ax, w.bx)
+    vs, dv = disc.grid(w.d, w.av, w.bv)
+    np.testing.assert_allclose(mom, errors.moments(u.cpu().numpy(), xs, vs, dx, dv), rtol=1e-10, atol=1e-12)
+    s.close()
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_empty_and_invalid_calls():
+    w = LANGEVIN_32.with_(paths=2)
+    s = solver(w)
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    msk.msk_solve_magnus(s.ctx, 2, 1, 0, msk.MSK_F64, out)          # zero paths: no-op
+    msk.msk_solve_euler(s.ctx, 10, 0, msk.MSK_F64, out)
+    with pytest.raises(msk.MskError) as e:
+        msk.msk_solve_magnus(s.ctx, 4, 1, 1, msk.MSK_F64, out)       # order out of range
+    assert e.value.status == msk.MSK_ERR_ARG
+    with pytest.raises(msk.MskError):
+        msk.msk_solve_magnus(s.ctx, 2, 3, 1, msk.MSK_F64, out)       # 3 does not divide 10000
+    with pytest.raises(msk.MskError):
+        msk.msk_set_seed(s.ctx, 1, 0, 0, 1.0)
+    with pytest.raises(msk.MskError) as e:
+        msk.msk_set_coefficients(s.ctx, 1, 0, float("inf"), 0, 0.5, 0)
+    assert e.value.status == msk.MSK_ERR_NONFINITE
+    # a single path and the context still works after rejected calls
+    u = s.magnus(2, 1, paths=1)
+    ref = omagnus.solve(w, 2, 1, [0])
+    assert rel_l2(u.cpu().numpy(), ref).max() <= TOL64
+    s.close()
+
+
+def test_deterministic_case_and_blowup_flag():
+    # sigma = 0: order 1 with any step count is exp(T B) u0 (Remark determLangevin)
+    w = LANGEVIN_32.with_(paths=2, s0=0.0)
+    s = solver(w)
+    u1 = s.magnus(1, 1).cpu().numpy()
+    u8 = s.magnus(1, 8).cpu().numpy()
+    assert rel_l2(u8, u1).max() <= 1e-11
+    s.close()
+    # sigma^2 > a: the Ito correction -A^2/2 outweighs the diffusion and the
+    # order-2 solution grows without bound (flagged, not an error)
+    w = LANGEVIN_32.with_(paths=8, s0=3.0)
+    s = solver(w)
+    _, st = s.magnus(2, 1, precision=msk.MSK_F64, status=True)
+    assert (st.cpu().numpy() & msk.MSK_PATH_BLOWUP).any()
+    s.close()
+
+
+def test_paths_are_keyed_by_global_index():
+    w = LANGEVIN_32.with_(paths=6)
+    s = solver(w)
+    full = s.magnus(2, 2).cpu().numpy()
+    msk.msk_set_seed(s.ctx, w.seed, 3, w.n_fine, w.T)
+    tail = s.magnus(2, 2, paths=3).cpu().numpy()
+    np.testing.assert_array_equal(tail, full[3:])
+    s.close()
