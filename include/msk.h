@@ -111,7 +111,9 @@ msk_status msk_create(msk_ctx** out, const msk_grid* grid, int device);
  * Must not be called while work using the context is in flight. */
 void msk_destroy(msk_ctx* ctx);
 
-/* Last error message of the context ("" if none); a static string for ctx NULL. */
+/* Last error message of the context ("" if none).  For ctx NULL: the message
+ * of the last msk_create that failed after validating its arguments on this
+ * thread, or "null context". */
 const char* msk_last_error(const msk_ctx* ctx);
 
 /* Set the coefficient profile (see msk_coeffs).  Non-finite values -> MSK_ERR_NONFINITE. */

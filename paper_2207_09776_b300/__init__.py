@@ -137,7 +137,9 @@ def _need(t, n, dtype, name):
 def msk_create(nx: int, nv: int, ax: float, bx: float, av: float, bv: float, device: int = 0):
     h = _P()
     g = msk_grid(nx, nv, ax, bx, av, bv)
-    _check(load_library().msk_create(ctypes.byref(h), ctypes.byref(g), device))
+    st = load_library().msk_create(ctypes.byref(h), ctypes.byref(g), device)
+    if st != MSK_OK:
+        raise MskError(st, load_library().msk_last_error(None).decode())
     return h
 
 

@@ -7,6 +7,9 @@
 
 msk_status msk_refresh_u0max(msk_ctx* ctx, cudaStream_t stream);
 
+// Message of the last failed msk_create on this thread (returned for ctx NULL).
+static thread_local std::string t_create_err = "null context";
+
 msk_status msk_fail(msk_ctx* ctx, msk_status st, const std::string& msg) {
   if (ctx) ctx->err = msg;
   return st;
@@ -39,7 +42,7 @@ bool msk_supported_d(int d) { return d == 32 || d == 64 || d == 128 || d == 256 
 static bool is_fin(double x) { return isfinite(x) != 0; }
 
 extern "C" const char* msk_last_error(const msk_ctx* ctx) {
-  if (!ctx) return "null context";
+  if (!ctx) return t_create_err.c_str();
   return ctx->err.c_str();
 }
 
@@ -87,6 +90,7 @@ extern "C" msk_status msk_create(msk_ctx** out, const msk_grid* g, int device) {
   if (st == MSK_OK) st = launch_band_tables(ctx, 0);
   if (st == MSK_OK) st = launch_gaussian_u0(ctx, 0);
   if (st != MSK_OK) {
+    t_create_err = ctx->err;
     msk_destroy(ctx);
     return st;
   }

@@ -8,16 +8,22 @@
 // the products of the truncated matrices (the commutators of Eq.
 // MagnusFormulas computed the way the paper computes them, as sparse matrix
 // products).  Commutators with Nv use the exact difference v_j - v_l =
-// (j - l) dv, so interior rows are bit-identical.
+// (j - l) dv, so interior rows are bit-identical.  Products and sums use
+// explicit round-to-nearest operations (no fused multiply-add contraction), so
+// x y - y x cancels to an exact zero as it does in unfused arithmetic.
 #include "philox.cuh"
 #include "stencil.cuh"
 
 namespace {
 
+__device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+
 struct VPrims {
   int D;
   double dv, av, kappa;
-  __device__ double nv(int j, int l) const { return j == l ? av + (j + 1) * dv : 0.0; }
+  __device__ double nv(int j, int l) const { return j == l ? add(av, mul((double)(j + 1), dv)) : 0.0; }
   __device__ double t1(int j, int l) const {
     if (l < 0 || l >= D || j < 0 || j >= D) return 0.0;
     if (l == j + 1) return 0.5 / dv;
@@ -31,47 +37,47 @@ struct VPrims {
     return 0.0;
   }
   // P = [Nv, T1], Q = [T2, T1]
-  __device__ double P(int j, int l) const { return (j - l) * dv * t1(j, l); }
+  __device__ double P(int j, int l) const { return mul(mul((double)(j - l), dv), t1(j, l)); }
   __device__ double Q(int j, int l) const {
     if (j < 0 || j >= D || l < 0 || l >= D) return 0.0;
     double s = 0.0;
-    for (int m = j - 1; m <= j + 1; ++m) s += t2(j, m) * t1(m, l) - t1(j, m) * t2(m, l);
+    for (int m = j - 1; m <= j + 1; ++m) s = add(s, sub(mul(t2(j, m), t1(m, l)), mul(t1(j, m), t2(m, l))));
     return s;
   }
   __device__ double entry(int op, int j, int l) const {
     if (j < 0 || j >= D || l < 0 || l >= D) return 0.0;
     switch (op) {
-      case MSK_OP_BX: return kappa * nv(j, l);
+      case MSK_OP_BX: return mul(kappa, nv(j, l));
       case MSK_OP_BVV: return t2(j, l);
       case MSK_OP_A0: return t1(j, l);
       case MSK_OP_A0A0: {
         double s = 0.0;
-        for (int m = j - 1; m <= j + 1; ++m) s += t1(j, m) * t1(m, l);
+        for (int m = j - 1; m <= j + 1; ++m) s = add(s, mul(t1(j, m), t1(m, l)));
         return s;
       }
-      case MSK_OP_BX_A0: return kappa * P(j, l);
+      case MSK_OP_BX_A0: return mul(kappa, P(j, l));
       case MSK_OP_BVV_A0: return Q(j, l);
-      case MSK_OP_BX_BVV: return kappa * (j - l) * dv * t2(j, l);
+      case MSK_OP_BX_BVV: return mul(kappa, mul(mul((double)(j - l), dv), t2(j, l)));
       case MSK_OP_BXA0_A0: {
         double s = 0.0;
-        for (int m = j - 1; m <= j + 1; ++m) s += P(j, m) * t1(m, l) - t1(j, m) * P(m, l);
-        return kappa * s;
+        for (int m = j - 1; m <= j + 1; ++m) s = add(s, sub(mul(P(j, m), t1(m, l)), mul(t1(j, m), P(m, l))));
+        return mul(kappa, s);
       }
       case MSK_OP_BVVA0_A0: {
         double s = 0.0;
-        for (int m = j - 2; m <= j + 2; ++m) s += Q(j, m) * t1(m, l) - t1(j, m) * Q(m, l);
+        for (int m = j - 2; m <= j + 2; ++m) s = add(s, sub(mul(Q(j, m), t1(m, l)), mul(t1(j, m), Q(m, l))));
         return s;
       }
-      case MSK_OP_BXA0_BX: return kappa * kappa * (l - j) * dv * P(j, l);
+      case MSK_OP_BXA0_BX: return mul(mul(kappa, kappa), mul(mul((double)(l - j), dv), P(j, l)));
       case MSK_OP_BXA0_BVV: {
         double s = 0.0;
-        for (int m = j - 1; m <= j + 1; ++m) s += P(j, m) * t2(m, l) - t2(j, m) * P(m, l);
-        return kappa * s;
+        for (int m = j - 1; m <= j + 1; ++m) s = add(s, sub(mul(P(j, m), t2(m, l)), mul(t2(j, m), P(m, l))));
+        return mul(kappa, s);
       }
-      case MSK_OP_BVVA0_BX: return kappa * (l - j) * dv * Q(j, l);
+      case MSK_OP_BVVA0_BX: return mul(kappa, mul(mul((double)(l - j), dv), Q(j, l)));
       case MSK_OP_BVVA0_BVV: {
         double s = 0.0;
-        for (int m = j - 2; m <= j + 2; ++m) s += Q(j, m) * t2(m, l) - t2(j, m) * Q(m, l);
+        for (int m = j - 2; m <= j + 2; ++m) s = add(s, sub(mul(Q(j, m), t2(m, l)), mul(t2(j, m), Q(m, l))));
         return s;
       }
     }
