@@ -55,6 +55,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-comparators", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=0, help="paths in the CPU-oracle sample (0 = auto)")
+    p.add_argument("--profile-case", type=int, default=0, metavar="PATHS",
+                   help="run two plain solves of the benchmark workload with PATHS paths at K = 8 "
+                        "(a small case for ncu captures) and exit")
     return p.parse_args()
 
 
@@ -412,8 +415,34 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(a):
+    """Two solves (functionals, weights, engine) of the workload on a small path count."""
+    import torch
+
+    import paper_2207_09776_b300 as msk
+    from paper_2207_09776_b300 import build as mbuild
+    mbuild.build()
+    msk.load_library()
+    P, K = a.profile_case, K_CANDIDATES[0]
+    w = LANGEVIN_TRIG_128.with_(paths=P)
+    s = msk.Solver(w)
+    F = torch.empty(P * K * msk.MSK_NF, dtype=torch.float64, device="cuda")
+    Wt = torch.empty(P * K * msk.MSK_NWT, dtype=torch.float64, device="cuda")
+    out = torch.empty(P * w.d * w.d, dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        msk.msk_brownian_functionals(s.ctx, K, P, F)
+        msk.msk_omega_weights(s.ctx, ORDER, K, P, msk.MSK_F32, F, Wt)
+        msk.msk_magnus_from_weights(s.ctx, K, P, msk.MSK_F32, Wt, out)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": P, "matvecs": msk.msk_work_counter(s.ctx)}))
+    s.close()
+
+
 def main():
     a = parse()
+    if a.profile_case:
+        run_profile_case(a)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:

@@ -13,11 +13,24 @@
 //     int omega~ += delta (omega0 + omega1) / 2
 //     G1 = int omega~ ds - sum s_mid sigma(t_mid) dW_k
 //     G2 = delta/2 sum (alpha0 omega0 + alpha1 omega1) - sum alpha_bar(s_mid) sigma(t_mid) dW_k.
-// One thread integrates one (path, step) pair sequentially over its fine cells.
+//
+// Parallel layout: one warp per (path, step).  The step's fine cells are
+// processed in rounds of 32 x 64 cells; in a round each lane draws the normals
+// of 64 consecutive cells (Philox4x32-10 + Box-Muller, double precision) into
+// shared memory and sums its chunk's dW and sigma dW; an exclusive warp scan
+// gives every lane the values of W~ and omega~ at its chunk start; a second
+// pass over the staged increments accumulates the functionals, which are
+// summed over the warp at the end.  The deterministic per-cell values
+// (sigma at cell midpoints, alpha at the nodes, the antiderivative of alpha at
+// the midpoints) come from a table built once per (T, n_fine, coefficients).
 #include "philox.cuh"
 #include "msk_internal.cuh"
 
 namespace {
+
+constexpr int kChunk = 64;                 // cells per lane per round
+constexpr int kWarps = 4;                  // warps (path-steps) per block
+constexpr int kRound = 32 * kChunk;        // cells per round
 
 struct BrownArgs {
   uint64_t seed, path_offset;
@@ -25,90 +38,175 @@ struct BrownArgs {
   int steps;
   double T;
   CoefDev c;
+  const double* tab;   // TRIG: [3][n_fine + 1]: sigma(mid), alpha(node), A(mid); null for CONST
 };
 
-__device__ __forceinline__ double sigma_t(const CoefDev& c, double t) {
-  return c.s0 * (1.0 + c.s1 * cospi(2.0 * t));
+// antiderivative of alpha: A(t) = int_0^t alpha = (a0 t + a1 (1 - cos 2 pi t) / (2 pi)) / 2
+__device__ __forceinline__ double alpha_anti(const CoefDev& c, double t) {
+  return 0.5 * (c.a0 * t + c.a1 * (1.0 - cospi(2.0 * t)) / (2.0 * M_PI));
 }
-__device__ __forceinline__ double alpha_t(const CoefDev& c, double t) {
-  return 0.5 * (c.a0 + c.a1 * sinpi(2.0 * t));
+
+__global__ void cell_table_kernel(CoefDev c, int64_t n_fine, double T, double* tab) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > n_fine) return;
+  const double delta = T / (double)n_fine;
+  const double tk = delta * (double)k, tm = delta * ((double)k + 0.5);
+  tab[k] = c.s0 * (1.0 + c.s1 * cospi(2.0 * tm));                              // sigma at cell midpoint
+  tab[(n_fine + 1) + k] = 0.5 * (c.a0 + c.a1 * sinpi(2.0 * tk));                  // alpha at node
+  tab[2 * (n_fine + 1) + k] = alpha_anti(c, tm);                                  // A at cell midpoint
 }
-// int_{t0}^{t0+s} alpha
-__device__ __forceinline__ double alpha_bar(const CoefDev& c, double t0, double s) {
-  return 0.5 * (c.a0 * s + c.a1 * (cospi(2.0 * t0) - cospi(2.0 * (t0 + s))) / (2.0 * M_PI));
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_excl_scan(double v, int lane) {
+  double x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x - v;
 }
 
 template <bool FULL, bool TRIG>
-__global__ void brownian_kernel(BrownArgs a, double* __restrict__ out) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= a.paths * a.steps) return;
+__global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, double* __restrict__ out) {
+  __shared__ double stage[kWarps][32 * kChunk];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t idx = (int64_t)blockIdx.x * kWarps + wib;   // (path, step) pair of this warp
+  if (idx >= a.paths * a.steps) return;                     // whole warp leaves together
   const int64_t p = idx / a.steps;
   const int n = (int)(idx % a.steps);
   const int64_t L = a.n_fine / a.steps;
   const double delta = a.T / (double)a.n_fine;
   const double sq = sqrt(delta);
-  const double h = a.T / a.steps;
-  const double tn = n * h;
   const uint64_t gpath = a.path_offset + (uint64_t)p;
-  const int64_t f0 = (int64_t)n * L;
+  const int64_t f0 = (int64_t)n * L;                        // first fine cell of the step
+  const double* tsig = a.tab;
+  const double* talp = a.tab + (a.n_fine + 1);
+  const double* tA = a.tab + 2 * (a.n_fine + 1);
+  double* st = stage[wib];
+  const double Astart = TRIG ? alpha_anti(a.c, delta * (double)f0) : 0.0;   // A at the step start
+  const double sg0 = a.c.s0, al0 = 0.5 * a.c.a0;
 
-  double w0 = 0.0, I1 = 0.0, I2 = 0.0, I3 = 0.0;
-  double om0 = 0.0, jom = 0.0, ssdw = 0.0, jaom = 0.0, abdw = 0.0;
-  double z0 = 0.0, z1 = 0.0;
-  for (int64_t k = 0; k < L; ++k) {
-    const int64_t fi = f0 + k;
-    if (k == 0 || (fi & 1) == 0) brownian_pair(a.seed, gpath, 0u, (uint64_t)(fi >> 1), z0, z1);
-    const double dw = sq * ((fi & 1) ? z1 : z0);
-    const double w1 = w0 + dw;
-    if (FULL) {
-      const double s0 = delta * (double)k, s1 = delta * (double)(k + 1);
-      I1 += delta * (w0 + w1) / 2.0;
-      I2 += delta * (w0 * w0 + w0 * w1 + w1 * w1) / 3.0;
-      I3 += delta * (s0 * (2.0 * w0 + w1) + s1 * (w0 + 2.0 * w1)) / 6.0;
-      const double smid = delta * ((double)k + 0.5);
-      const double sig = TRIG ? sigma_t(a.c, tn + smid) : a.c.s0;
-      const double om1 = om0 + sig * dw;
-      jom += delta * (om0 + om1) / 2.0;
-      ssdw += smid * sig * dw;
-      if (TRIG) {
-        jaom += delta * (alpha_t(a.c, tn + s0) * om0 + alpha_t(a.c, tn + s1) * om1) / 2.0;
-        abdw += alpha_bar(a.c, tn, smid) * sig * dw;
-      } else {
-        const double al = 0.5 * a.c.a0;
-        jaom += delta * (al * om0 + al * om1) / 2.0;
-        abdw += al * smid * sig * dw;
-      }
-      om0 = om1;
+  double W0 = 0.0, O0 = 0.0;                                // W~ and omega~ at the round start
+  double S1 = 0.0, S2 = 0.0, S3 = 0.0, J1 = 0.0, J2 = 0.0, J3 = 0.0, J4 = 0.0;
+  for (int64_t rb = 0; rb < L; rb += kRound) {
+    // ---- pass 1: normals of this lane's chunk, chunk sums -------------------------
+    const int64_t c0 = rb + (int64_t)lane * kChunk;
+    const int cnt = (int)max((int64_t)0, min((int64_t)kChunk, L - c0));
+    double sw = 0.0, so = 0.0, z0 = 0.0, z1 = 0.0;
+    for (int q = 0; q < cnt; ++q) {
+      const int64_t fi = f0 + c0 + q;
+      if (q == 0 || (fi & 1) == 0) brownian_pair(a.seed, gpath, 0u, (uint64_t)(fi >> 1), z0, z1);
+      const double dw = sq * ((fi & 1) ? z1 : z0);
+      st[q * 32 + lane] = dw;
+      sw += dw;
+      if (FULL) so += (TRIG ? tsig[fi] : sg0) * dw;
     }
-    w0 = w1;
+    const double woff = W0 + warp_excl_scan(sw, lane);
+    const double ooff = O0 + warp_excl_scan(so, lane);
+    W0 += warp_sum(sw);
+    O0 += warp_sum(so);
+    if (!FULL) continue;
+    // ---- pass 2: functionals over the staged increments -------------------------
+    // Sums are kept without their constant factors (delta/2, delta/3, delta^2/6,
+    // delta), applied once at the end; k is carried as a double counter.
+    double w0 = woff, om0 = ooff;
+    double kd = (double)c0;
+    for (int q = 0; q < cnt; ++q) {
+      const int64_t fi = f0 + c0 + q;
+      const double dw = st[q * 32 + lane];
+      const double w1 = w0 + dw;
+      const double ws = w0 + w1;
+      S1 += ws;                                              // delta/2 sum (w0 + w1)
+      S2 = fma(w0, ws, fma(w1, w1, S2));                     // delta/3 sum (w0^2 + w0 w1 + w1^2)
+      S3 = fma(3.0 * kd, ws, S3 + (w0 + 2.0 * w1));          // delta^2/6 sum (3k (w0+w1) + w0 + 2 w1)
+      const double sig = TRIG ? tsig[fi] : sg0;
+      const double sdw = sig * dw;
+      const double om1 = om0 + sdw;
+      J1 += om0 + om1;                                       // delta/2 sum (om0 + om1)
+      J2 = fma(kd + 0.5, sdw, J2);                           // delta sum (k + 1/2) sigma dW
+      if (TRIG) {
+        J3 = fma(talp[fi], om0, fma(talp[fi + 1], om1, J3)); // delta/2 sum (alpha0 om0 + alpha1 om1)
+        J4 = fma(tA[fi] - Astart, sdw, J4);                  // sum alpha_bar(s_mid) sigma dW
+      }
+      w0 = w1;
+      om0 = om1;
+      kd += 1.0;
+    }
+    __syncwarp();   // the stage buffer is rewritten by the next round
   }
   if (FULL) {
-    double* o = out + idx * MSK_NF;
-    o[MSK_F_DW] = w0;
-    o[MSK_F_I1] = I1;
-    o[MSK_F_I2] = I2;
-    o[MSK_F_I3] = I3;
-    o[MSK_F_OM] = om0;
-    o[MSK_F_JOM] = jom;
-    o[MSK_F_G1] = jom - ssdw;
-    o[MSK_F_G2] = jaom - abdw;
-  } else {
-    out[idx] = w0;
+    const double I1 = 0.5 * delta * warp_sum(S1);
+    const double I2 = delta / 3.0 * warp_sum(S2);
+    const double I3 = delta * delta / 6.0 * warp_sum(S3);
+    const double jom = 0.5 * delta * warp_sum(J1);
+    const double ssdw = delta * warp_sum(J2);
+    // constant coefficients: alpha_bar(s) = alpha s and alpha0 = alpha1 = alpha
+    const double jaom = TRIG ? 0.5 * delta * warp_sum(J3) : al0 * jom;
+    const double abdw = TRIG ? warp_sum(J4) : al0 * ssdw;
+    if (lane == 0) {
+      double* o = out + idx * MSK_NF;
+      o[MSK_F_DW] = W0;
+      o[MSK_F_I1] = I1;
+      o[MSK_F_I2] = I2;
+      o[MSK_F_I3] = I3;
+      o[MSK_F_OM] = O0;
+      o[MSK_F_JOM] = jom;
+      o[MSK_F_G1] = jom - ssdw;
+      o[MSK_F_G2] = jaom - abdw;
+    }
+  } else if (lane == 0) {
+    out[idx] = W0;
   }
 }
 
 }  // namespace
 
+// Per-cell table of the deterministic coefficient values, rebuilt when T,
+// n_fine or the coefficient profile changed since the last build.
+static msk_status ensure_cell_table(msk_ctx* ctx, cudaStream_t stream) {
+  const msk_coeffs& c = ctx->coef;
+  if (ctx->tab && ctx->tab_n == ctx->n_fine && ctx->tab_T == ctx->T && ctx->tab_coef.a0 == c.a0 &&
+      ctx->tab_coef.a1 == c.a1 && ctx->tab_coef.s0 == c.s0 && ctx->tab_coef.s1 == c.s1 &&
+      ctx->tab_coef.kind == c.kind)
+    return MSK_OK;
+  if (ctx->tab && ctx->tab_n != ctx->n_fine) {
+    cudaFree(ctx->tab);   // waits for work that may still read it
+    ctx->tab = nullptr;
+  }
+  if (!ctx->tab) {
+    msk_status st = msk_cuda(ctx, cudaMalloc(&ctx->tab, 3 * (size_t)(ctx->n_fine + 1) * sizeof(double)),
+                             "cell table allocation");
+    if (st != MSK_OK) return st;
+  }
+  const int64_t n = ctx->n_fine + 1;
+  cell_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(coef_dev(c), ctx->n_fine, ctx->T, ctx->tab);
+  msk_status st = msk_cuda(ctx, cudaGetLastError(), "cell table");
+  if (st != MSK_OK) return st;
+  ctx->tab_n = ctx->n_fine;
+  ctx->tab_T = ctx->T;
+  ctx->tab_coef = c;
+  return MSK_OK;
+}
+
 msk_status launch_brownian(msk_ctx* ctx, int steps, int64_t paths, double* out, bool increments_only,
                            cudaStream_t stream) {
-  BrownArgs a{ctx->seed, ctx->path_offset, ctx->n_fine, paths, steps, ctx->T, coef_dev(ctx->coef)};
   const int64_t n = paths * steps;
   if (n == 0) return MSK_OK;
-  const int threads = 128;
-  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
   const bool trig = ctx->coef.kind == MSK_COEF_TRIG;
-  if (increments_only) brownian_kernel<false, false><<<blocks, threads, 0, stream>>>(a, out);
-  else if (trig) brownian_kernel<true, true><<<blocks, threads, 0, stream>>>(a, out);
-  else brownian_kernel<true, false><<<blocks, threads, 0, stream>>>(a, out);
+  if (trig && !increments_only) {
+    msk_status st = ensure_cell_table(ctx, stream);
+    if (st != MSK_OK) return st;
+  }
+  BrownArgs a{ctx->seed, ctx->path_offset, ctx->n_fine, paths, steps, ctx->T, coef_dev(ctx->coef),
+              trig ? ctx->tab : nullptr};
+  const unsigned blocks = (unsigned)((n + kWarps - 1) / kWarps);
+  if (increments_only) brownian_kernel<false, false><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
+  else if (trig) brownian_kernel<true, true><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
+  else brownian_kernel<true, false><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
   return msk_cuda(ctx, cudaGetLastError(), "brownian kernel");
 }

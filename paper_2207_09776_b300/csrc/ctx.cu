@@ -5,8 +5,6 @@
 
 #include "msk_internal.cuh"
 
-msk_status msk_refresh_u0max(msk_ctx* ctx, cudaStream_t stream);
-
 // Message of the last failed msk_create on this thread (returned for ctx NULL).
 static thread_local std::string t_create_err = "null context";
 
@@ -54,6 +52,7 @@ extern "C" void msk_destroy(msk_ctx* ctx) {
   if (ctx->aux) cudaFree(ctx->aux);
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (ctx->work) cudaFree(ctx->work);
+  if (ctx->tab) cudaFree(ctx->tab);
   delete ctx;
 }
 
@@ -130,10 +129,8 @@ extern "C" msk_status msk_set_initial(msk_ctx* ctx, const double* u0_dev, void* 
   msk_status st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
   if (st != MSK_OK) return st;
   const size_t dd = (size_t)ctx->d * ctx->d;
-  st = msk_cuda(ctx, cudaMemcpyAsync(ctx->u0, u0_dev, dd * sizeof(double), cudaMemcpyDeviceToDevice,
-                                     (cudaStream_t)stream), "copy u0");
-  if (st != MSK_OK) return st;
-  return msk_refresh_u0max(ctx, (cudaStream_t)stream);
+  return msk_cuda(ctx, cudaMemcpyAsync(ctx->u0, u0_dev, dd * sizeof(double), cudaMemcpyDeviceToDevice,
+                                       (cudaStream_t)stream), "copy u0");
 }
 
 extern "C" msk_status msk_set_seed(msk_ctx* ctx, uint64_t seed, uint64_t path_offset, int64_t n_fine, double T) {

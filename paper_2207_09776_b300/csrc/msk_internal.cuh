@@ -25,11 +25,14 @@ struct msk_ctx {
   double T = 1.0;
   double* u0 = nullptr;       // [d][d] (v-major, x fastest), device
   double* band = nullptr;     // [MSK_NOPS][d][MSK_BAND], device
-  double* aux = nullptr;      // [MSK_NOPS] operator traces, then C_T (3), then u0 max (1)
+  double* aux = nullptr;      // [MSK_NOPS] operator traces, then C_T (3), then check flags
   unsigned long long* work = nullptr;   // engine work counter (stencil applications)
   double host_trace[MSK_NOPS] = {0};
-  double host_u0max = 0;
   double cT[3] = {0, 0, 0};   // deterministic covariance of the closed form
+  double* tab = nullptr;      // per fine cell: sigma(mid), alpha(node), A(mid) (time-dependent coefficients)
+  int64_t tab_n = 0;
+  double tab_T = 0;
+  msk_coeffs tab_coef{};
   void* scratch = nullptr;    // library-owned scratch (functionals + weights)
   size_t scratch_bytes = 0;
   int num_sms = 0;

@@ -146,19 +146,6 @@ __global__ void gaussian_u0_kernel(int D, double ax, double dx, double av, doubl
   u0[idx] = g.scale * exp(-0.5 * q) / (2.0 * M_PI * sqrt(det));
 }
 
-__global__ void max_abs_kernel(const double* x, int n, double* out) {
-  __shared__ double red[256];
-  double m = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(x[i]));
-  red[threadIdx.x] = m;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = red[0];
-}
-
 // out = Omega u, one thread per grid point, with Omega's coefficients folded per row.
 __global__ void apply_omega_kernel(const double* band, int D, double inv2dx, double inv4dx2,
                                    const double* weights, int64_t paths, const double* u,
@@ -235,26 +222,9 @@ msk_status launch_gaussian_u0(msk_ctx* ctx, cudaStream_t stream) {
   const int n = ctx->d * ctx->d;
   gaussian_u0_kernel<<<(n + 255) / 256, 256, 0, stream>>>(ctx->d, ctx->ax, ctx->dx, ctx->av, ctx->dv,
                                                           ctx->u0g, ctx->u0);
-  double* dmax = ctx->aux + MSK_NOPS + 4;
-  max_abs_kernel<<<1, 256, 0, stream>>>(ctx->u0, n, dmax);
   msk_status st = msk_cuda(ctx, cudaGetLastError(), "gaussian u0");
   if (st != MSK_OK) return st;
-  st = msk_cuda(ctx, cudaMemcpyAsync(&ctx->host_u0max, dmax, sizeof(double), cudaMemcpyDeviceToHost,
-                                     stream), "copy u0 max");
-  if (st != MSK_OK) return st;
   return msk_cuda(ctx, cudaStreamSynchronize(stream), "sync u0");
-}
-
-msk_status msk_refresh_u0max(msk_ctx* ctx, cudaStream_t stream) {
-  const int n = ctx->d * ctx->d;
-  double* dmax = ctx->aux + MSK_NOPS + 4;
-  max_abs_kernel<<<1, 256, 0, stream>>>(ctx->u0, n, dmax);
-  msk_status st = msk_cuda(ctx, cudaGetLastError(), "u0 max");
-  if (st != MSK_OK) return st;
-  st = msk_cuda(ctx, cudaMemcpyAsync(&ctx->host_u0max, dmax, sizeof(double), cudaMemcpyDeviceToHost,
-                                     stream), "copy u0 max");
-  if (st != MSK_OK) return st;
-  return msk_cuda(ctx, cudaStreamSynchronize(stream), "sync u0 max");
 }
 
 extern "C" msk_status msk_apply_omega(msk_ctx* ctx, const double* weights_dev, int64_t paths,
