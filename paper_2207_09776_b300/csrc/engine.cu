@@ -84,6 +84,7 @@ struct Cfg {
   static constexpr size_t OFF_SLOT = OFF_SCALE + kMaxTerms + 1;   // 2 x NW x 2 norm slots
   static constexpr size_t NELEM = OFF_SLOT + 4 * NW;
   static constexpr size_t SMEM = NELEM * sizeof(T);
+  static_assert(SMEM <= 232448, "slab does not fit the 227 KB of shared memory per CTA");
 };
 
 template <typename T> struct V4 { T x, y, z, w; };
@@ -184,12 +185,15 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineArgs a) {
   }
   sync_all<C>();
 
-  // left/right column pairs of row p from the four own columns `v` of that row
-  auto pairs = [&](const V4<T>& v, const T* buf, int p, T (&l)[2], T (&r)[2]) {
-    // the shuffles cross a row boundary for the first/last thread of a row: those
-    // neighbours are outside the grid and are zeroed by a 0/1 factor
-    T lz = __shfl_up_sync(0xffffffffu, v.z, 1) * mL, lw = __shfl_up_sync(0xffffffffu, v.w, 1) * mL;
-    T rx = __shfl_down_sync(0xffffffffu, v.x, 1) * mR, ry = __shfl_down_sync(0xffffffffu, v.y, 1) * mR;
+  // For row p with own columns v: the centred x differences d1 = u(i+1) - u(i-1)
+  // and the distance-two sums s2 = u(i+2) + u(i-2) of the thread's four columns.
+  // The neighbour columns come from the adjacent threads by shuffles; across a
+  // row boundary they lie outside the grid and a 0/1 factor fused into the
+  // multiply-adds removes them; across a warp boundary they are read from
+  // shared memory.
+  auto xterms = [&](const V4<T>& v, const T* buf, int p, V4<T>& d1, V4<T>& s2) {
+    T lz = __shfl_up_sync(0xffffffffu, v.z, 1), lw = __shfl_up_sync(0xffffffffu, v.w, 1);
+    T rx = __shfl_down_sync(0xffffffffu, v.x, 1), ry = __shfl_down_sync(0xffffffffu, v.y, 1);
     if (ldsL) {
       lz = buf[at(p, i0 - 2)];
       lw = buf[at(p, i0 - 1)];
@@ -198,10 +202,14 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineArgs a) {
       rx = buf[at(p, i0 + 4)];
       ry = buf[at(p, i0 + 5)];
     }
-    l[0] = lz;
-    l[1] = lw;
-    r[0] = rx;
-    r[1] = ry;
+    d1.x = fma(-mL, lw, v.y);
+    d1.y = v.z - v.x;
+    d1.z = v.w - v.y;
+    d1.w = fma(mR, rx, -v.z);
+    s2.x = fma(mL, lz, v.z);
+    s2.y = fma(mL, lw, v.w);
+    s2.z = fma(mR, rx, v.x);
+    s2.w = fma(mR, ry, v.y);
   };
 
   // store the four own columns of local row p into buffer b, and into the facing
@@ -333,30 +341,24 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineArgs a) {
           const int nxt = cur ^ 1;
           const T* src = sm + cur * K::BUF;
           T mn = T(0), ma = T(0);
-          // sliding window: own columns of rows j-2..j+2, neighbour pairs of rows j-1..j+1
+          // sliding window: own columns of rows j-2..j+2, x terms of rows j-1..j+1
           V4<T> cw0 = ld4(src + at(j0 - 2, i0)), cw1 = ld4(src + at(j0 - 1, i0));
           V4<T> cw2 = ld4(src + at(j0, i0)), cw3 = ld4(src + at(j0 + 1, i0));
-          T l0[2], r0v[2], l1[2], r1v[2], l2[2], r2v[2];
-          pairs(cw1, src, j0 - 1, l0, r0v);
-          pairs(cw2, src, j0, l1, r1v);
+          V4<T> d10, s20, d11, s21, d12, s22;
+          xterms(cw1, src, j0 - 1, d10, s20);
+          xterms(cw2, src, j0, d11, s21);
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const int p = j0 + r;
             const int jg = r0 + p;
             const V4<T> cw4 = ld4(src + at(p + 2, i0));
-            pairs(cw3, src, p + 1, l2, r2v);
+            xterms(cw3, src, p + 1, d12, s22);
             RowCoef<T> c = ci;
             if (is_special_row(jg, D)) c = make(coef + special_index(jg, D) * MSK_NCOEF);
             else c.b1 = b0row[p] * sc;
             V4<T> out;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              // x-neighbours of column i0 + q at rows j-1 (0), j (1), j+1 (2)
-              const T xm1_0 = q == 0 ? l0[1] : get(cw1, q - 1), xp1_0 = q == 3 ? r0v[0] : get(cw1, q + 1);
-              const T xm1_1 = q == 0 ? l1[1] : get(cw2, q - 1), xp1_1 = q == 3 ? r1v[0] : get(cw2, q + 1);
-              const T xm1_2 = q == 0 ? l2[1] : get(cw3, q - 1), xp1_2 = q == 3 ? r2v[0] : get(cw3, q + 1);
-              const T xm2_0 = q < 2 ? l0[q] : get(cw1, q - 2), xp2_0 = q > 1 ? r0v[q - 2] : get(cw1, q + 2);
-              const T xm2_2 = q < 2 ? l2[q] : get(cw3, q - 2), xp2_2 = q > 1 ? r2v[q - 2] : get(cw3, q + 2);
               const T a1 = q == 0 ? c.a1q0 : (q == 3 ? c.a1q3 : c.a1);
               const T a3 = q == 0 ? c.a3q0 : (q == 3 ? c.a3q3 : c.a3);
               T v = c.a0 * get(cw0, q);
@@ -364,11 +366,11 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineArgs a) {
               v = fma(c.a2, get(cw2, q), v);
               v = fma(a3, get(cw3, q), v);
               v = fma(c.a4, get(cw4, q), v);
-              v = fma(c.b0, xp1_0 - xm1_0, v);
-              v = fma(c.b1, xp1_1 - xm1_1, v);
-              v = fma(c.b2, xp1_2 - xm1_2, v);
-              v = fma(c.c0, xp2_0 + xm2_0, v);
-              v = fma(c.c1, xp2_2 + xm2_2, v);
+              v = fma(c.b0, get(d10, q), v);
+              v = fma(c.b1, get(d11, q), v);
+              v = fma(c.b2, get(d12, q), v);
+              v = fma(c.c0, get(s20, q), v);
+              v = fma(c.c1, get(s22, q), v);
               set(out, q, v);
             }
             store_row(nxt, p, out);
@@ -383,8 +385,7 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineArgs a) {
               ma = tmax(ma, amax4(acc[r]));
             }
             cw0 = cw1; cw1 = cw2; cw2 = cw3; cw3 = cw4;
-            l0[0] = l1[0]; l0[1] = l1[1]; l1[0] = l2[0]; l1[1] = l2[1];
-            r0v[0] = r1v[0]; r0v[1] = r1v[1]; r1v[0] = r2v[0]; r1v[1] = r2v[1];
+            d10 = d11; s20 = s21; d11 = d12; s21 = s22;
           }
           ++nmv;
           if constexpr (EULER) {

@@ -263,3 +263,42 @@ def test_paths_are_keyed_by_global_index():
     tail = s.magnus(2, 2, paths=3).cpu().numpy()
     np.testing.assert_array_equal(tail, full[3:])
     s.close()
+
+
+# ---------------------------------------------------------------- cluster configurations
+
+from workloads import BATCH_GRIDS, LARGE_512  # noqa: E402
+
+
+@pytest.mark.parametrize("precision,tol", [(msk.MSK_F32, TOL32), (msk.MSK_F64, TOL64)])
+def test_d256_cluster_slabs_match_the_oracle(precision, tol):
+    """256 x 256: four (float) or eight (double) CTAs per path exchange halo rows
+    through distributed shared memory."""
+    w = BATCH_GRIDS[2].with_(paths=2, T=0.25, n_fine=256)
+    s = solver(w)
+    u, st = s.magnus(3, 2, precision=precision, status=True)
+    ref = _oracle_magnus(w, 3, 2, [0, 1])
+    assert rel_l2(u.cpu().numpy(), ref).max() <= tol
+    assert int(st.cpu().numpy().max()) == 0
+    s.close()
+
+
+def test_d512_sixteen_cta_clusters_match_the_oracle():
+    w = LARGE_512[1].with_(paths=1, T=0.05, n_fine=64)
+    s = solver(w)
+    u = s.magnus(2, 1, precision=msk.MSK_F32)
+    ref = _oracle_magnus(w, 2, 1, [0])
+    assert rel_l2(u.cpu().numpy(), ref).max() <= TOL32
+    with pytest.raises(msk.MskError) as e:
+        s.magnus(2, 1, precision=msk.MSK_F64)        # double at 512^2 is not built
+    assert e.value.status == msk.MSK_ERR_UNSUPPORTED
+    s.close()
+
+
+def test_d256_euler_clusters():
+    w = BATCH_GRIDS[2].with_(paths=2, T=0.05, n_fine=64)
+    s = solver(w)
+    ref = oeuler.solve(w, 64, [0, 1])
+    assert rel_l2(s.euler(64, precision=msk.MSK_F64).cpu().numpy(), ref).max() <= TOL64
+    assert rel_l2(s.euler(64, precision=msk.MSK_F32).cpu().numpy(), ref).max() <= TOL32
+    s.close()
