@@ -186,6 +186,26 @@ msk_status msk_magnus_from_weights(msk_ctx* ctx, int steps, int64_t paths, int p
                                    const double* Wt_dev, void* u_out_dev,
                                    uint32_t* path_status_dev, void* stream);
 
+/* msk_solve_magnus for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this is a property of the library, not of the method.
+ * Callers whose device memory belongs to another allocator (a framework's
+ * caching allocator, a fixed budget) or who must not hit cudaMalloc/cudaFree
+ * (which synchronise the device) inside a latency-bound loop get the same
+ * solve with its scratch (functionals, weights, per-cell table) taken from one
+ * file-scope __device__ array of 2^21 doubles (16 MiB) that every GPU loading
+ * the library holds until exit.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.  Requests needing more than the array
+ * (paths * steps * (MSK_NF + MSK_NWT) doubles, plus 3 (n_fine + 1) for
+ * MSK_COEF_TRIG) fail with MSK_ERR_ARG before any device work.  The first call
+ * on a device looks up the array's address (once per device); make it before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents (nothing in it needs to start at zero); calls whose work overlaps
+ * on the GPU race on it and must be serialised by the caller.  Arguments and
+ * outputs as for msk_solve_magnus. */
+msk_status msk_solve_magnus_noalloc(msk_ctx* ctx, int order, int steps, int64_t paths,
+                                    int precision, void* u_out_dev,
+                                    uint32_t* path_status_dev, void* stream);
+
 /* Work counter: number of whole-grid stencil applications (Taylor terms and
  * Euler steps, summed over paths) performed by the engine since the last
  * reset, read after synchronising `stream`.  reset != 0 zeroes it afterwards. */

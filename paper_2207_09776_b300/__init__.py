@@ -70,6 +70,7 @@ SIGNATURES = {
     "msk_solve_magnus": (_INT, [_P, _INT, _INT, _I64, _INT, _P, _P, _P]),
     "msk_solve_euler": (_INT, [_P, _INT, _I64, _INT, _P, _P, _P]),
     "msk_magnus_from_weights": (_INT, [_P, _INT, _I64, _INT, _P, _P, _P, _P]),
+    "msk_solve_magnus_noalloc": (_INT, [_P, _INT, _INT, _I64, _INT, _P, _P, _P]),
     "msk_work_counter": (_INT, [_P, ctypes.POINTER(ctypes.c_uint64), _INT, _P]),
     "msk_explicit_solution": (_INT, [_P, _I64, _P, _P]),
     "msk_error": (_INT, [_P, _P, _INT, _I64, _INT, _P, _INT, _INT, _P, _P, _P]),
@@ -204,6 +205,14 @@ def msk_solve_magnus(ctx, order, steps, paths, precision, u_out, status=None, st
     _need(u_out, 1, _dtype(precision), "u_out")
     _check(load_library().msk_solve_magnus(ctx, order, steps, paths, precision, _ptr(u_out), _ptr(status),
                                            _stream(stream)), ctx)
+
+
+def msk_solve_magnus_noalloc(ctx, order, steps, paths, precision, u_out, status=None, stream=None):
+    """msk_solve_magnus without device allocation: scratch comes from the library's
+    16 MiB static device array (see include/msk.h for the limits and sharing rules)."""
+    _need(u_out, 1, _dtype(precision), "u_out")
+    _check(load_library().msk_solve_magnus_noalloc(ctx, order, steps, paths, precision, _ptr(u_out), _ptr(status),
+                                                   _stream(stream)), ctx)
 
 
 def msk_magnus_from_weights(ctx, steps, paths, precision, Wt, u_out, status=None, stream=None):

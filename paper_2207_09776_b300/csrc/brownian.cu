@@ -210,3 +210,24 @@ msk_status launch_brownian(msk_ctx* ctx, int steps, int64_t paths, double* out, 
   else brownian_kernel<true, false><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
   return msk_cuda(ctx, cudaGetLastError(), "brownian kernel");
 }
+
+// Variants for callers that supply the per-cell table buffer themselves
+// (3 * (n_fine + 1) doubles); used by the entry point that allocates nothing.
+msk_status launch_cell_table_into(msk_ctx* ctx, double* tab, cudaStream_t stream) {
+  const int64_t n = ctx->n_fine + 1;
+  cell_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(coef_dev(ctx->coef), ctx->n_fine, ctx->T, tab);
+  return msk_cuda(ctx, cudaGetLastError(), "cell table");
+}
+
+msk_status launch_brownian_with_table(msk_ctx* ctx, int steps, int64_t paths, double* out, const double* tab,
+                                      cudaStream_t stream) {
+  const int64_t n = paths * steps;
+  if (n == 0) return MSK_OK;
+  const bool trig = ctx->coef.kind == MSK_COEF_TRIG;
+  BrownArgs a{ctx->seed, ctx->path_offset, ctx->n_fine, paths, steps, ctx->T, coef_dev(ctx->coef),
+              trig ? tab : nullptr};
+  const unsigned blocks = (unsigned)((n + kWarps - 1) / kWarps);
+  if (trig) brownian_kernel<true, true><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
+  else brownian_kernel<true, false><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
+  return msk_cuda(ctx, cudaGetLastError(), "brownian kernel");
+}
