@@ -55,6 +55,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-comparators", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=0, help="paths in the CPU-oracle sample (0 = auto)")
+    p.add_argument("--workload", default="trig128", choices=("trig128", "batch"),
+                   help="trig128: the time-dependent 128^2 workload (default); batch: grids 64/128/256 "
+                        "in ratio 4:2:1 of 16384 paths in one persistent launch")
     p.add_argument("--profile-case", type=int, default=0, metavar="PATHS",
                    help="run two plain solves of the benchmark workload with PATHS paths at K = 8 "
                         "(a small case for ncu captures) and exit")
@@ -415,6 +418,98 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(a):
+    """Uneven batch: one persistent launch (CUDA graph) over 64^2, 128^2 and 256^2 paths."""
+    import torch
+
+    import paper_2207_09776_b300 as msk
+    from paper_2207_09776_b300 import build as mbuild
+    from workloads import BATCH_GRIDS
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    mbuild.build()
+    msk.load_library()
+    K, order = 16, 3
+    ws = [g.with_(path_offset=rank * g.paths) for g in BATCH_GRIDS]
+    solvers = [msk.Solver(w, device=local) for w in ws]
+    outs = [s.state(w.paths, msk.MSK_F32) for s, w in zip(solvers, ws)]
+    sts = [torch.zeros(w.paths, dtype=torch.int32, device="cuda") for w in ws]
+    items = [(s.ctx, order, K, w.paths, o, st) for s, w, o, st in zip(solvers, ws, outs, sts)]
+    b = msk.msk_batch_create(items)
+    variant, tune_ms = msk.msk_batch_tune(b)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(a.warmup, 0)):
+        msk.msk_batch_run(b, stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for s in solvers:
+        msk.msk_work_counter(s.ctx, reset=True, stream=stream)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        msk.msk_batch_run(b, stream)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    matvec_pts = sum(msk.msk_work_counter(s.ctx, stream=stream) * w.d * w.d for s, w in zip(solvers, ws)) / a.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total = sum(w.paths for w in ws)
+    # per-grid launches one after another, for comparison
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for s, w, o in zip(solvers, ws, outs):
+        msk.msk_solve_magnus(s.ctx, order, K, w.paths, msk.MSK_F32, o, None, stream)
+    t0.record(stream)
+    for s, w, o in zip(solvers, ws, outs):
+        msk.msk_solve_magnus(s.ctx, order, K, w.paths, msk.MSK_F32, o, None, stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = t0.elapsed_time(t1)
+    msk.msk_batch_run(b, stream)
+    torch.cuda.synchronize()
+    errs = {}
+    for s, w, o in zip(solvers, ws, outs):
+        e, m = s.error(o[:64].contiguous(), msk.MSK_F32)
+        errs[f"d{w.d}"] = float(m.cpu()[0])
+    peaks, peak_src = measured_peaks()
+    fp32_peak = 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    achieved = matvec_pts * FLOPS_PER_POINT / (ms / 1e3) / 1e12
+    line = {"metric": METRIC, "value": world * total / (ms / 1e3), "unit": "paths/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch_64_128_256", "grids": [w.d for w in ws],
+                       "paths_per_gpu": [w.paths for w in ws], "order": order, "magnus_steps": K,
+                       "n_fine": ws[0].n_fine, "variant": variant, "tune_ms": tune_ms,
+                       "err_vs_closed_form_64_paths": errs,
+                       "parallelism": f"replicas x{world} (path ranges)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "traffic": None, "kernel": "batch_kernel (whole step)"},
+            "clocks": clk, "gpu_launches": 2 * len(ws) + 2,
+            "comparators": {"per_grid_launches_ms": seq_ms,
+                            "per_grid_paths_per_s": total / (seq_ms / 1e3)}}
+    msk.msk_batch_destroy(b)
+    for s in solvers:
+        s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_profile_case(a):
     """Two solves (functionals, weights, engine) of the workload on a small path count."""
     import torch
@@ -445,6 +540,8 @@ def main():
         return
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch":
+        run_batch(a)
     else:
         run_ours(a)
 

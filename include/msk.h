@@ -211,6 +211,50 @@ msk_status msk_solve_magnus_noalloc(msk_ctx* ctx, int order, int steps, int64_t 
  * reset, read after synchronising `stream`.  reset != 0 zeroes it afterwards. */
 msk_status msk_work_counter(msk_ctx* ctx, uint64_t* matvecs_host, int reset, void* stream);
 
+/* S10: uneven batches in one persistent launch.  An item is one context (grid
+ * 64, 128 or 256; its coefficients, initial datum and seed as set at
+ * msk_batch_create, which snapshots them) with its own order, step count and
+ * path count; the outputs are float [paths][d][d] (float stencil/Taylor
+ * arithmetic, double functionals, weights and Taylor parameters).  All items
+ * must live on one device. */
+typedef struct {
+  msk_ctx* ctx;
+  int32_t order;
+  int32_t steps;
+  int64_t paths;
+  float* u_out_dev;        /* caller-owned [paths][d][d] */
+  uint32_t* status_dev;    /* optional [paths] of MSK_PATH_* bits */
+} msk_batch_item;
+
+typedef struct msk_batch msk_batch;
+
+/* Build a batch: library-owned scratch for every item, the work-unit queue of
+ * the persistent kernel (one 256^2 path per 4-CTA cluster, four 128^2 paths,
+ * or four/eight 64^2 paths per cluster), and the variant cached under
+ * `tune_cache` for this device and batch shape (NULL or "": default variant). */
+msk_status msk_batch_create(msk_batch** out, const msk_batch_item* items, int n_items,
+                            const char* tune_cache);
+
+/* Run the batch on `stream`: per-item Brownian functionals and weights, then one
+ * persistent launch of the megakernel over all items' paths.  The first run
+ * captures these launches into a CUDA graph (on a private stream of the batch);
+ * every run launches that graph on `stream`. */
+msk_status msk_batch_run(msk_batch* b, void* stream);
+
+/* Autotune: time every variant (queue order x 64^2 packing) on this batch,
+ * keep the fastest, append it to `tune_cache` (if given), report the chosen
+ * variant and the four times in milliseconds (ms_out[4], nullable). */
+msk_status msk_batch_tune(msk_batch* b, void* stream, const char* tune_cache, int* variant_out,
+                          float* ms_out);
+
+/* Current variant of the batch (bit 0: interleaved queue, bit 1: one 64^2 path per
+ * CTA), and setting it explicitly (0..3; the next run re-captures the graph). */
+int msk_batch_variant(const msk_batch* b);
+msk_status msk_batch_set_variant(msk_batch* b, int variant);
+
+const char* msk_batch_last_error(const msk_batch* b);
+void msk_batch_destroy(msk_batch* b);
+
 /* S7: Euler-Maruyama (Eq. EulerMaruyama) with `steps` equal steps, a(t),
  * sigma(t) at the left end of each step, dW the sum of the fine increments. */
 msk_status msk_solve_euler(msk_ctx* ctx, int steps, int64_t paths, int precision,

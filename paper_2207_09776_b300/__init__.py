@@ -47,6 +47,11 @@ class msk_gaussian(ctypes.Structure):
                 ("cov_xv", ctypes.c_double), ("cov_vv", ctypes.c_double), ("scale", ctypes.c_double)]
 
 
+class msk_batch_item(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("order", ctypes.c_int32), ("steps", ctypes.c_int32),
+                ("paths", ctypes.c_int64), ("u_out_dev", ctypes.c_void_p), ("status_dev", ctypes.c_void_p)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _U64 = ctypes.c_uint64
@@ -72,6 +77,13 @@ SIGNATURES = {
     "msk_magnus_from_weights": (_INT, [_P, _INT, _I64, _INT, _P, _P, _P, _P]),
     "msk_solve_magnus_noalloc": (_INT, [_P, _INT, _INT, _I64, _INT, _P, _P, _P]),
     "msk_work_counter": (_INT, [_P, ctypes.POINTER(ctypes.c_uint64), _INT, _P]),
+    "msk_batch_create": (_INT, [ctypes.POINTER(_P), ctypes.POINTER(msk_batch_item), _INT, ctypes.c_char_p]),
+    "msk_batch_run": (_INT, [_P, _P]),
+    "msk_batch_tune": (_INT, [_P, _P, ctypes.c_char_p, ctypes.POINTER(_INT), ctypes.POINTER(ctypes.c_float)]),
+    "msk_batch_variant": (_INT, [_P]),
+    "msk_batch_set_variant": (_INT, [_P, _INT]),
+    "msk_batch_last_error": (ctypes.c_char_p, [_P]),
+    "msk_batch_destroy": (None, [_P]),
     "msk_explicit_solution": (_INT, [_P, _I64, _P, _P]),
     "msk_error": (_INT, [_P, _P, _INT, _I64, _INT, _P, _INT, _INT, _P, _P, _P]),
     "msk_moments": (_INT, [_P, _P, _INT, _I64, _P, _P]),
@@ -249,6 +261,54 @@ def msk_error(ctx, u, u_precision, paths, ref_kind, ref, ref_precision, kappa, e
 
 def msk_moments(ctx, u, precision, paths, mom, stream=None):
     _check(load_library().msk_moments(ctx, _ptr(u), precision, paths, _ptr(mom), _stream(stream)), ctx)
+
+
+def msk_batch_create(items, tune_cache=None):
+    """items: sequence of (ctx, order, steps, paths, u_out float tensor, status int32 tensor or None)."""
+    arr = (msk_batch_item * len(items))()
+    for k, (ctx, order, steps, paths, out, st) in enumerate(items):
+        arr[k] = msk_batch_item(ctx.value if hasattr(ctx, "value") else ctx, order, steps, paths,
+                                _ptr(out), _ptr(st))
+    h = _P()
+    rc = load_library().msk_batch_create(ctypes.byref(h), arr, len(items),
+                                         tune_cache.encode() if tune_cache else None)
+    if rc != MSK_OK:
+        raise MskError(rc, "batch creation failed")
+    return h
+
+
+def msk_batch_run(b, stream=None):
+    rc = load_library().msk_batch_run(b, _stream(stream))
+    if rc != MSK_OK:
+        raise MskError(rc, load_library().msk_batch_last_error(b).decode())
+
+
+def msk_batch_tune(b, tune_cache=None, stream=None):
+    v = _INT(0)
+    ms = (ctypes.c_float * 4)()
+    rc = load_library().msk_batch_tune(b, _stream(stream), tune_cache.encode() if tune_cache else None,
+                                       ctypes.byref(v), ms)
+    if rc != MSK_OK:
+        raise MskError(rc, load_library().msk_batch_last_error(b).decode())
+    return v.value, list(ms)
+
+
+def msk_batch_variant(b) -> int:
+    return load_library().msk_batch_variant(b)
+
+
+def msk_batch_set_variant(b, variant):
+    rc = load_library().msk_batch_set_variant(b, variant)
+    if rc != MSK_OK:
+        raise MskError(rc, load_library().msk_batch_last_error(b).decode())
+
+
+def msk_batch_last_error(b) -> str:
+    return load_library().msk_batch_last_error(b).decode()
+
+
+def msk_batch_destroy(b):
+    load_library().msk_batch_destroy(b)
 
 
 # ---- convenience ---------------------------------------------------------------------

@@ -1,0 +1,431 @@
+// S10: uneven batches (grids 64^2, 128^2, 256^2, any path counts) in one
+// persistent launch, captured with the batch's Brownian and weight kernels in
+// a CUDA graph, with the work layout chosen by a small autotuner.
+//
+// The megakernel runs thread-block clusters of four 512-thread CTAs, one CTA
+// per SM.  Each cluster repeatedly takes the next work unit from a queue (one
+// atomic counter) and runs it with the engine's per-path solver
+// (engine_core.cuh):
+//   D256   one 256^2 path, split into four 64-row slabs (the cluster's CTAs)
+//   D128   up to four 128^2 paths, one per CTA
+//   D64x2  up to eight 64^2 paths, two per CTA (two 256-thread halves, each
+//          synchronised by its own named barrier)
+//   D64x1  up to four 64^2 paths, one per CTA (512 threads, two rows each)
+// Every unit keeps one SM busy per CTA for about the same number of grid
+// points (16384), so units differ in length only by their Taylor work, which
+// grows with the grid (the operator norm scales like 1/Delta^2).
+//
+// Tuned choices (the "variant"): bit 0 orders the queue by decreasing unit
+// length (largest grids first) or interleaves the items; bit 1 packs 64^2
+// paths two per CTA or one per CTA.  msk_batch_tune times all four on the
+// batch itself and keeps the fastest; the result can be cached in a text file
+// keyed by device name and batch shape.
+#include <stdio.h>
+
+#include <new>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "engine_core.cuh"
+
+extern const double kMskScaleCap;
+msk_status msk_prepare_brownian(msk_ctx* ctx, cudaStream_t stream);
+msk_status msk_prepare_omega(msk_ctx* ctx);
+
+namespace {
+
+enum { UNIT_D256 = 0, UNIT_D128 = 1, UNIT_D64X2 = 2, UNIT_D64X1 = 3 };
+
+struct BatchUnit {
+  int32_t type, item;
+  int64_t first;
+  int32_t count, pad;
+};
+
+constexpr int kNT = 512;
+using K256 = Cfg<float, 256, 4, kNT>;
+using K128 = Cfg<float, 128, 1, kNT>;
+using K64h = Cfg<float, 64, 1, kNT / 2>;
+using K64 = Cfg<float, 64, 1, kNT>;
+constexpr size_t kHalf64 = (K64h::SMEM + 255) / 256 * 256;   // byte offset of the second half-slab
+constexpr size_t kSlabBytes = std::max(std::max(K256::SMEM, K128::SMEM), std::max(2 * kHalf64, K64::SMEM));
+constexpr size_t kBatchSmem = kSlabBytes + 16;                 // + the unit index slot
+static_assert(kBatchSmem <= 232448, "batch slab does not fit shared memory");
+
+__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kNT, 1)
+    batch_kernel(const EngineArgs* __restrict__ items, const BatchUnit* __restrict__ units, int n_units,
+                 unsigned int* __restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  int* s_unit = reinterpret_cast<int*>(smem_raw + kSlabBytes);
+  const int tid = threadIdx.x;
+  const int rank = (int)cg::this_cluster().block_rank();
+  const ClusterSync csync;
+  for (;;) {
+    // The previous unit is finished by every CTA once all have reached this
+    // barrier; rank 0 then publishes the next unit index in its shared memory.
+    if (rank == 0 && tid == 0) *s_unit = (int)atomicAdd(counter, 1u);
+    csync();
+    const int u = *cg::this_cluster().map_shared_rank(s_unit, 0);
+    // Every CTA has read the index before rank 0 may overwrite it or exit
+    // (a CTA's shared memory must not be read through DSMEM after it exits).
+    csync();
+    if (u >= n_units) break;                        // same value in every thread of the cluster
+    const BatchUnit un = units[u];
+    const EngineArgs a = items[un.item];
+    switch (un.type) {
+      case UNIT_D256:
+        slab_init<float, 256, 4, kNT>(sm, tid, rank, csync);
+        solve_path<float, 256, 4, kNT, false>(a, un.first, sm, tid, rank, csync);
+        break;
+      case UNIT_D128: {
+        const CtaSync s;
+        slab_init<float, 128, 1, kNT>(sm, tid, 0, s);
+        if (rank < un.count) solve_path<float, 128, 1, kNT, false>(a, un.first + rank, sm, tid, 0, s);
+        break;
+      }
+      case UNIT_D64X2: {
+        const int g = tid / (kNT / 2), t = tid % (kNT / 2);
+        const NamedSync s{1 + g, kNT / 2};
+        float* half = reinterpret_cast<float*>(smem_raw + g * kHalf64);
+        slab_init<float, 64, 1, kNT / 2>(half, t, 0, s);
+        const int idx = 2 * rank + g;
+        if (idx < un.count) solve_path<float, 64, 1, kNT / 2, false>(a, un.first + idx, half, t, 0, s);
+        break;
+      }
+      default: {
+        const CtaSync s;
+        slab_init<float, 64, 1, kNT>(sm, tid, 0, s);
+        if (rank < un.count) solve_path<float, 64, 1, kNT, false>(a, un.first + rank, sm, tid, 0, s);
+        break;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+struct msk_batch {
+  int device = 0;
+  std::vector<msk_batch_item> items;
+  std::vector<EngineArgs> args;
+  std::vector<size_t> f_off, w_off;
+  double* scratch = nullptr;
+  EngineArgs* d_args = nullptr;
+  BatchUnit* d_units = nullptr;
+  unsigned int* d_counter = nullptr;
+  int n_units = 0, units_cap = 0;
+  int variant = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap_stream = nullptr;   // private stream the graph is captured on
+  std::string key;
+  std::string err;
+};
+
+namespace {
+
+msk_status bfail(msk_batch* b, msk_status st, const std::string& m) {
+  if (b) b->err = m;
+  return st;
+}
+msk_status bcuda(msk_batch* b, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MSK_OK;
+  cudaGetLastError();
+  return bfail(b, e == cudaErrorMemoryAllocation ? MSK_ERR_OOM : MSK_ERR_CUDA,
+               std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+std::vector<BatchUnit> build_units(const msk_batch* b, int variant) {
+  const bool interleave = variant & 1, one64 = variant & 2;
+  std::vector<std::vector<BatchUnit>> per(b->items.size());
+  for (size_t k = 0; k < b->items.size(); ++k) {
+    const msk_batch_item& it = b->items[k];
+    const int d = it.ctx->d;
+    const int type = d == 256 ? UNIT_D256 : d == 128 ? UNIT_D128 : one64 ? UNIT_D64X1 : UNIT_D64X2;
+    const int per_unit = type == UNIT_D256 ? 1 : type == UNIT_D64X2 ? 8 : 4;
+    for (int64_t p = 0; p < it.paths; p += per_unit)
+      per[k].push_back({type, (int32_t)k, p, (int32_t)std::min<int64_t>(per_unit, it.paths - p), 0});
+  }
+  std::vector<BatchUnit> out;
+  if (interleave) {
+    for (size_t r = 0;; ++r) {
+      bool any = false;
+      for (auto& v : per)
+        if (r < v.size()) {
+          out.push_back(v[r]);
+          any = true;
+        }
+      if (!any) break;
+    }
+  } else {
+    for (auto& v : per) out.insert(out.end(), v.begin(), v.end());
+    // longest units first: larger grids carry more Taylor work per grid point
+    std::stable_sort(out.begin(), out.end(), [&](const BatchUnit& x, const BatchUnit& y) {
+      return b->items[x.item].ctx->d > b->items[y.item].ctx->d;
+    });
+  }
+  return out;
+}
+
+void drop_graph(msk_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+msk_status set_variant(msk_batch* b, int variant) {
+  const std::vector<BatchUnit> units = build_units(b, variant);
+  if ((int)units.size() > b->units_cap) {
+    if (b->d_units) cudaFree(b->d_units);
+    b->d_units = nullptr;
+    msk_status st = bcuda(b, cudaMalloc(&b->d_units, std::max<size_t>(1, units.size()) * sizeof(BatchUnit)),
+                          "unit list allocation");
+    if (st != MSK_OK) return st;
+    b->units_cap = (int)units.size();
+  }
+  if (!units.empty()) {
+    msk_status st = bcuda(b, cudaMemcpy(b->d_units, units.data(), units.size() * sizeof(BatchUnit),
+                                        cudaMemcpyHostToDevice), "unit list upload");
+    if (st != MSK_OK) return st;
+  }
+  b->n_units = (int)units.size();
+  b->variant = variant;
+  drop_graph(b);
+  return MSK_OK;
+}
+
+// Enqueue the whole batch on `s`: counter reset, per-item Brownian functionals
+// and weights, then the persistent megakernel.
+msk_status enqueue(msk_batch* b, cudaStream_t s) {
+  msk_status st = bcuda(b, cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), s), "counter reset");
+  for (size_t k = 0; k < b->items.size() && st == MSK_OK; ++k) {
+    const msk_batch_item& it = b->items[k];
+    if (it.paths == 0) continue;
+    double* F = b->scratch + b->f_off[k];
+    double* Wt = b->scratch + b->w_off[k];
+    st = launch_brownian(it.ctx, it.steps, it.paths, F, false, s);
+    if (st == MSK_OK) st = launch_omega(it.ctx, it.order, it.steps, it.paths, MSK_F32, F, Wt, s);
+    if (st != MSK_OK) b->err = it.ctx->err;
+  }
+  if (st != MSK_OK || b->n_units == 0) return st;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(148 * 4, 1, 1);
+  cfg.blockDim = dim3(kNT, 1, 1);
+  cfg.dynamicSmemBytes = kBatchSmem;
+  cfg.stream = s;
+  int nc = 0;
+  st = bcuda(b, cudaOccupancyMaxActiveClusters(&nc, batch_kernel, &cfg), "occupancy clusters");
+  if (st != MSK_OK) return st;
+  if (nc < 1) return bfail(b, MSK_ERR_UNSUPPORTED, "batch cluster configuration cannot be scheduled");
+  cfg.gridDim = dim3((unsigned)(std::min(nc, b->n_units) * 4), 1, 1);
+  return bcuda(b, cudaLaunchKernelEx(&cfg, batch_kernel, (const EngineArgs*)b->d_args,
+                                     (const BatchUnit*)b->d_units, b->n_units, b->d_counter),
+               "batch launch");
+}
+
+msk_status capture(msk_batch* b, cudaStream_t s) {
+  drop_graph(b);
+  msk_status st = bcuda(b, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+  if (st != MSK_OK) return st;
+  msk_status est = enqueue(b, s);
+  cudaGraph_t g = nullptr;
+  st = bcuda(b, cudaStreamEndCapture(s, &g), "end capture");
+  if (est != MSK_OK) {
+    if (g) cudaGraphDestroy(g);
+    return est;
+  }
+  if (st != MSK_OK) return st;
+  b->graph = g;
+  return bcuda(b, cudaGraphInstantiate(&b->exec, g, 0), "graph instantiate");
+}
+
+std::string batch_key(const msk_batch* b) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, b->device);
+  std::string k = prop.name;
+  for (const auto& it : b->items)
+    k += "|" + std::to_string(it.ctx->d) + "x" + std::to_string(it.paths) + "o" + std::to_string(it.order) + "k" +
+         std::to_string(it.steps);
+  for (auto& ch : k)
+    if (ch == ' ') ch = '_';
+  return k;
+}
+
+int cached_variant(const char* path, const std::string& key) {
+  if (!path || !*path) return -1;
+  FILE* f = fopen(path, "r");
+  if (!f) return -1;
+  char line[4096];
+  int v = -1;
+  while (fgets(line, sizeof line, f)) {
+    std::string l(line);
+    const size_t sp = l.rfind(' ');
+    if (sp != std::string::npos && l.substr(0, sp) == key) v = atoi(l.c_str() + sp + 1);
+  }
+  fclose(f);
+  return v;
+}
+
+}  // namespace
+
+extern "C" msk_status msk_batch_create(msk_batch** out, const msk_batch_item* items, int n_items,
+                                       const char* tune_cache) {
+  if (!out) return MSK_ERR_ARG;
+  *out = nullptr;
+  if (!items || n_items < 1) return MSK_ERR_ARG;
+  const int dev = items[0].ctx ? items[0].ctx->device : -1;
+  for (int k = 0; k < n_items; ++k) {
+    const msk_batch_item& it = items[k];
+    if (!it.ctx || it.ctx->device != dev) return MSK_ERR_ARG;
+    const int d = it.ctx->d;
+    if (d != 64 && d != 128 && d != 256) return MSK_ERR_UNSUPPORTED;
+    if (it.order < 1 || it.order > 3 || it.steps < 1 || it.ctx->n_fine % it.steps != 0 || it.paths < 0)
+      return MSK_ERR_ARG;
+    if (it.paths > 0 && !it.u_out_dev) return MSK_ERR_ARG;
+  }
+  msk_batch* b = new (std::nothrow) msk_batch();
+  if (!b) return MSK_ERR_OOM;
+  b->device = dev;
+  b->items.assign(items, items + n_items);
+  msk_status st = bcuda(b, cudaSetDevice(dev), "set device");
+  size_t total = 0;
+  for (int k = 0; k < n_items; ++k) {
+    b->f_off.push_back(total);
+    total += (size_t)items[k].paths * items[k].steps * MSK_NF;
+    b->w_off.push_back(total);
+    total += (size_t)items[k].paths * items[k].steps * MSK_NWT;
+  }
+  if (st == MSK_OK) st = bcuda(b, cudaMalloc(&b->scratch, std::max<size_t>(total, 1) * sizeof(double)), "scratch");
+  if (st == MSK_OK) st = bcuda(b, cudaMalloc(&b->d_counter, sizeof(unsigned int)), "counter");
+  if (st == MSK_OK) st = bcuda(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "capture stream");
+  if (st == MSK_OK) st = bcuda(b, cudaMalloc(&b->d_args, n_items * sizeof(EngineArgs)), "item table");
+  for (int k = 0; k < n_items && st == MSK_OK; ++k) {
+    const msk_batch_item& it = items[k];
+    msk_ctx* c = it.ctx;
+    EngineArgs a{};
+    a.band = c->band;
+    a.u0 = c->u0;
+    a.Wt = b->scratch + b->w_off[k];
+    a.dW = nullptr;
+    a.out = it.u_out_dev;
+    a.status = it.status_dev;
+    a.work = c->work;
+    a.paths = it.paths;
+    a.steps = it.steps;
+    a.dx = c->dx;
+    a.T = c->T;
+    a.s_cap = kMskScaleCap;
+    a.tol32 = 0x1p-24f;
+    a.tol64 = 0x1p-53;
+    a.c = coef_dev(c->coef);
+    b->args.push_back(a);
+    st = msk_prepare_brownian(c, 0);
+    if (st == MSK_OK) st = msk_prepare_omega(c);
+    if (st != MSK_OK) b->err = c->err;
+  }
+  if (st == MSK_OK)
+    st = bcuda(b, cudaMemcpy(b->d_args, b->args.data(), n_items * sizeof(EngineArgs), cudaMemcpyHostToDevice),
+               "item table upload");
+  if (st == MSK_OK)
+    st = bcuda(b, cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem),
+               "smem attribute");
+  if (st == MSK_OK) st = bcuda(b, cudaDeviceSynchronize(), "prepare");
+  if (st == MSK_OK) {
+    b->key = batch_key(b);
+    const int v = cached_variant(tune_cache, b->key);
+    st = set_variant(b, v >= 0 && v < 4 ? v : 0);
+  }
+  if (st != MSK_OK) {
+    msk_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return MSK_OK;
+}
+
+extern "C" void msk_batch_destroy(msk_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  drop_graph(b);
+  if (b->scratch) cudaFree(b->scratch);
+  if (b->d_args) cudaFree(b->d_args);
+  if (b->d_units) cudaFree(b->d_units);
+  if (b->d_counter) cudaFree(b->d_counter);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+extern "C" const char* msk_batch_last_error(const msk_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+extern "C" msk_status msk_batch_run(msk_batch* b, void* stream) {
+  if (!b) return MSK_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  msk_status st = bcuda(b, cudaSetDevice(b->device), "set device");
+  if (st != MSK_OK) return st;
+  if (!b->exec) {
+    // capture on the batch's own stream (capture is not possible on the legacy
+    // default stream); the instantiated graph then runs on the caller's stream
+    st = capture(b, b->cap_stream);
+    if (st != MSK_OK) return st;
+  }
+  return bcuda(b, cudaGraphLaunch(b->exec, s), "graph launch");
+}
+
+extern "C" msk_status msk_batch_tune(msk_batch* b, void* stream, const char* tune_cache, int* variant_out,
+                                     float* ms_out) {
+  if (!b) return MSK_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  msk_status st = bcuda(b, cudaSetDevice(b->device), "set device");
+  if (st != MSK_OK) return st;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f, times[4] = {0, 0, 0, 0};
+  int best_v = 0;
+  for (int v = 0; v < 4 && st == MSK_OK; ++v) {
+    st = set_variant(b, v);
+    if (st == MSK_OK) st = msk_batch_run(b, stream);            // capture + warm-up
+    if (st != MSK_OK) break;
+    cudaEventRecord(e0, s);
+    st = msk_batch_run(b, stream);
+    cudaEventRecord(e1, s);
+    if (st == MSK_OK) st = bcuda(b, cudaEventSynchronize(e1), "tune sync");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    times[v] = ms;
+    if (ms < best) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != MSK_OK) return st;
+  st = set_variant(b, best_v);
+  if (st != MSK_OK) return st;
+  if (variant_out) *variant_out = best_v;
+  if (ms_out)
+    for (int v = 0; v < 4; ++v) ms_out[v] = times[v];
+  if (tune_cache && *tune_cache) {
+    FILE* f = fopen(tune_cache, "a");
+    if (f) {
+      fprintf(f, "%s %d\n", b->key.c_str(), best_v);
+      fclose(f);
+    }
+  }
+  return MSK_OK;
+}
+
+extern "C" int msk_batch_variant(const msk_batch* b) { return b ? b->variant : -1; }
+
+extern "C" msk_status msk_batch_set_variant(msk_batch* b, int variant) {
+  if (!b) return MSK_ERR_ARG;
+  if (variant < 0 || variant > 3) return bfail(b, MSK_ERR_ARG, "variant must be 0..3");
+  msk_status st = bcuda(b, cudaSetDevice(b->device), "set device");
+  if (st != MSK_OK) return st;
+  return set_variant(b, variant);
+}

@@ -231,3 +231,10 @@ msk_status launch_brownian_with_table(msk_ctx* ctx, int steps, int64_t paths, do
   else brownian_kernel<true, false><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
   return msk_cuda(ctx, cudaGetLastError(), "brownian kernel");
 }
+
+// Allocate/refresh the per-cell coefficient table now (so that a later
+// launch_brownian performs no allocation, e.g. inside a stream capture).
+msk_status msk_prepare_brownian(msk_ctx* ctx, cudaStream_t stream) {
+  if (ctx->coef.kind != MSK_COEF_TRIG) return MSK_OK;
+  return ensure_cell_table(ctx, stream);
+}

@@ -171,8 +171,8 @@ bool g_theta_loaded[64] = {false};
 // Taylor scaling cap: beyond it the path is flagged MSK_PATH_SCALE_CAP.
 extern const double kMskScaleCap = 16384.0;
 
-msk_status launch_omega(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
-                        const double* F, double* Wt, cudaStream_t stream) {
+// Upload the theta tables to this device's constant memory (once per device).
+msk_status msk_prepare_omega(msk_ctx* ctx) {
   if (ctx->device >= 0 && ctx->device < 64 && !g_theta_loaded[ctx->device]) {
     msk_status st = msk_cuda(ctx, cudaMemcpyToSymbol(c_theta64, msk_theta_f64, sizeof(msk_theta_f64)),
                              "theta64");
@@ -181,6 +181,13 @@ msk_status launch_omega(msk_ctx* ctx, int order, int steps, int64_t paths, int p
     if (st != MSK_OK) return st;
     g_theta_loaded[ctx->device] = true;
   }
+  return MSK_OK;
+}
+
+msk_status launch_omega(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
+                        const double* F, double* Wt, cudaStream_t stream) {
+  msk_status st0 = msk_prepare_omega(ctx);
+  if (st0 != MSK_OK) return st0;
   const int64_t n = paths * steps;
   if (n == 0) return MSK_OK;
   OmegaArgs a{ctx->band, ctx->aux, ctx->d, order, steps, precision, paths, ctx->T, ctx->dx,

@@ -1,0 +1,115 @@
+"""Uneven batches in one persistent launch (grids 64^2, 128^2, 256^2)."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import paper_2207_09776_b300 as msk  # noqa: E402
+from oracle import magnus as omagnus  # noqa: E402
+from workloads import BATCH_GRIDS, LANGEVIN_32  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2207_09776_b300 import build
+    build.build()
+    msk.load_library()
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64).reshape(len(b), -1)
+    b = np.asarray(b, dtype=np.float64).reshape(len(b), -1)
+    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+
+
+def _items(paths=(21, 7, 3), T=0.25, K=4, order=3):
+    ws = [g.with_(paths=p, T=T, n_fine=256) for g, p in zip(BATCH_GRIDS, paths)]
+    solvers = [msk.Solver(w) for w in ws]
+    outs = [s.state(max(w.paths, 1), msk.MSK_F32) for s, w in zip(solvers, ws)]
+    sts = [torch.full((max(w.paths, 1),), 9, dtype=torch.int32, device="cuda") for w in ws]
+    items = [(s.ctx, order, K, w.paths, o, st) for s, w, o, st in zip(solvers, ws, outs, sts)]
+    return ws, solvers, outs, sts, items
+
+
+def test_batch_matches_per_grid_solves_and_the_oracle(tmp_path):
+    ws, solvers, outs, sts, items = _items()
+    b = msk.msk_batch_create(items)
+    for _ in range(2):                                  # capture, then graph replay
+        for o in outs:
+            o.fill_(float("nan"))
+        msk.msk_batch_run(b)
+        torch.cuda.synchronize()
+        for w, s, o, st in zip(ws, solvers, outs, sts):
+            ref = s.magnus(3, 4, precision=msk.MSK_F32)
+            assert rel_l2(o.cpu().numpy(), ref.cpu().numpy()).max() <= 1e-6
+            assert int(st[: w.paths].max()) == 0
+    # one path per grid against the CPU oracle
+    for w, o in zip(ws, outs):
+        ref = omagnus.solve(w, 3, 4, [w.paths - 1])
+        assert rel_l2(o[w.paths - 1:].cpu().numpy(), ref)[0] <= 1e-4
+    msk.msk_batch_destroy(b)
+    for s in solvers:
+        s.close()
+
+
+def test_autotuner_picks_and_caches_a_variant(tmp_path):
+    cache = str(tmp_path / "tune.txt")
+    ws, solvers, outs, sts, items = _items(paths=(17, 5, 2))
+    b = msk.msk_batch_create(items, cache)
+    v, times = msk.msk_batch_tune(b, cache)
+    assert 0 <= v < 4 and all(t > 0 for t in times) and times[v] == min(times)
+    assert msk.msk_batch_variant(b) == v
+    msk.msk_batch_run(b)
+    torch.cuda.synchronize()
+    for w, s, o in zip(ws, solvers, outs):
+        ref = s.magnus(3, 4, precision=msk.MSK_F32)
+        assert rel_l2(o.cpu().numpy(), ref.cpu().numpy()).max() <= 1e-6
+    msk.msk_batch_destroy(b)
+    assert os.path.exists(cache)
+    b2 = msk.msk_batch_create(items, cache)            # picks the cached variant
+    assert msk.msk_batch_variant(b2) == v
+    msk.msk_batch_destroy(b2)
+    for s in solvers:
+        s.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_every_variant_gives_the_same_answer(variant):
+    ws, solvers, outs, sts, items = _items(paths=(11, 6, 1))
+    b = msk.msk_batch_create(items)
+    msk.msk_batch_set_variant(b, variant)
+    assert msk.msk_batch_variant(b) == variant
+    msk.msk_batch_run(b)
+    torch.cuda.synchronize()
+    for w, s, o in zip(ws, solvers, outs):
+        ref = s.magnus(3, 4, precision=msk.MSK_F32)
+        assert rel_l2(o.cpu().numpy(), ref.cpu().numpy()).max() <= 1e-6
+    with pytest.raises(msk.MskError):
+        msk.msk_batch_set_variant(b, 4)
+    msk.msk_batch_destroy(b)
+    for s in solvers:
+        s.close()
+
+
+def test_batch_edge_cases():
+    ws, solvers, outs, sts, items = _items(paths=(0, 3, 0))
+    b = msk.msk_batch_create(items)
+    msk.msk_batch_run(b)
+    torch.cuda.synchronize()
+    ref = solvers[1].magnus(3, 4, precision=msk.MSK_F32)
+    assert rel_l2(outs[1].cpu().numpy(), ref.cpu().numpy()).max() <= 1e-6
+    msk.msk_batch_destroy(b)
+    s32 = msk.Solver(LANGEVIN_32.with_(paths=2))
+    out = s32.state(2, msk.MSK_F32)
+    with pytest.raises(msk.MskError) as e:
+        msk.msk_batch_create([(s32.ctx, 2, 1, 2, out, None)])          # 32^2 is not a batch grid
+    assert e.value.status == msk.MSK_ERR_UNSUPPORTED
+    with pytest.raises(msk.MskError):
+        msk.msk_batch_create([(solvers[0].ctx, 2, 3, 2, outs[0], None)])   # 3 does not divide 256
+    s32.close()
+    for s in solvers:
+        s.close()
