@@ -255,6 +255,124 @@ msk_status msk_batch_set_variant(msk_batch* b, int variant);
 const char* msk_batch_last_error(const msk_batch* b);
 void msk_batch_destroy(msk_batch* b);
 
+/* S11: learned surrogate of the Magnus solver (not part of the paper).
+ *
+ * For each path, features x = [dW_k / sqrt(h), int W ds_k / s3,
+ * int s dW_k / s3]_{k < K} (h = T/K, s3 = h^1.5/sqrt 3; the Ito integrals of
+ * the path's fine increments over each of K equal substeps, piecewise-linear
+ * W in each fine cell, single-precision normals from the same Philox words as
+ * the solver) are mapped by an MLP of `layers` GELU layers of width `hidden`
+ * (bf16 operands, fp32 accumulation) to r scaled POD coefficients c, and
+ * u_T = mean + coef_scale * c Phi.  The network is trained by the library's
+ * forward/backward kernels and Adam on Magnus solutions (order ref_order,
+ * ref_steps steps, float arithmetic) of the same paths.  Serving audits every
+ * audit_every-th path against the Magnus solver and falls back to it.
+ *
+ * Layouts: features uint16 (bfloat16 bits) [paths][3K]; coefficients float
+ * [paths][r]; solutions float [paths][v][x]; the flat parameter vector is
+ * float, per layer l = 0..layers: W_l [out][in] at offset W_l, then b_l [out]
+ * at offset b_l (msk_surrogate_param_layout; every block starts at a multiple
+ * of 8 elements).  A surrogate keeps a pointer to its context (which must
+ * outlive it) and reads the context's seed, path offset and n_fine at each
+ * call; one host thread at a time may use a surrogate. */
+typedef struct msk_surrogate msk_surrogate;
+
+typedef struct {
+  int32_t steps;         /* K feature substeps (divides n_fine); input width 3K <= 4096 */
+  int32_t rank;          /* r POD modes, 1..64 */
+  int32_t hidden;        /* hidden width, a multiple of 64 in 64..4096 */
+  int32_t layers;        /* hidden layers, 1..8 */
+  int32_t train_batch;   /* largest training minibatch (activation buffers) */
+  int32_t infer_batch;   /* paths per inference chunk */
+  int32_t ref_order;     /* Magnus order of the reference solutions, 1..3 */
+  int32_t ref_steps;     /* Magnus steps of the reference solutions (divides n_fine) */
+  uint64_t init_seed;    /* Philox key of the He-normal weight init (tag 4) and the POD sketch (tag 3) */
+} msk_surrogate_config;
+
+/* Create (weights He-normal N(0, 2/fan_in), biases and Adam state zero); on
+ * failure the message is in msk_last_error(ctx). */
+msk_status msk_surrogate_create(msk_surrogate** out, msk_ctx* ctx, const msk_surrogate_config* cfg);
+void msk_surrogate_destroy(msk_surrogate* s);
+const char* msk_surrogate_last_error(const msk_surrogate* s);
+
+/* Number of floats in the flat parameter vector (-1 for NULL), and the offsets
+ * of W_l and b_l: offsets_host[2 l], offsets_host[2 l + 1], l = 0..layers. */
+int64_t msk_surrogate_num_params(const msk_surrogate* s);
+msk_status msk_surrogate_param_layout(const msk_surrogate* s, int64_t* offsets_host);
+
+/* Copy the parameters out / in (set also refreshes the bf16 copy and resets Adam). */
+msk_status msk_surrogate_get_params(msk_surrogate* s, float* params_dev, void* stream);
+msk_status msk_surrogate_set_params(msk_surrogate* s, const float* params_dev, void* stream);
+
+/* Features of the context's paths path0 .. path0 + paths - 1 into X_dev. */
+msk_status msk_surrogate_features(msk_surrogate* s, int64_t path0, int64_t paths, uint16_t* X_dev,
+                                  void* stream);
+
+/* Reference solutions (Magnus, ref_order, ref_steps, float) of the same paths
+ * into U_dev [paths][d][d]. */
+msk_status msk_surrogate_reference(msk_surrogate* s, int64_t path0, int64_t paths, float* U_dev,
+                                   void* stream);
+
+/* POD of N snapshots S_dev [N][d][d]: mean and the leading r right singular
+ * vectors of S - mean by a randomized range finder (Gaussian sketch of
+ * min(r + 16, 80) columns, one power iteration, eigen-orthonormalisation,
+ * Rayleigh-Ritz), each mode signed so that its entry of largest magnitude is
+ * positive.  Directions with sigma <= 1e-6 sigma_1 (below the resolution of
+ * float snapshots) are not resolved: if fewer than r modes remain, the
+ * remaining rows of Phi are zero.  coef_scale = sqrt(sum_j sigma_j^2 / (N r))
+ * over the resolved modes.  sv_host (nullable) receives the min(r + 16, 80)
+ * singular-value estimates.  Synchronises `stream`.  MSK_ERR_ARG if the
+ * snapshots do not vary about their mean. */
+msk_status msk_surrogate_fit_pod(msk_surrogate* s, const float* S_dev, int64_t N, double* sv_host,
+                                 void* stream);
+
+/* Read / set the POD basis: mean [d*d], Phi [r][d*d] (orthonormal rows, or zero), coef_scale.
+ * Both synchronise `stream`.  get: any output may be NULL. */
+msk_status msk_surrogate_get_pod(msk_surrogate* s, float* mean_dev, float* phi_dev, double* scale_host,
+                                 void* stream);
+msk_status msk_surrogate_set_pod(msk_surrogate* s, const float* mean_dev, const float* phi_dev,
+                                 double coef_scale, void* stream);
+
+/* Scaled coefficients C = (S - mean) Phi^T / coef_scale [N][r] (synchronises),
+ * and the decode U = mean + coef_scale C Phi [N][d][d] (U_dev 16-byte aligned). */
+msk_status msk_surrogate_project(msk_surrogate* s, const float* S_dev, int64_t N, float* C_dev,
+                                 void* stream);
+msk_status msk_surrogate_decode(msk_surrogate* s, const float* C_dev, int64_t N, float* U_dev,
+                                void* stream);
+
+/* Network output for B feature rows (any B; chunks of infer_batch). */
+msk_status msk_surrogate_forward(msk_surrogate* s, const uint16_t* X_dev, int64_t B, float* C_dev,
+                                 void* stream);
+
+/* Loss L = (1/B) sum_b sum_j (out_bj - C_bj)^2 of B <= train_batch rows and
+ * its gradient (flat, like the parameters) into the surrogate's gradient
+ * buffer; loss_dev (float[1]) and grads_dev (float[num_params]) nullable copies. */
+msk_status msk_surrogate_loss_grads(msk_surrogate* s, const uint16_t* X_dev, const float* C_dev, int64_t B,
+                                    float* loss_dev, float* grads_dev, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with the
+ * gradient of the last msk_surrogate_loss_grads. */
+msk_status msk_surrogate_adam_step(msk_surrogate* s, float lr, void* stream);
+
+/* `epochs` passes over N rows in minibatches of train_batch (in order, the last
+ * one ragged), one Adam step each; loss_hist_dev (nullable) float[epochs * nb],
+ * nb = ceil(N / train_batch), receives each step's loss. */
+msk_status msk_surrogate_train(msk_surrogate* s, const uint16_t* X_dev, const float* C_dev, int64_t N,
+                               int epochs, float lr, float* loss_hist_dev, void* stream);
+
+/* Serve paths path0 .. path0 + paths - 1: features, network, decode into U_dev
+ * (16-byte aligned).  audit_every > 0: paths j * audit_every of each
+ * infer_batch chunk are re-solved by the reference Magnus solver; a path whose
+ * relative L2 distance exceeds tol (or is not finite) is replaced by the Magnus
+ * solution; if more than max_fail_frac of the audited paths fail, every path
+ * is re-solved by Magnus.  flags_dev (nullable) uint32[paths]: bit 0 audited,
+ * bit 1 replaced, bit 2 whole-batch fallback.  report_host (nullable)
+ * double[5] = {audited, max error, mean error, failed, whole-batch fallback}.
+ * With audit_every > 0 the call synchronises `stream`. */
+msk_status msk_surrogate_infer(msk_surrogate* s, int64_t path0, int64_t paths, float* U_dev,
+                               uint32_t* flags_dev, int64_t audit_every, double tol,
+                               double max_fail_frac, double* report_host, void* stream);
+
 /* S7: Euler-Maruyama (Eq. EulerMaruyama) with `steps` equal steps, a(t),
  * sigma(t) at the left end of each step, dW the sum of the fine increments. */
 msk_status msk_solve_euler(msk_ctx* ctx, int steps, int64_t paths, int precision,

@@ -47,6 +47,12 @@ class msk_gaussian(ctypes.Structure):
                 ("cov_xv", ctypes.c_double), ("cov_vv", ctypes.c_double), ("scale", ctypes.c_double)]
 
 
+class msk_surrogate_config(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("rank", ctypes.c_int32), ("hidden", ctypes.c_int32),
+                ("layers", ctypes.c_int32), ("train_batch", ctypes.c_int32), ("infer_batch", ctypes.c_int32),
+                ("ref_order", ctypes.c_int32), ("ref_steps", ctypes.c_int32), ("init_seed", ctypes.c_uint64)]
+
+
 class msk_batch_item(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_void_p), ("order", ctypes.c_int32), ("steps", ctypes.c_int32),
                 ("paths", ctypes.c_int64), ("u_out_dev", ctypes.c_void_p), ("status_dev", ctypes.c_void_p)]
@@ -84,6 +90,25 @@ SIGNATURES = {
     "msk_batch_set_variant": (_INT, [_P, _INT]),
     "msk_batch_last_error": (ctypes.c_char_p, [_P]),
     "msk_batch_destroy": (None, [_P]),
+    "msk_surrogate_create": (_INT, [ctypes.POINTER(_P), _P, ctypes.POINTER(msk_surrogate_config)]),
+    "msk_surrogate_destroy": (None, [_P]),
+    "msk_surrogate_last_error": (ctypes.c_char_p, [_P]),
+    "msk_surrogate_num_params": (_I64, [_P]),
+    "msk_surrogate_param_layout": (_INT, [_P, ctypes.POINTER(_I64)]),
+    "msk_surrogate_get_params": (_INT, [_P, _P, _P]),
+    "msk_surrogate_set_params": (_INT, [_P, _P, _P]),
+    "msk_surrogate_features": (_INT, [_P, _I64, _I64, _P, _P]),
+    "msk_surrogate_reference": (_INT, [_P, _I64, _I64, _P, _P]),
+    "msk_surrogate_fit_pod": (_INT, [_P, _P, _I64, ctypes.POINTER(_DBL), _P]),
+    "msk_surrogate_get_pod": (_INT, [_P, _P, _P, ctypes.POINTER(_DBL), _P]),
+    "msk_surrogate_set_pod": (_INT, [_P, _P, _P, _DBL, _P]),
+    "msk_surrogate_project": (_INT, [_P, _P, _I64, _P, _P]),
+    "msk_surrogate_decode": (_INT, [_P, _P, _I64, _P, _P]),
+    "msk_surrogate_forward": (_INT, [_P, _P, _I64, _P, _P]),
+    "msk_surrogate_loss_grads": (_INT, [_P, _P, _P, _I64, _P, _P, _P]),
+    "msk_surrogate_adam_step": (_INT, [_P, ctypes.c_float, _P]),
+    "msk_surrogate_train": (_INT, [_P, _P, _P, _I64, _INT, ctypes.c_float, _P, _P]),
+    "msk_surrogate_infer": (_INT, [_P, _I64, _I64, _P, _P, _I64, _DBL, _DBL, ctypes.POINTER(_DBL), _P]),
     "msk_explicit_solution": (_INT, [_P, _I64, _P, _P]),
     "msk_error": (_INT, [_P, _P, _INT, _I64, _INT, _P, _INT, _INT, _P, _P, _P]),
     "msk_moments": (_INT, [_P, _P, _INT, _I64, _P, _P]),
@@ -309,6 +334,121 @@ def msk_batch_last_error(b) -> str:
 
 def msk_batch_destroy(b):
     load_library().msk_batch_destroy(b)
+
+
+def _scheck(st: int, s):
+    if st != MSK_OK:
+        raise MskError(st, load_library().msk_surrogate_last_error(s).decode())
+
+
+def msk_surrogate_create(ctx, steps=16, rank=64, hidden=512, layers=4, train_batch=4096, infer_batch=65536,
+                         ref_order=3, ref_steps=8, init_seed=0):
+    h = _P()
+    cfg = msk_surrogate_config(steps, rank, hidden, layers, train_batch, infer_batch, ref_order, ref_steps, init_seed)
+    _check(load_library().msk_surrogate_create(ctypes.byref(h), ctx, ctypes.byref(cfg)), ctx)
+    return h
+
+
+def msk_surrogate_destroy(s):
+    load_library().msk_surrogate_destroy(s)
+
+
+def msk_surrogate_last_error(s) -> str:
+    return load_library().msk_surrogate_last_error(s).decode()
+
+
+def msk_surrogate_num_params(s) -> int:
+    return int(load_library().msk_surrogate_num_params(s))
+
+
+def msk_surrogate_param_layout(s, layers):
+    """[(offset of W_l, offset of b_l)] for l = 0..layers (weight layers = hidden layers + 1)."""
+    arr = (_I64 * (2 * (layers + 1)))()
+    _scheck(load_library().msk_surrogate_param_layout(s, arr), s)
+    return [(arr[2 * l], arr[2 * l + 1]) for l in range(layers + 1)]
+
+
+def msk_surrogate_get_params(s, params, stream=None):
+    import torch
+    _need(params, msk_surrogate_num_params(s), torch.float32, "params")
+    _scheck(load_library().msk_surrogate_get_params(s, _ptr(params), _stream(stream)), s)
+
+
+def msk_surrogate_set_params(s, params, stream=None):
+    import torch
+    _need(params, msk_surrogate_num_params(s), torch.float32, "params")
+    _scheck(load_library().msk_surrogate_set_params(s, _ptr(params), _stream(stream)), s)
+
+
+def _bf16_ptr(X):
+    import torch
+    if X.dtype not in (torch.bfloat16, torch.int16):
+        raise ValueError("features must be a bfloat16 (or int16 bit-pattern) tensor")
+    return _ptr(X)
+
+
+def msk_surrogate_features(s, path0, paths, X, stream=None):
+    _scheck(load_library().msk_surrogate_features(s, path0, paths, _bf16_ptr(X) if paths else None,
+                                                  _stream(stream)), s)
+
+
+def msk_surrogate_reference(s, path0, paths, U, stream=None):
+    import torch
+    _need(U, 1, torch.float32, "U")
+    _scheck(load_library().msk_surrogate_reference(s, path0, paths, _ptr(U), _stream(stream)), s)
+
+
+def msk_surrogate_fit_pod(s, S, N, stream=None):
+    import torch
+    _need(S, 1, torch.float32, "S")
+    sv = (_DBL * 80)()
+    _scheck(load_library().msk_surrogate_fit_pod(s, _ptr(S), N, sv, _stream(stream)), s)
+    return list(sv)
+
+
+def msk_surrogate_get_pod(s, mean=None, phi=None, stream=None):
+    sc = _DBL(0)
+    _scheck(load_library().msk_surrogate_get_pod(s, _ptr(mean), _ptr(phi), ctypes.byref(sc), _stream(stream)), s)
+    return sc.value
+
+
+def msk_surrogate_set_pod(s, mean, phi, coef_scale, stream=None):
+    _scheck(load_library().msk_surrogate_set_pod(s, _ptr(mean), _ptr(phi), coef_scale, _stream(stream)), s)
+
+
+def msk_surrogate_project(s, S, N, C, stream=None):
+    _scheck(load_library().msk_surrogate_project(s, _ptr(S), N, _ptr(C), _stream(stream)), s)
+
+
+def msk_surrogate_decode(s, C, N, U, stream=None):
+    _scheck(load_library().msk_surrogate_decode(s, _ptr(C), N, _ptr(U), _stream(stream)), s)
+
+
+def msk_surrogate_forward(s, X, B, C, stream=None):
+    _scheck(load_library().msk_surrogate_forward(s, _bf16_ptr(X), B, _ptr(C), _stream(stream)), s)
+
+
+def msk_surrogate_loss_grads(s, X, C, B, loss=None, grads=None, stream=None):
+    _scheck(load_library().msk_surrogate_loss_grads(s, _bf16_ptr(X), _ptr(C), B, _ptr(loss), _ptr(grads),
+                                                    _stream(stream)), s)
+
+
+def msk_surrogate_adam_step(s, lr, stream=None):
+    _scheck(load_library().msk_surrogate_adam_step(s, lr, _stream(stream)), s)
+
+
+def msk_surrogate_train(s, X, C, N, epochs, lr, loss_hist=None, stream=None):
+    _scheck(load_library().msk_surrogate_train(s, _bf16_ptr(X), _ptr(C), N, epochs, lr, _ptr(loss_hist),
+                                               _stream(stream)), s)
+
+
+def msk_surrogate_infer(s, path0, paths, U, flags=None, audit_every=0, tol=1e-2, max_fail_frac=0.05,
+                        stream=None):
+    """Returns the audit report (audited, max error, mean error, failed, whole-batch fallback)."""
+    rep = (_DBL * 5)()
+    _scheck(load_library().msk_surrogate_infer(s, path0, paths, _ptr(U), _ptr(flags), audit_every, tol,
+                                               max_fail_frac, rep, _stream(stream)), s)
+    return list(rep)
 
 
 # ---- convenience ---------------------------------------------------------------------

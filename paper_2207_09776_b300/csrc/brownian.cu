@@ -33,7 +33,7 @@ constexpr int kWarps = 4;                  // warps (path-steps) per block
 constexpr int kRound = 32 * kChunk;        // cells per round
 
 struct BrownArgs {
-  uint64_t seed, path_offset;
+  uint64_t seed, path_offset, path_stride;   // local path p is global path path_offset + p * path_stride
   int64_t n_fine, paths;
   int steps;
   double T;
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
   const int64_t L = a.n_fine / a.steps;
   const double delta = a.T / (double)a.n_fine;
   const double sq = sqrt(delta);
-  const uint64_t gpath = a.path_offset + (uint64_t)p;
+  const uint64_t gpath = a.path_offset + (uint64_t)p * a.path_stride;
   const int64_t f0 = (int64_t)n * L;                        // first fine cell of the step
   const double* tsig = a.tab;
   const double* talp = a.tab + (a.n_fine + 1);
@@ -202,11 +202,29 @@ msk_status launch_brownian(msk_ctx* ctx, int steps, int64_t paths, double* out, 
     msk_status st = ensure_cell_table(ctx, stream);
     if (st != MSK_OK) return st;
   }
-  BrownArgs a{ctx->seed, ctx->path_offset, ctx->n_fine, paths, steps, ctx->T, coef_dev(ctx->coef),
+  BrownArgs a{ctx->seed, ctx->path_offset, 1, ctx->n_fine, paths, steps, ctx->T, coef_dev(ctx->coef),
               trig ? ctx->tab : nullptr};
   const unsigned blocks = (unsigned)((n + kWarps - 1) / kWarps);
   if (increments_only) brownian_kernel<false, false><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
   else if (trig) brownian_kernel<true, true><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
+  else brownian_kernel<true, false><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
+  return msk_cuda(ctx, cudaGetLastError(), "brownian kernel");
+}
+
+// Functionals of the global paths first, first + stride, ... (paths of them).
+msk_status launch_brownian_strided(msk_ctx* ctx, int steps, int64_t paths, double* out, uint64_t first,
+                                   uint64_t stride, cudaStream_t stream) {
+  const int64_t n = paths * steps;
+  if (n == 0) return MSK_OK;
+  const bool trig = ctx->coef.kind == MSK_COEF_TRIG;
+  if (trig) {
+    msk_status st = ensure_cell_table(ctx, stream);
+    if (st != MSK_OK) return st;
+  }
+  BrownArgs a{ctx->seed, first, stride, ctx->n_fine, paths, steps, ctx->T, coef_dev(ctx->coef),
+              trig ? ctx->tab : nullptr};
+  const unsigned blocks = (unsigned)((n + kWarps - 1) / kWarps);
+  if (trig) brownian_kernel<true, true><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
   else brownian_kernel<true, false><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
   return msk_cuda(ctx, cudaGetLastError(), "brownian kernel");
 }
@@ -224,7 +242,7 @@ msk_status launch_brownian_with_table(msk_ctx* ctx, int steps, int64_t paths, do
   const int64_t n = paths * steps;
   if (n == 0) return MSK_OK;
   const bool trig = ctx->coef.kind == MSK_COEF_TRIG;
-  BrownArgs a{ctx->seed, ctx->path_offset, ctx->n_fine, paths, steps, ctx->T, coef_dev(ctx->coef),
+  BrownArgs a{ctx->seed, ctx->path_offset, 1, ctx->n_fine, paths, steps, ctx->T, coef_dev(ctx->coef),
               trig ? tab : nullptr};
   const unsigned blocks = (unsigned)((n + kWarps - 1) / kWarps);
   if (trig) brownian_kernel<true, true><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
