@@ -373,6 +373,11 @@ msk_status msk_surrogate_infer(msk_surrogate* s, int64_t path0, int64_t paths, f
                                uint32_t* flags_dev, int64_t audit_every, double tol,
                                double max_fail_frac, double* report_host, void* stream);
 
+/* Synchronise `stream` and report the surrogate's device status: MSK_ERR_TIMEOUT
+ * if a tensor-core pipeline wait of any earlier call ran out (the affected
+ * outputs are invalid), else MSK_OK. */
+msk_status msk_surrogate_sync_status(msk_surrogate* s, void* stream);
+
 /* S7: Euler-Maruyama (Eq. EulerMaruyama) with `steps` equal steps, a(t),
  * sigma(t) at the left end of each step, dW the sum of the fine increments. */
 msk_status msk_solve_euler(msk_ctx* ctx, int steps, int64_t paths, int precision,

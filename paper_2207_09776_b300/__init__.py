@@ -109,6 +109,7 @@ SIGNATURES = {
     "msk_surrogate_adam_step": (_INT, [_P, ctypes.c_float, _P]),
     "msk_surrogate_train": (_INT, [_P, _P, _P, _I64, _INT, ctypes.c_float, _P, _P]),
     "msk_surrogate_infer": (_INT, [_P, _I64, _I64, _P, _P, _I64, _DBL, _DBL, ctypes.POINTER(_DBL), _P]),
+    "msk_surrogate_sync_status": (_INT, [_P, _P]),
     "msk_explicit_solution": (_INT, [_P, _I64, _P, _P]),
     "msk_error": (_INT, [_P, _P, _INT, _I64, _INT, _P, _INT, _INT, _P, _P, _P]),
     "msk_moments": (_INT, [_P, _P, _INT, _I64, _P, _P]),
@@ -449,6 +450,11 @@ def msk_surrogate_infer(s, path0, paths, U, flags=None, audit_every=0, tol=1e-2,
     _scheck(load_library().msk_surrogate_infer(s, path0, paths, _ptr(U), _ptr(flags), audit_every, tol,
                                                max_fail_frac, rep, _stream(stream)), s)
     return list(rep)
+
+
+def msk_surrogate_sync_status(s, stream=None):
+    """Synchronise the stream; raises MskError (MSK_ERR_TIMEOUT) if a tensor-core pipeline wait ran out."""
+    _scheck(load_library().msk_surrogate_sync_status(s, _stream(stream)), s)
 
 
 # ---- convenience ---------------------------------------------------------------------

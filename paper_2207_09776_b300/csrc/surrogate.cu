@@ -5,8 +5,10 @@
 #include <math.h>
 
 #include <algorithm>
+#include <map>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "surrogate_kernels.cuh"
@@ -27,6 +29,8 @@ struct msk_surrogate {
   float* phi = nullptr;             // [r][n]
   double coef_scale = 0;            // network coefficients are (u - mean) Phi^T / coef_scale
   bool pod_ready = false;
+  int ldk = 0;                      // 3r rounded up to a multiple of 8
+  bf16* basis = nullptr;            // split decode basis [n][ldk] = [phi_hi | phi_lo | phi_hi]
   // parameters and Adam state (flat, fp32 master + bf16 copy)
   float* w = nullptr;
   bf16* w16 = nullptr;
@@ -34,14 +38,20 @@ struct msk_surrogate {
   float* am = nullptr;
   float* av = nullptr;
   int64_t t = 0;
-  // training activations [train_batch][.]
+  bf16* w16T = nullptr;              // per layer W_l^T [in][out] (bf16), same offsets as w
+  // training activations [train_batch][.] and their transposes [.][ldT]
+  int ldT = 0;                        // train_batch rounded up to a multiple of 8
   std::vector<float*> z;
   std::vector<bf16*> h;
+  std::vector<bf16*> hT;
+  bf16* XT = nullptr;
   float* out = nullptr;
   float* g = nullptr;
   bf16* g16 = nullptr;
+  bf16* g16T = nullptr;
   float* dz[2] = {nullptr, nullptr};
   bf16* dz16[2] = {nullptr, nullptr};
+  bf16* dz16T[2] = {nullptr, nullptr};
   float* ws = nullptr;              // split-K workspace
   int64_t ws_elems = 0;
   double* partial = nullptr;        // loss partial sums
@@ -49,7 +59,7 @@ struct msk_surrogate {
   // inference [infer_batch][.]
   bf16* iX = nullptr;
   bf16* ih[2] = {nullptr, nullptr};
-  float* iout = nullptr;
+  bf16* iA = nullptr;               // split coefficients [infer_batch][ldk] = [c_hi | c_hi | c_lo]
   // reference solves and audit (grown on demand)
   void* rs = nullptr;
   size_t rs_bytes = 0;
@@ -57,6 +67,8 @@ struct msk_surrogate {
   size_t uref_bytes = 0;
   double* aerr = nullptr;
   size_t aerr_bytes = 0;
+  uint32_t* dev_err = nullptr;        // set by kernels whose bounded waits ran out
+  std::map<std::tuple<uintptr_t, int, int, int, int>, CUtensorMap> maps;   // TMA descriptors
   std::string err;
 };
 
@@ -107,107 +119,245 @@ inline unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)((n + t - 
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// One BF16 GEMM launch (see gemm_bf16_kernel); EPI_F32 with splits > 1 writes
-// the split-K partials to the workspace and reduces them into C in fixed order.
-template <bool A_KC, bool B_KC, int EPI>
-msk_status gemm(msk_surrogate* s, const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, float* C,
-                int ldc, bf16* C16, int ldc16, const float* bias, const float* aux, int ldaux, bool split,
-                cudaStream_t stream) {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeTiledFn) nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// TMA descriptor of a K-major bf16 operand [rows][cols] (row stride ld
+// elements), box of box_rows x 64 with the 128-byte swizzle; cached per shape.
+msk_status tensor_map(msk_surrogate* s, const bf16* ptr, int rows, int cols, int ld, int box_rows, CUtensorMap* out) {
+  const auto key = std::make_tuple(reinterpret_cast<uintptr_t>(ptr), rows, cols, ld, box_rows);
+  const auto it = s->maps.find(key);
+  if (it != s->maps.end()) {
+    *out = it->second;
+    return MSK_OK;
+  }
+  if (!aligned16(ptr) || ld % 8 != 0 || ld < cols)
+    return sfail(s, MSK_ERR_UNSUPPORTED, "GEMM operand must be 16-byte aligned with a row stride of 8k elements");
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn) return sfail(s, MSK_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(bf16)};
+  const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUtensorMap m;
+  const CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(ptr), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return sfail(s, MSK_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  if (s->maps.size() > 4096) s->maps.clear();
+  s->maps.emplace(key, m);
+  *out = m;
+  return MSK_OK;
+}
+
+struct TcOut {
+  float* C = nullptr;
+  int ldc = 0;
+  bf16* C16 = nullptr;
+  int ldc16 = 0;
+  bf16* CT = nullptr;
+  int ldct = 0;
+  const float* bias = nullptr;
+  const float* aux = nullptr;
+  int ldaux = 0;
+};
+
+constexpr int kStages = 4;        // pipeline depth of the MLP GEMMs
+constexpr int kDecodeStages = 3;  // decode: K = 3r <= 192, two CTAs per SM
+
+template <int BN, int EPI, int ST>
+void launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& g, dim3 grid, cudaStream_t stream) {
+  gemm_tc_kernel<BN, EPI, ST><<<grid, 128, tc_smem_bytes(BN, ST), stream>>>(ta, tb, g);
+}
+
+template <int BN, int EPI, int ST>
+cudaError_t tc_attribute() {
+  return cudaFuncSetAttribute(gemm_tc_kernel<BN, EPI, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc_smem_bytes(BN, ST));
+}
+
+template <int BN>
+cudaError_t tc_attributes() {
+  cudaError_t e = tc_attribute<BN, EPI_F32, kStages>();
+  if (e == cudaSuccess) e = tc_attribute<BN, EPI_BIAS_F32, kStages>();
+  if (e == cudaSuccess) e = tc_attribute<BN, EPI_BIAS_GELU, kStages>();
+  if (e == cudaSuccess) e = tc_attribute<BN, EPI_GELU_BWD, kStages>();
+  if (e == cudaSuccess) e = tc_attribute<BN, EPI_BIAS_SPLIT, kStages>();
+  if (e == cudaSuccess) e = tc_attribute<BN, EPI_ADD_MEAN, kDecodeStages>();
+  return e;
+}
+
+// C = A B^T with A [M][K] (row stride lda) and B [N][K] (row stride ldb), both
+// bf16 K-major, on the tcgen05 kernel.  The tile width is the widest of 256,
+// 128, 64 whose grid still covers the SMs; split (EPI_F32 only) spreads K over
+// blockIdx.z into the workspace and reduces in a fixed order into C [M][N].
+template <int EPI>
+msk_status gemm(msk_surrogate* s, const bf16* A, int lda, int M, const bf16* B, int ldb, int N, int K, const TcOut& o,
+                bool split, cudaStream_t stream) {
   if (M == 0 || N == 0) return MSK_OK;
-  GemmArgs g{};
-  g.A = A;
-  g.B = B;
-  g.M = M;
-  g.N = N;
-  g.K = K;
-  g.lda = lda;
-  g.ldb = ldb;
-  g.vecA = aligned16(A) && lda % 8 == 0;
-  g.vecB = aligned16(B) && ldb % 8 == 0;
-  g.C = C;
-  g.ldc = ldc;
-  g.C16 = C16;
-  g.ldc16 = ldc16;
-  g.bias = bias;
-  g.aux = aux;
-  g.ldaux = ldaux;
-  const int bm = (M + GBM - 1) / GBM, bn = (N + GBN - 1) / GBN;
-  int splits = 1, kchunk = ((K + GBK - 1) / GBK) * GBK;
+  if (K < 1) return sfail(s, MSK_ERR_ARG, "GEMM with K = 0");
+  const int sms = std::max(1, s->ctx->num_sms);
+  const int bm = (M + TC_BM - 1) / TC_BM;
+  int BN = N > 128 ? 256 : (N > 64 ? 128 : 64);
+  if (EPI == EPI_ADD_MEAN) BN = std::min(BN, 128);
+  while (BN > 64 && (int64_t)bm * ((N + BN - 1) / BN) < sms) BN /= 2;
+  const int bn = (N + BN - 1) / BN;
+  const auto rup = [](int64_t x, int64_t m) { return (x + m - 1) / m * m; };
+  int splits = 1, kchunk = (int)rup(K, TC_BK);
   if (split && EPI == EPI_F32) {
-    const int want = std::max(1, (2 * s->ctx->num_sms + bm * bn - 1) / (bm * bn));
-    splits = std::min(want, std::max(1, K / 64));
-    kchunk = ((K + splits - 1) / splits + GBK - 1) / GBK * GBK;
+    const int64_t tiles = (int64_t)bm * bn;
+    splits = (int)std::min<int64_t>(std::max<int64_t>(1, (sms + tiles - 1) / tiles), std::max(1, K / 256));
+    kchunk = (int)rup((K + splits - 1) / splits, TC_BK);
     splits = (K + kchunk - 1) / kchunk;
     if (splits > 1 && (int64_t)splits * M * N > s->ws_elems) {   // workspace too small: no split
       splits = 1;
-      kchunk = ((K + GBK - 1) / GBK) * GBK;
+      kchunk = (int)rup(K, TC_BK);
     }
   }
-  g.kchunk = std::max(kchunk, GBK);
+  CUtensorMap ta, tb;
+  msk_status st = tensor_map(s, A, M, K, lda, TC_BM, &ta);
+  if (st == MSK_OK) st = tensor_map(s, B, N, K, ldb, BN, &tb);
+  if (st != MSK_OK) return st;
+  TcArgs g{};
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.kchunk = kchunk;
+  g.C = o.C;
+  g.ldc = o.ldc;
+  g.C16 = o.C16;
+  g.ldc16 = o.ldc16;
+  g.CT = o.CT;
+  g.ldct = o.ldct;
+  g.bias = o.bias;
+  g.aux = o.aux;
+  g.ldaux = o.ldaux;
+  g.err = s->dev_err;
   if (splits > 1) {
     g.C = s->ws;
     g.ldc = N;
     g.split_stride = (int64_t)M * N;
   }
-  gemm_bf16_kernel<A_KC, B_KC, EPI><<<dim3(bn, bm, splits), 256, 0, stream>>>(g);
-  msk_status st = scuda(s, cudaGetLastError(), "gemm kernel");
+  const dim3 grid(bn, bm, splits);
+  constexpr int ST = EPI == EPI_ADD_MEAN ? kDecodeStages : kStages;
+  if (BN == 256) launch_tc<256, EPI, ST>(ta, tb, g, grid, stream);
+  else if (BN == 128) launch_tc<128, EPI, ST>(ta, tb, g, grid, stream);
+  else launch_tc<64, EPI, ST>(ta, tb, g, grid, stream);
+  st = scuda(s, cudaGetLastError(), "tensor-core GEMM");
   if (st != MSK_OK || splits == 1) return st;
-  // C is contiguous [M][N] (weight gradients)
-  reduce_splits_kernel<<<blocks_for((int64_t)M * N), 256, 0, stream>>>(s->ws, splits, (int64_t)M * N, C);
+  reduce_splits_kernel<<<blocks_for((int64_t)M * N), 256, 0, stream>>>(s->ws, splits, (int64_t)M * N, o.C);
   return scuda(s, cudaGetLastError(), "split-K reduction");
 }
 
-// Forward pass of B rows of X.  train: keeps z_l and h_l of every hidden layer;
-// otherwise ping-pongs the inference buffers.  Output: out [B][r] (fp32).
-msk_status forward_chain(msk_surrogate* s, const bf16* X, int64_t B, bool train, float* out, cudaStream_t stream) {
+// W_l^T [in][out] (bf16) of every layer, the B operand of the data gradients.
+msk_status refresh_transposed_weights(msk_surrogate* s, cudaStream_t stream) {
+  for (int l = 0; l < s->L; ++l) {
+    const int out = s->dims[l + 1], in = s->dims[l];
+    transpose_bf16_kernel<<<dim3(blocks_for(in, 32), blocks_for(out, 32)), dim3(32, 8), 0, stream>>>(
+        s->w16 + s->offW[l], out, in, in, s->w16T + s->offW[l], out);
+  }
+  return scuda(s, cudaGetLastError(), "weight transpose");
+}
+
+// Forward pass of B rows of X.  train: keeps z_l, h_l and h_l^T of every
+// hidden layer; otherwise ping-pongs the inference buffers.  Output: out [B][r] (fp32).
+msk_status forward_chain(msk_surrogate* s, const bf16* X, int64_t B, bool train, float* out, cudaStream_t stream,
+                         bf16* split_out = nullptr) {
   const bf16* hin = X;
   int in = s->in_dim;
   const int H = s->cfg.hidden;
   for (int l = 0; l < s->L - 1; ++l) {
-    float* zl = train ? s->z[l] : nullptr;
-    bf16* hl = train ? s->h[l] : s->ih[l & 1];
-    msk_status st = gemm<true, true, EPI_BIAS_GELU>(s, hin, in, s->w16 + s->offW[l], in, (int)B, H, in, zl, H, hl, H,
-                                                    s->w + s->offB[l], nullptr, 0, false, stream);
+    TcOut o;
+    o.bias = s->w + s->offB[l];
+    if (train) {
+      o.C = s->z[l];
+      o.ldc = H;
+      o.C16 = s->h[l];
+      o.ldc16 = H;
+      o.CT = s->hT[l];
+      o.ldct = s->ldT;
+    } else {
+      o.C16 = s->ih[l & 1];
+      o.ldc16 = H;
+    }
+    msk_status st = gemm<EPI_BIAS_GELU>(s, hin, in, (int)B, s->w16 + s->offW[l], in, H, in, o, false, stream);
     if (st != MSK_OK) return st;
-    hin = hl;
+    hin = o.C16;
     in = H;
   }
   const int l = s->L - 1, r = s->cfg.rank;
-  return gemm<true, true, EPI_BIAS_F32>(s, hin, in, s->w16 + s->offW[l], in, (int)B, r, in, out, r, nullptr, 0,
-                                        s->w + s->offB[l], nullptr, 0, false, stream);
+  TcOut o;
+  o.C = out;
+  o.ldc = r;
+  o.bias = s->w + s->offB[l];
+  if (split_out) {   // also write the split coefficients for the tensor-core decode
+    o.C16 = split_out;
+    o.ldc16 = s->ldk;
+    return gemm<EPI_BIAS_SPLIT>(s, hin, in, (int)B, s->w16 + s->offW[l], in, r, in, o, false, stream);
+  }
+  return gemm<EPI_BIAS_F32>(s, hin, in, (int)B, s->w16 + s->offW[l], in, r, in, o, false, stream);
 }
 
 // Loss and gradients of one minibatch (B <= train_batch) into s->grad and s->loss.
+// Every GEMM is K-major x K-major: weight gradients contract over the batch
+// with the transposed copies dz^T and h^T written by the producing epilogues,
+// data gradients use the transposed weights W^T.
 msk_status loss_grads(msk_surrogate* s, const bf16* X, const float* C, int64_t B, cudaStream_t stream) {
   msk_status st = forward_chain(s, X, B, true, s->out, stream);
   if (st != MSK_OK) return st;
-  const int r = s->cfg.rank, H = s->cfg.hidden, L = s->L;
-  loss_grad_kernel<<<kLossBlocks, 256, 0, stream>>>(s->out, C, B * r, 1.0f / (float)B, s->g, s->g16, s->partial);
+  const int r = s->cfg.rank, H = s->cfg.hidden, L = s->L, ldT = s->ldT;
+  transpose_bf16_kernel<<<dim3(blocks_for(s->in_dim, 32), blocks_for(B, 32)), dim3(32, 8), 0, stream>>>(
+      X, (int)B, s->in_dim, s->in_dim, s->XT, ldT);
+  loss_grad_kernel<<<kLossBlocks, 256, 0, stream>>>(s->out, C, B * r, r, 1.0f / (float)B, s->g, s->g16, s->g16T, ldT,
+                                                    s->partial);
   loss_final_kernel<<<1, 256, 0, stream>>>(s->partial, kLossBlocks, 1.0 / (double)B, s->loss);
   st = scuda(s, cudaGetLastError(), "loss kernels");
   if (st != MSK_OK) return st;
   const bf16* cur16 = s->g16;
+  const bf16* cur16T = s->g16T;
   const float* cur = s->g;
   int cur_dim = r;
   for (int l = L - 1; l >= 0; --l) {
     const int in = s->dims[l];
-    const bf16* hprev = l > 0 ? s->h[l - 1] : X;
-    // dW_l = dz_l^T h_{l-1}  ([out][in], split-K over the batch)
-    st = gemm<false, false, EPI_F32>(s, cur16, cur_dim, hprev, in, cur_dim, in, (int)B, s->grad + s->offW[l], in,
-                                     nullptr, 0, nullptr, nullptr, 0, true, stream);
+    const bf16* prevT = l > 0 ? s->hT[l - 1] : s->XT;
+    // dW_l [out][in] = dz_l^T h_{l-1}: A = dz_l^T [out][B], B = h_{l-1}^T [in][B]
+    TcOut ow;
+    ow.C = s->grad + s->offW[l];
+    ow.ldc = in;
+    st = gemm<EPI_F32>(s, cur16T, ldT, cur_dim, prevT, ldT, in, (int)B, ow, true, stream);
     if (st != MSK_OK) return st;
     colsum_kernel<<<blocks_for(cur_dim, 32), dim3(32, 8), 0, stream>>>(cur, (int)B, cur_dim, s->grad + s->offB[l]);
     st = scuda(s, cudaGetLastError(), "bias gradient");
     if (st != MSK_OK) return st;
     if (l == 0) break;
-    // dz_{l-1} = (dz_l W_l) * GELU'(z_{l-1})
-    float* nd = s->dz[l & 1];
-    bf16* nd16 = s->dz16[l & 1];
-    st = gemm<true, false, EPI_GELU_BWD>(s, cur16, cur_dim, s->w16 + s->offW[l], in, (int)B, H, cur_dim, nd, H, nd16,
-                                         H, nullptr, s->z[l - 1], H, false, stream);
+    // dz_{l-1} = (dz_l W_l) * GELU'(z_{l-1}): A = dz_l [B][out], B = W_l^T [in][out]
+    TcOut od;
+    od.C = s->dz[l & 1];
+    od.ldc = H;
+    od.C16 = s->dz16[l & 1];
+    od.ldc16 = H;
+    od.CT = s->dz16T[l & 1];
+    od.ldct = ldT;
+    od.aux = s->z[l - 1];
+    od.ldaux = H;
+    st = gemm<EPI_GELU_BWD>(s, cur16, cur_dim, (int)B, s->w16T + s->offW[l], cur_dim, in, cur_dim, od, false, stream);
     if (st != MSK_OK) return st;
-    cur = nd;
-    cur16 = nd16;
+    cur = od.C;
+    cur16 = od.C16;
+    cur16T = od.CT;
     cur_dim = H;
   }
   return MSK_OK;
@@ -219,7 +369,8 @@ msk_status adam(msk_surrogate* s, float lr, cudaStream_t stream) {
   const float c1 = (float)(1.0 - pow(b1, (double)s->t)), c2 = (float)(1.0 - pow(b2, (double)s->t));
   adam_kernel<<<blocks_for(s->nparam), 256, 0, stream>>>(s->w, s->w16, s->grad, s->am, s->av, s->nparam, lr,
                                                          (float)b1, (float)b2, 1e-8f, c1, c2);
-  return scuda(s, cudaGetLastError(), "adam kernel");
+  msk_status st = scuda(s, cudaGetLastError(), "adam kernel");
+  return st == MSK_OK ? refresh_transposed_weights(s, stream) : st;
 }
 
 // Magnus FP32 solutions (reference order/steps) of the global paths
@@ -251,13 +402,32 @@ msk_status features(msk_surrogate* s, uint64_t first, int64_t paths, bf16* X, cu
   return scuda(s, cudaGetLastError(), "features kernel");
 }
 
+// U [P][n] = mean + c Phi as one tensor-core contraction over K = 3r of the
+// split coefficients A' (already in s->iA, P <= infer_batch) with the split basis.
+msk_status decode_split(msk_surrogate* s, int64_t P, float* U, cudaStream_t stream) {
+  TcOut o;
+  o.C = U;
+  o.ldc = s->n;
+  o.bias = s->mean;
+  return gemm<EPI_ADD_MEAN>(s, s->iA, s->ldk, (int)P, s->basis, s->ldk, s->n, 3 * s->cfg.rank, o, false, stream);
+}
+
 msk_status decode(msk_surrogate* s, const float* C, int64_t P, float* U, cudaStream_t stream) {
-  if (P == 0) return MSK_OK;
-  const dim3 grid(blocks_for(s->n / 4), (unsigned)((P + 7) / 8));
-  // coefficients are scaled: u = mean + coef_scale * C Phi.  The scale is folded
-  // into Phi at fit/set time (phi holds coef_scale * Phi).
-  decode_kernel<<<grid, 256, 0, stream>>>(C, P, s->cfg.rank, s->phi, s->mean, s->n, U);
-  return scuda(s, cudaGetLastError(), "decode kernel");
+  const int r = s->cfg.rank;
+  for (int64_t o = 0; o < P; o += s->cfg.infer_batch) {
+    const int64_t Pc = std::min<int64_t>(s->cfg.infer_batch, P - o);
+    split_coef_kernel<<<blocks_for(Pc * r), 256, 0, stream>>>(C + o * r, Pc, r, s->iA, s->ldk);
+    msk_status st = scuda(s, cudaGetLastError(), "coefficient split");
+    if (st == MSK_OK) st = decode_split(s, Pc, U + (size_t)o * s->n, stream);
+    if (st != MSK_OK) return st;
+  }
+  return MSK_OK;
+}
+
+msk_status refresh_basis(msk_surrogate* s, cudaStream_t stream) {
+  const int64_t cnt = (int64_t)s->cfg.rank * s->n;
+  split_basis_kernel<<<blocks_for(cnt), 256, 0, stream>>>(s->phi, s->cfg.rank, s->n, s->basis, s->ldk);
+  return scuda(s, cudaGetLastError(), "decode basis");
 }
 
 void free_all(msk_surrogate* s) {
@@ -268,24 +438,31 @@ void free_all(msk_surrogate* s) {
   F(s->phi);
   F(s->w);
   F(s->w16);
+  F(s->w16T);
   F(s->grad);
   F(s->am);
   F(s->av);
   for (float* p : s->z) F(p);
   for (bf16* p : s->h) F(p);
+  for (bf16* p : s->hT) F(p);
+  F(s->XT);
   F(s->out);
   F(s->g);
   F(s->g16);
+  F(s->g16T);
   for (int i = 0; i < 2; ++i) {
     F(s->dz[i]);
     F(s->dz16[i]);
+    F(s->dz16T[i]);
     F(s->ih[i]);
   }
+  F(s->dev_err);
   F(s->ws);
   F(s->partial);
   F(s->loss);
   F(s->iX);
-  F(s->iout);
+  F(s->iA);
+  F(s->basis);
   F(s->rs);
   F(s->uref);
   F(s->aerr);
@@ -361,21 +538,31 @@ extern "C" msk_status msk_surrogate_create(msk_surrogate** out, msk_ctx* ctx, co
   if (st == MSK_OK) st = salloc(s, &s->phi, (size_t)r * s->n, "POD basis");
   if (st == MSK_OK) st = salloc(s, &s->w, s->nparam, "parameters");
   if (st == MSK_OK) st = salloc(s, &s->w16, s->nparam, "bf16 parameters");
+  if (st == MSK_OK) st = salloc(s, &s->w16T, s->nparam, "transposed bf16 weights");
+  if (st == MSK_OK) st = salloc(s, &s->dev_err, 1, "error word");
+  if (st == MSK_OK) st = scuda(s, cudaMemset(s->dev_err, 0, sizeof(uint32_t)), "error word");
   if (st == MSK_OK) st = salloc(s, &s->grad, s->nparam, "gradients");
   if (st == MSK_OK) st = salloc(s, &s->am, s->nparam, "Adam m");
   if (st == MSK_OK) st = salloc(s, &s->av, s->nparam, "Adam v");
+  s->ldT = (int)((TB + 7) / 8 * 8);
+  const int64_t LT = s->ldT;
   s->z.assign(c.layers, nullptr);
   s->h.assign(c.layers, nullptr);
+  s->hT.assign(c.layers, nullptr);
   for (int l = 0; l < c.layers && st == MSK_OK; ++l) {
     st = salloc(s, &s->z[l], (size_t)TB * H, "activations");
     if (st == MSK_OK) st = salloc(s, &s->h[l], (size_t)TB * H, "activations");
+    if (st == MSK_OK) st = salloc(s, &s->hT[l], (size_t)H * LT, "activations");
   }
+  if (st == MSK_OK) st = salloc(s, &s->XT, (size_t)s->in_dim * LT, "transposed features");
   if (st == MSK_OK) st = salloc(s, &s->out, (size_t)TB * r, "outputs");
   if (st == MSK_OK) st = salloc(s, &s->g, (size_t)TB * r, "output gradient");
   if (st == MSK_OK) st = salloc(s, &s->g16, (size_t)TB * r, "output gradient");
+  if (st == MSK_OK) st = salloc(s, &s->g16T, (size_t)r * LT, "output gradient");
   for (int i = 0; i < 2 && st == MSK_OK; ++i) {
     st = salloc(s, &s->dz[i], (size_t)TB * H, "backward buffers");
     if (st == MSK_OK) st = salloc(s, &s->dz16[i], (size_t)TB * H, "backward buffers");
+    if (st == MSK_OK) st = salloc(s, &s->dz16T[i], (size_t)H * LT, "backward buffers");
     if (st == MSK_OK) st = salloc(s, &s->ih[i], (size_t)IB * H, "inference buffers");
   }
   // split-K workspace: up to 2 * SMs splits of the largest weight gradient
@@ -385,7 +572,14 @@ extern "C" msk_status msk_surrogate_create(msk_surrogate** out, msk_ctx* ctx, co
   if (st == MSK_OK) st = salloc(s, &s->partial, kLossBlocks, "loss partials");
   if (st == MSK_OK) st = salloc(s, &s->loss, 1, "loss");
   if (st == MSK_OK) st = salloc(s, &s->iX, (size_t)IB * s->in_dim, "inference features");
-  if (st == MSK_OK) st = salloc(s, &s->iout, (size_t)IB * r, "inference outputs");
+  s->ldk = (int)((3 * r + 7) / 8 * 8);
+  if (st == MSK_OK) st = salloc(s, &s->iA, (size_t)IB * s->ldk, "split coefficients");
+  if (st == MSK_OK) st = salloc(s, &s->basis, (size_t)s->n * s->ldk, "decode basis");
+  if (st == MSK_OK) st = scuda(s, cudaMemset(s->iA, 0, (size_t)IB * s->ldk * sizeof(bf16)), "split coefficients");
+  if (st == MSK_OK) st = scuda(s, cudaMemset(s->basis, 0, (size_t)s->n * s->ldk * sizeof(bf16)), "decode basis");
+  if (st == MSK_OK) st = scuda(s, tc_attributes<64>(), "GEMM attributes");
+  if (st == MSK_OK) st = scuda(s, tc_attributes<128>(), "GEMM attributes");
+  if (st == MSK_OK) st = scuda(s, tc_attributes<256>(), "GEMM attributes");
   if (st == MSK_OK)
     st = scuda(s, cudaFuncSetAttribute(sym_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        2 * SK_Q * SK_Q * (int)sizeof(double) + SK_Q * (int)sizeof(int)),
@@ -402,6 +596,7 @@ extern "C" msk_status msk_surrogate_create(msk_surrogate** out, msk_ctx* ctx, co
     to_bf16_kernel<<<blocks_for(s->nparam), 256>>>(s->w, s->w16, s->nparam);
     st = scuda(s, cudaGetLastError(), "bf16 copy");
   }
+  if (st == MSK_OK) st = refresh_transposed_weights(s, 0);
   if (st == MSK_OK) st = scuda(s, cudaMemset(s->am, 0, s->nparam * sizeof(float)), "Adam init");
   if (st == MSK_OK) st = scuda(s, cudaMemset(s->av, 0, s->nparam * sizeof(float)), "Adam init");
   if (st == MSK_OK) st = scuda(s, cudaMemset(s->grad, 0, s->nparam * sizeof(float)), "gradient init");
@@ -434,6 +629,7 @@ extern "C" msk_status msk_surrogate_set_params(msk_surrogate* s, const float* pa
   if (st != MSK_OK) return st;
   to_bf16_kernel<<<blocks_for(s->nparam), 256, 0, st_>>>(s->w, s->w16, s->nparam);
   st = scuda(s, cudaGetLastError(), "bf16 copy");
+  if (st == MSK_OK) st = refresh_transposed_weights(s, st_);
   if (st == MSK_OK) st = scuda(s, cudaMemsetAsync(s->am, 0, s->nparam * sizeof(float), st_), "Adam reset");
   if (st == MSK_OK) st = scuda(s, cudaMemsetAsync(s->av, 0, s->nparam * sizeof(float), st_), "Adam reset");
   s->t = 0;
@@ -592,6 +788,7 @@ extern "C" msk_status msk_surrogate_fit_pod(msk_surrogate* s, const float* S_dev
       small_left_mul_kernel<<<dim3(blocks_for(n), r), 256, 0, stm>>>(M, r, r, Qa, n, s->phi);
       st = scuda(s, cudaGetLastError(), "POD basis scaling");
     }
+    if (st == MSK_OK) st = refresh_basis(s, stm);
     if (st == MSK_OK) st = scuda(s, cudaStreamSynchronize(stm), "POD sync");
   }
   if (st == MSK_OK && sv_host)
@@ -647,6 +844,7 @@ extern "C" msk_status msk_surrogate_set_pod(msk_surrogate* s, const float* mean_
     small_left_mul_kernel<<<dim3(blocks_for(s->n), r), 256, 0, stm>>>(Md, r, r, phi_dev, s->n, s->phi);
     st = scuda(s, cudaGetLastError(), "POD basis copy");
   }
+  if (st == MSK_OK) st = refresh_basis(s, stm);
   if (st == MSK_OK) st = scuda(s, cudaStreamSynchronize(stm), "sync");
   if (Md) cudaFree(Md);
   if (st == MSK_OK) {
@@ -792,8 +990,8 @@ extern "C" msk_status msk_surrogate_infer(msk_surrogate* s, int64_t path0, int64
     const int64_t P = std::min(IB, paths - o);
     float* U = U_dev + (size_t)o * s->n;
     st = features(s, first + (uint64_t)o, P, s->iX, stm);
-    if (st == MSK_OK) st = forward_chain(s, s->iX, P, false, s->iout, stm);
-    if (st == MSK_OK) st = decode(s, s->iout, P, U, stm);
+    if (st == MSK_OK) st = forward_chain(s, s->iX, P, false, nullptr, stm, s->iA);
+    if (st == MSK_OK) st = decode_split(s, P, U, stm);
     if (st != MSK_OK || audit_every == 0) continue;
     const int64_t na = (P + audit_every - 1) / audit_every;
     st = sgrow(s, &s->uref, &s->uref_bytes, (size_t)na * s->n * sizeof(float), "audit solutions");
@@ -832,5 +1030,16 @@ extern "C" msk_status msk_surrogate_infer(msk_surrogate* s, int64_t path0, int64
     report_host[3] = (double)fails;
     report_host[4] = whole ? 1.0 : 0.0;
   }
+  return st;
+}
+
+extern "C" msk_status msk_surrogate_sync_status(msk_surrogate* s, void* stream) {
+  if (!s) return MSK_ERR_ARG;
+  uint32_t e = 0;
+  msk_status st = scuda(s, cudaSetDevice(s->ctx->device), "set device");
+  if (st == MSK_OK)
+    st = scuda(s, cudaMemcpyAsync(&e, s->dev_err, sizeof(e), cudaMemcpyDeviceToHost, (cudaStream_t)stream), "copy");
+  if (st == MSK_OK) st = scuda(s, cudaStreamSynchronize((cudaStream_t)stream), "sync");
+  if (st == MSK_OK && e) st = sfail(s, MSK_ERR_TIMEOUT, "a tensor-core pipeline wait ran out");
   return st;
 }

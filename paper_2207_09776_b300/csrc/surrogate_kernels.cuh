@@ -7,6 +7,7 @@
 
 #include "msk_internal.cuh"
 #include "philox.cuh"
+#include "umma.cuh"
 
 namespace sgk {
 
@@ -81,158 +82,297 @@ __device__ __forceinline__ float gelu_prime(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.3989422804014327f;
 }
 
-// ------------------------------------------------------------------ BF16 GEMM (mma.sync)
-// C[M][N] = sum_k A(m, k) B(n, k): bf16 operands, fp32 accumulation.
-// A_KC: A stored [M][K] (row stride lda), else [K][M]; B_KC: B stored [N][K], else [K][N].
-// Shared-memory tiles keep the global layout; ldmatrix (.trans for the [K][.]
-// layouts) builds the m16n8k16 fragments.
-enum { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_GELU = 2, EPI_GELU_BWD = 3 };
+// ------------------------------------------------------------------ BF16 GEMM (tcgen05)
+// C[M][N] = sum_k A[m][k] B[n][k]: both operands K-major bf16 in global memory
+// (row strides multiples of 8 elements), fp32 accumulation in tensor memory.
+// One 128 x BN output tile per CTA of 4 warps: warp 0 lane 0 streams 128 x 64
+// and BN x 64 operand tiles by TMA (128-byte swizzle) through a 4-stage
+// shared-memory ring, warp 1 lane 0 issues tcgen05.mma (128 x BN x 16 per
+// instruction) into a BN-column TMEM accumulator, and all four warps run the
+// epilogue (warp w owns TMEM lanes = tile rows 32w .. 32w + 31).
+// blockIdx.z selects a K range (split-K; EPI_F32 writes C + z * split_stride).
+enum { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_GELU = 2, EPI_GELU_BWD = 3, EPI_BIAS_SPLIT = 4, EPI_ADD_MEAN = 5 };
 
-struct GemmArgs {
-  const bf16* A;
-  const bf16* B;
-  int M, N, K, lda, ldb;
-  int kchunk;             // K range per blockIdx.z (multiple of 32)
-  int vecA, vecB;         // 16-byte loads allowed (aligned base, ld % 8 == 0)
-  float* C;               // fp32 output; EPI_F32 with split-K: C + z * split_stride
+struct TcArgs {
+  int M, N, K, kchunk;
+  float* C;              // fp32 row-major [M][ldc] (EPI_BIAS_GELU: z, optional; EPI_GELU_BWD: dz, optional)
   int ldc;
   int64_t split_stride;
-  bf16* C16;              // bf16 output (EPI_BIAS_GELU: GELU(z); EPI_GELU_BWD: dz)
+  bf16* C16;             // bf16 row-major [M][ldc16] (EPI_BIAS_GELU: GELU(z); EPI_GELU_BWD: dz;
+                         // EPI_BIAS_SPLIT: [hi | hi | lo] of the output, 3N columns), optional
   int ldc16;
-  const float* bias;      // [N]
-  const float* aux;       // EPI_GELU_BWD: pre-activation z [M][ldaux]
+  bf16* CT;              // bf16 transposed [N][ldct] copy of the bf16 output, optional
+  int ldct;
+  const float* bias;     // [N] (EPI_ADD_MEAN: the POD mean)
+  const float* aux;      // EPI_GELU_BWD: pre-activation z [M][ldaux]
   int ldaux;
+  uint32_t* err;         // bit 0 set if a pipeline wait ran out
 };
 
-constexpr int GBM = 128, GBN = 64, GBK = 32;
-constexpr int KC_LD = GBK + 8;            // [rows][k] tiles: 80-byte rows
-constexpr int A_T_LD = GBM + 8;           // [k][m] tile: 272-byte rows
-constexpr int B_T_LD = GBN + 8;           // [k][n] tile: 144-byte rows
+constexpr int TC_BM = 128, TC_BK = 64;
+constexpr uint32_t kTcWaitLimit = 1u << 24;   // polls of one mbarrier before giving up
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+__host__ __device__ constexpr size_t tc_smem_bytes(int BN, int stages) {
+  return 1024 + (size_t)stages * (TC_BM + BN) * TC_BK * 2 + (2 * stages + 1) * 8 + 16;
 }
 
-template <bool TRANS>
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const bf16* p) {
-  const uint32_t s = (uint32_t)__cvta_generic_to_shared(p);
-  if (TRANS)
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(s));
-  else
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(s));
-}
-
-// Copy the (ROWS x GBK) tile at (r0, k0) of an operand into shared memory in
-// its own layout: KC -> sm[ROWS][KC_LD] (k fastest), else sm[GBK][ROWS + 8]
-// (rows fastest).  Elements outside [0, rows) x [k0, k1) are zero.
-template <int ROWS, bool KC>
-__device__ __forceinline__ void fill_tile(bf16* sm, const bf16* __restrict__ G, int ld, int rows, int r0, int k0,
-                                          int k1, bool vec, int tid) {
-  constexpr int CH = KC ? ROWS * (GBK / 8) : GBK * (ROWS / 8);   // 16-byte chunks
-  const bf16 zero = __float2bfloat16(0.f);
-  for (int c = tid; c < CH; c += 256) {
-    int rr, kk;
-    if (KC) {
-      rr = c / (GBK / 8);
-      kk = (c % (GBK / 8)) * 8;
-    } else {
-      kk = c / (ROWS / 8);
-      rr = (c % (ROWS / 8)) * 8;
-    }
-    const int gr = r0 + rr, gk = k0 + kk;
-    bf16* dst = KC ? sm + rr * KC_LD + kk : sm + kk * (ROWS + 8) + rr;
-    const bool full = KC ? (gr < rows && gk + 8 <= k1) : (gk < k1 && gr + 8 <= rows);
-    if (vec && full) {
-      const bf16* src = KC ? G + (size_t)gr * ld + gk : G + (size_t)gk * ld + gr;
-      *reinterpret_cast<uint4*>(dst) = __ldg(reinterpret_cast<const uint4*>(src));
-    } else {
+__device__ __forceinline__ void store_row_f32(float* dst, const float (&v)[32], int nn) {
+  if (nn == 32 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int r = KC ? gr : gr + e, k = KC ? gk + e : gk;
-        dst[e] = (r < rows && k < k1) ? (KC ? G[(size_t)r * ld + k] : G[(size_t)k * ld + r]) : zero;
-      }
-    }
+    for (int q = 0; q < 8; ++q)
+      reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < nn) dst[j] = v[j];
   }
 }
 
-template <bool A_KC, bool B_KC, int EPI>
-__global__ void __launch_bounds__(256) gemm_bf16_kernel(const GemmArgs g) {
-  constexpr int A_ELEMS = A_KC ? GBM * KC_LD : GBK * A_T_LD;
-  constexpr int B_ELEMS = B_KC ? GBN * KC_LD : GBK * B_T_LD;
-  __shared__ __align__(128) bf16 As[A_ELEMS];
-  __shared__ __align__(128) bf16 Bs[B_ELEMS];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wm = warp & 3, wn = warp >> 2;     // 4 x 2 warps, 32 x 32 outputs per warp
-  const int gid = lane >> 2, tig = lane & 3;
-  const int mi = lane >> 3, rr = lane & 7;     // ldmatrix: matrix and row served by this lane
-  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-  const int kbeg = blockIdx.z * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
-  float acc[2][4][4];
+__device__ __forceinline__ void store_row_bf16(bf16* dst, const float (&v)[32], int nn) {
+  if (nn == 32 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+    uint32_t pk[16];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
-    fill_tile<GBM, A_KC>(As, g.A, g.lda, g.M, m0, k0, kend, g.vecA, tid);
-    fill_tile<GBN, B_KC>(Bs, g.B, g.ldb, g.N, n0, k0, kend, g.vecB, tid);
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GBK; kk += 16) {
-      uint32_t a[2][4], b[2][4];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        // matrices: (m 0-7, k 0-7), (m 8-15, k 0-7), (m 0-7, k 8-15), (m 8-15, k 8-15)
-        const int mo = wm * 32 + i * 16 + (mi & 1) * 8, ko = kk + (mi >> 1) * 8;
-        if (A_KC) ldsm_x4<false>(a[i], As + (mo + rr) * KC_LD + ko);
-        else ldsm_x4<true>(a[i], As + (ko + rr) * A_T_LD + mo);
-      }
-#pragma unroll
-      for (int jp = 0; jp < 2; ++jp) {
-        // matrices: (n-tile 2jp, k 0-7), (2jp, k 8-15), (2jp+1, k 0-7), (2jp+1, k 8-15)
-        const int no = wn * 32 + jp * 16 + (mi >> 1) * 8, ko = kk + (mi & 1) * 8;
-        if (B_KC) ldsm_x4<false>(b[jp], Bs + (no + rr) * KC_LD + ko);
-        else ldsm_x4<true>(b[jp], Bs + (ko + rr) * B_T_LD + no);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j >> 1][(j & 1) * 2], b[j >> 1][(j & 1) * 2 + 1]);
+    for (int q = 0; q < 16; ++q) {
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+      pk[q] = *reinterpret_cast<const uint32_t*>(&b2);
     }
-    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      reinterpret_cast<uint4*>(dst)[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < nn) dst[j] = __float2bfloat16(v[j]);
   }
-  float* Cz = (EPI == EPI_F32) ? g.C + (size_t)blockIdx.z * g.split_stride : g.C;
+}
+
+__device__ __forceinline__ void store_row_f32_stream(float* dst, const float (&v)[32], int nn) {
+  if (nn == 32 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+    for (int q = 0; q < 8; ++q)
+      __stcs(reinterpret_cast<float4*>(dst) + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+  } else {
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < 32; ++j)
+      if (j < nn) __stcs(dst + j, v[j]);
+  }
+}
+
+// Column j of the chunk goes to CT[(nb + j) * ldct + m]: the 32 lanes of a warp
+// hold consecutive rows m, so each j is one coalesced 64-byte store.
+__device__ __forceinline__ void store_col_bf16(bf16* CT, int ldct, int nb, int m, const float (&v)[32], int nn) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = m0 + wm * 32 + i * 16 + gid + (q >= 2 ? 8 : 0);
-        const int c = n0 + wn * 32 + j * 8 + tig * 2 + (q & 1);
-        if (r >= g.M || c >= g.N) continue;
-        float v = acc[i][j][q];
-        if (EPI == EPI_F32) {
-          Cz[(size_t)r * g.ldc + c] = v;
-        } else if (EPI == EPI_BIAS_F32) {
-          g.C[(size_t)r * g.ldc + c] = v + g.bias[c];
-        } else if (EPI == EPI_BIAS_GELU) {
-          v += g.bias[c];
-          if (g.C) g.C[(size_t)r * g.ldc + c] = v;
-          g.C16[(size_t)r * g.ldc16 + c] = __float2bfloat16(gelu(v));
-        } else {
-          const float dz = v * gelu_prime(g.aux[(size_t)r * g.ldaux + c]);
-          g.C[(size_t)r * g.ldc + c] = dz;
-          g.C16[(size_t)r * g.ldc16 + c] = __float2bfloat16(dz);
-        }
+  for (int j = 0; j < 32; ++j)
+    if (j < nn) CT[(size_t)(nb + j) * ldct + m] = __float2bfloat16(v[j]);
+}
+
+template <int EPI>
+__device__ __forceinline__ void tc_epilogue_chunk(const TcArgs& g, float (&v)[32], int m, int nb, int nn) {
+  if (EPI == EPI_F32) {
+    store_row_f32(g.C + (size_t)blockIdx.z * g.split_stride + (size_t)m * g.ldc + nb, v, nn);
+  } else if (EPI == EPI_BIAS_F32) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < nn) v[j] += __ldg(g.bias + nb + j);
+    store_row_f32(g.C + (size_t)m * g.ldc + nb, v, nn);
+  } else if (EPI == EPI_BIAS_GELU) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < nn) v[j] += __ldg(g.bias + nb + j);
+    if (g.C) store_row_f32(g.C + (size_t)m * g.ldc + nb, v, nn);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = gelu(v[j]);
+    if (g.C16) store_row_bf16(g.C16 + (size_t)m * g.ldc16 + nb, v, nn);
+    if (g.CT) store_col_bf16(g.CT, g.ldct, nb, m, v, nn);
+  } else if (EPI == EPI_BIAS_SPLIT) {
+    // network output c = acc + bias, and its two-term bf16 split c ~ hi + lo
+    // laid out [hi | hi | lo] so that one K = 3N contraction with the split
+    // basis [Phi_hi | Phi_lo | Phi_hi] gives hi Phi_hi + hi Phi_lo + lo Phi_hi.
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < nn) v[j] += __ldg(g.bias + nb + j);
+    if (g.C) store_row_f32(g.C + (size_t)m * g.ldc + nb, v, nn);
+    float hi[32], lo[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      hi[j] = __bfloat162float(__float2bfloat16(v[j]));
+      lo[j] = v[j] - hi[j];
+    }
+    bf16* row = g.C16 + (size_t)m * g.ldc16;
+    store_row_bf16(row + nb, hi, nn);
+    store_row_bf16(row + g.N + nb, hi, nn);
+    store_row_bf16(row + 2 * g.N + nb, lo, nn);
+  } else if (EPI == EPI_ADD_MEAN) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < nn) v[j] += __ldg(g.bias + nb + j);
+    store_row_f32_stream(g.C + (size_t)m * g.ldc + nb, v, nn);
+  } else {
+    const float* z = g.aux + (size_t)m * g.ldaux + nb;
+    if (nn == 32 && (reinterpret_cast<uintptr_t>(z) & 15) == 0) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 zz = __ldg(reinterpret_cast<const float4*>(z) + q);
+        v[4 * q] *= gelu_prime(zz.x);
+        v[4 * q + 1] *= gelu_prime(zz.y);
+        v[4 * q + 2] *= gelu_prime(zz.z);
+        v[4 * q + 3] *= gelu_prime(zz.w);
       }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < nn) v[j] *= gelu_prime(z[j]);
+    }
+    if (g.C) store_row_f32(g.C + (size_t)m * g.ldc + nb, v, nn);
+    if (g.C16) store_row_bf16(g.C16 + (size_t)m * g.ldc16 + nb, v, nn);
+    if (g.CT) store_col_bf16(g.CT, g.ldct, nb, m, v, nn);
+  }
+}
+
+template <int BN, int EPI, int TC_STAGES>
+__global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                          const __grid_constant__ CUtensorMap tmB, const TcArgs g) {
+  static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
+  static_assert(TC_STAGES >= 2 && TC_STAGES <= 6, "pipeline depth");
+  constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
+  extern __shared__ uint8_t tc_smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = base;
+  uint8_t* sB = base + TC_STAGES * A_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + TC_STAGES * B_BYTES);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* done = empty + TC_STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * BN;
+  const int kbeg = blockIdx.z * g.kchunk;
+  const int kend = min(g.K, kbeg + g.kchunk);
+  const int nk = (kend - kbeg + TC_BK - 1) / TC_BK;   // >= 1: every split owns a non-empty K range
+
+  if (threadIdx.x == 0) {
+    umma::prefetch_tensormap(&tmA);
+    umma::prefetch_tensormap(&tmB);
+    for (int s = 0; s < TC_STAGES; ++s) {
+      umma::mbar_init(full + s, 1);
+      umma::mbar_init(empty + s, 1);
+    }
+    umma::mbar_init(done, 1);
+    umma::fence_barrier_init();
+  }
+  if (warp == 0) umma::tmem_alloc(tmem_slot, BN);
+  umma::tc_fence_before();
+  __syncthreads();
+  umma::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  bool fail = false;
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    int issued = 0;
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % TC_STAGES;
+      if (!umma::mbar_wait(empty + s, ((it / TC_STAGES) & 1) ^ 1, kTcWaitLimit)) {
+        fail = true;
+        break;
+      }
+      umma::mbar_arrive_expect_tx(full + s, A_BYTES + B_BYTES);
+      const int kc = kbeg + it * TC_BK;
+      umma::tma_load_2d(sA + s * A_BYTES, &tmA, full + s, kc, m0);
+      umma::tma_load_2d(sB + s * B_BYTES, &tmB, full + s, kc, n0);
+      issued = it + 1;
+    }
+    // the last load of every stage has landed before the CTA can leave
+    for (int it = max(0, issued - TC_STAGES); it < issued; ++it)
+      if (!umma::mbar_wait(full + it % TC_STAGES, (it / TC_STAGES) & 1, kTcWaitLimit)) fail = true;
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(TC_BM, BN);
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % TC_STAGES;
+      if (!umma::mbar_wait(full + s, (it / TC_STAGES) & 1, kTcWaitLimit)) {
+        fail = true;
+        break;
+      }
+      umma::tc_fence_after();
+      const uint64_t da = umma::desc_sw128_kmajor(sA + s * A_BYTES);
+      const uint64_t db = umma::desc_sw128_kmajor(sB + s * B_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 16; ++kk)   // advance 16 bf16 = 32 bytes along K inside the swizzle atom
+        umma::mma_bf16(tmem, da + 2 * kk, db + 2 * kk, idesc, (it | kk) ? 1u : 0u);
+      umma::mma_commit(empty + s);
+    }
+    umma::mma_commit(done);
+  }
+  __syncwarp();
+  if (fail) atomicOr(g.err, 1u);
+
+  // ---- epilogue: TMEM -> registers -> global
+  const bool ready = __all_sync(0xffffffffu, umma::mbar_wait(done, 0, kTcWaitLimit));
+  umma::tc_fence_after();
+  if (!ready) {
+    if (lane == 0) atomicOr(g.err, 1u);
+  } else {
+    const int m = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c = 0; c < BN / 32; ++c) {
+      const int nb = n0 + c * 32;
+      if (nb >= g.N) break;                                   // same for the whole CTA
+      uint32_t r[32];
+      umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
+      float v[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+      if (m < g.M) tc_epilogue_chunk<EPI>(g, v, m, nb, min(32, g.N - nb));
+    }
+  }
+  umma::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tmem, BN);
+}
+
+// A' [P][ld] = [hi | hi | lo] of fp32 coefficients C [P][r] (see EPI_BIAS_SPLIT).
+__global__ void split_coef_kernel(const float* __restrict__ C, int64_t P, int r, bf16* __restrict__ A, int ld) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= P * r) return;
+  const int64_t p = e / r;
+  const int j = (int)(e % r);
+  const float v = C[e];
+  const bf16 hi = __float2bfloat16(v);
+  const bf16 lo = __float2bfloat16(v - __bfloat162float(hi));
+  bf16* row = A + p * ld;
+  row[j] = hi;
+  row[r + j] = hi;
+  row[2 * r + j] = lo;
+}
+
+// Split decode basis B' [n][ld] = [Phi_hi | Phi_lo | Phi_hi] (K-major) from Phi [r][n].
+__global__ void split_basis_kernel(const float* __restrict__ phi, int r, int n, bf16* __restrict__ B, int ld) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)r * n) return;
+  const int j = (int)(e / n), f = (int)(e % n);
+  const float v = phi[e];
+  const bf16 hi = __float2bfloat16(v);
+  const bf16 lo = __float2bfloat16(v - __bfloat162float(hi));
+  bf16* row = B + (size_t)f * ld;
+  row[j] = hi;
+  row[r + j] = lo;
+  row[2 * r + j] = hi;
+}
+
+// out[c][ld_out] = in[r][ld_in]^T for a rows x cols bf16 matrix (32 x 32 tiles).
+__global__ void transpose_bf16_kernel(const bf16* __restrict__ in, int rows, int cols, int ld_in,
+                                      bf16* __restrict__ out, int ld_out) {
+  __shared__ bf16 t[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    t[i][threadIdx.x] = (r < rows && c < cols) ? in[(size_t)r * ld_in + c] : __float2bfloat16(0.f);
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) out[(size_t)c * ld_out + r] = t[threadIdx.x][i];
+  }
 }
 
 // out[i] = sum_z ws[z][i] (split-K reduction, fixed order).
@@ -258,17 +398,21 @@ __device__ __forceinline__ double block_sum_d(double v, double* red) {
 }
 
 // g = 2 (out - target) / B as fp32 and bf16; per-block partial sums of (out - target)^2.
+// out, target, g, g16: [B][r]; g16T: [r][ldt] (transposed bf16 copy).
 __global__ void __launch_bounds__(256) loss_grad_kernel(const float* __restrict__ out, const float* __restrict__ target,
-                                                        int64_t n, float inv_b, float* __restrict__ g,
-                                                        bf16* __restrict__ g16, double* __restrict__ partial) {
+                                                        int64_t n, int r, float inv_b, float* __restrict__ g,
+                                                        bf16* __restrict__ g16, bf16* __restrict__ g16T, int ldt,
+                                                        double* __restrict__ partial) {
   __shared__ double red[256];
   double s = 0.0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const float d = out[e] - target[e];
     s += (double)d * d;
     const float gv = 2.0f * d * inv_b;
-    if (g) g[e] = gv;
-    if (g16) g16[e] = __float2bfloat16(gv);
+    const bf16 gq = __float2bfloat16(gv);
+    g[e] = gv;
+    g16[e] = gq;
+    g16T[(size_t)(e % r) * ldt + e / r] = gq;
   }
   s = block_sum_d(s, red);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -645,40 +789,6 @@ __global__ void __launch_bounds__(256) fix_sign_kernel(float* __restrict__ Phi, 
   __syncthreads();
   if (flip)
     for (int f = threadIdx.x; f < n; f += blockDim.x) row[f] = -row[f];
-}
-
-// U[p][f] = mean[f] + sum_j C[p][j] Phi[j][f]; block: 8 paths x 1024 columns,
-// float4 per thread (n % 4 == 0, r <= 80); streaming stores.
-__global__ void __launch_bounds__(256) decode_kernel(const float* __restrict__ C, int64_t P, int r,
-                                                     const float* __restrict__ Phi, const float* __restrict__ mean,
-                                                     int n, float* __restrict__ U) {
-  __shared__ float Cs[8][SK_Q];
-  const int64_t p0 = (int64_t)blockIdx.y * 8;
-  for (int e = threadIdx.x; e < 8 * r; e += blockDim.x) {
-    const int pp = e / r, j = e % r;
-    Cs[pp][j] = (p0 + pp < P) ? C[(p0 + pp) * r + j] : 0.f;
-  }
-  __syncthreads();
-  const int f = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
-  if (f >= n) return;
-  const float4 m = *reinterpret_cast<const float4*>(mean + f);
-  float4 acc[8];
-#pragma unroll
-  for (int pp = 0; pp < 8; ++pp) acc[pp] = m;
-  for (int j = 0; j < r; ++j) {
-    const float4 ph = __ldg(reinterpret_cast<const float4*>(Phi + (size_t)j * n + f));
-#pragma unroll
-    for (int pp = 0; pp < 8; ++pp) {
-      const float c = Cs[pp][j];
-      acc[pp].x = fmaf(c, ph.x, acc[pp].x);
-      acc[pp].y = fmaf(c, ph.y, acc[pp].y);
-      acc[pp].z = fmaf(c, ph.z, acc[pp].z);
-      acc[pp].w = fmaf(c, ph.w, acc[pp].w);
-    }
-  }
-#pragma unroll
-  for (int pp = 0; pp < 8; ++pp)
-    if (p0 + pp < P) __stcs(reinterpret_cast<float4*>(U + (p0 + pp) * n + f), acc[pp]);
 }
 
 // Audit of local path j * every: relative L2 distance of the surrogate solution

@@ -117,6 +117,28 @@ def test_forward_and_gradients_match_the_bf16_oracle(dims, B):
     # the bf16 rounding points matter: the unrounded float64 gradients are further away
     _, g64 = sg.loss_and_grads(params, X, C, bf16=False)
     assert rel(got[0][0], g64[0][0]) > 2 * rel(got[0][0], want_grads[0][0])
+    msk.msk_surrogate_sync_status(s)
+    msk.msk_surrogate_destroy(s)
+    solver.close()
+
+
+@pytest.mark.parametrize("B", [6000, 40000])
+def test_forward_on_large_batches_matches_the_oracle(B):
+    """Large batches run the 128- and 256-column tensor-core tiles; sampled rows
+    (including the ragged last tile) against the bf16 oracle."""
+    dims = [48, 512, 512, 64]
+    w = LANGEVIN_TRIG_128.with_(d=32, n_fine=1024)
+    solver, s = make(w, steps=16, rank=64, hidden=512, layers=2, train_batch=64, infer_batch=B)
+    params, _ = set_random_params(s, dims, seed=13)
+    rng = np.random.default_rng(14)
+    X = sg.to_bf16(rng.normal(size=(B, 48)))
+    out = torch.empty(B, 64, device="cuda")
+    msk.msk_surrogate_forward(s, bf16_tensor(X), B, out)
+    torch.cuda.synchronize()
+    rows = np.concatenate([rng.choice(B - 200, 56, replace=False), np.arange(B - 8, B)])
+    want, _ = sg.forward(params, X[rows], bf16=True)
+    assert rel(out.cpu().numpy()[rows], want) <= 1e-3
+    msk.msk_surrogate_sync_status(s)
     msk.msk_surrogate_destroy(s)
     solver.close()
 
