@@ -55,9 +55,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-comparators", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=0, help="paths in the CPU-oracle sample (0 = auto)")
-    p.add_argument("--workload", default="trig128", choices=("trig128", "batch"),
+    p.add_argument("--workload", default="trig128", choices=("trig128", "batch", "surrogate"),
                    help="trig128: the time-dependent 128^2 workload (default); batch: grids 64/128/256 "
-                        "in ratio 4:2:1 of 16384 paths in one persistent launch")
+                        "in ratio 4:2:1 of 16384 paths in one persistent launch; surrogate: the learned "
+                        "surrogate of the 128^2 workload served 65536 paths per step with a 1%% Magnus audit")
+    p.add_argument("--no-surrogate", action="store_true", help="skip the surrogate summary of the default line")
     p.add_argument("--profile-case", type=int, default=0, metavar="PATHS",
                    help="run two plain solves of the benchmark workload with PATHS paths at K = 8 "
                         "(a small case for ncu captures) and exit")
@@ -153,11 +155,17 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ helpers
 
+def engine_source_hash():
+    h = hashlib.sha256()
+    for f in ("engine.cu", "engine_core.cuh", "stencil.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2207_09776_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def engine_profile():
     """ncu DRAM traffic of the engine kernel from the committed profile summary,
-    valid only if the engine source is unchanged since it was taken."""
-    src = os.path.join(ROOT, "paper_2207_09776_b300", "csrc", "engine.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    valid only if the engine sources are unchanged since it was taken."""
+    h = engine_source_hash()
     prof = os.path.join(ROOT, "profiles", "magnus_engine_d128_f32.txt")
     if not os.path.exists(prof):
         return None, h
@@ -179,6 +187,160 @@ def measured_peaks():
     if os.path.exists(p):
         return json.load(open(p)), "measured"
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+# ------------------------------------------------------------------ learned surrogate
+
+SURR_CFG = dict(steps=16, rank=64, hidden=512, layers=4, train_batch=4096, infer_batch=65536)
+SURR_TRAIN = 196608          # Magnus solutions the surrogate is trained on
+SURR_EPOCHS = 300
+SURR_LR = 1e-3               # cosine decay to zero over the epochs
+SURR_SERVE = 65536           # paths per serve step
+SURR_AUDIT_EVERY = 100       # 1% Magnus audit
+SURR_TOL = 1e-2              # per-path relative L2 fallback threshold
+SURR_MAX_FAIL = 0.05         # whole-batch fallback above this audited failure rate
+SURR_HELDOUT = 8192
+MLP_FLOPS_PER_PATH = 2 * (48 * 512 + 3 * 512 * 512 + 512 * 64)
+
+
+def _events(torch, stream):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def train_surrogate(msk, torch, solver, K, stream):
+    """Untimed setup: reference solutions, POD, features, Adam training; returns (s, info)."""
+    w = solver.w
+    n = w.d * w.d
+    s = msk.msk_surrogate_create(solver.ctx, ref_order=ORDER, ref_steps=K, init_seed=w.seed, **SURR_CFG)
+
+    def timed(fn):
+        a, b = _events(torch, stream)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    U = torch.empty(SURR_TRAIN, n, device="cuda")
+    t_ref = timed(lambda: msk.msk_surrogate_reference(s, 0, SURR_TRAIN, U, stream))
+    t0 = time.perf_counter()
+    sv = msk.msk_surrogate_fit_pod(s, U, SURR_TRAIN, stream)
+    t_pod = time.perf_counter() - t0
+    C = torch.empty(SURR_TRAIN, SURR_CFG["rank"], device="cuda")
+    msk.msk_surrogate_project(s, U, SURR_TRAIN, C, stream)
+    X = torch.empty(SURR_TRAIN, 3 * SURR_CFG["steps"], dtype=torch.bfloat16, device="cuda")
+    msk.msk_surrogate_features(s, 0, SURR_TRAIN, X, stream)
+    del U
+    torch.cuda.empty_cache()
+    nb = SURR_TRAIN // SURR_CFG["train_batch"]
+    hist = torch.empty(SURR_EPOCHS * nb, device="cuda")
+
+    def train():
+        for e in range(SURR_EPOCHS):
+            lr = SURR_LR * 0.5 * (1 + math.cos(math.pi * e / SURR_EPOCHS)) + 1e-6
+            msk.msk_surrogate_train(s, X, C, SURR_TRAIN, 1, lr, hist[e * nb:], stream)
+    t_train = timed(train)
+    msk.msk_surrogate_sync_status(s, stream)
+    h = hist.view(SURR_EPOCHS, nb).mean(1).cpu().numpy()
+    steps = SURR_EPOCHS * nb
+    info = {"train_paths": SURR_TRAIN, "epochs": SURR_EPOCHS, "adam_steps": steps, "batch": SURR_CFG["train_batch"],
+            "lr": f"{SURR_LR} cosine", "ref": f"Magnus FP32 order {ORDER}, K={K}",
+            "ref_solve_paths_per_s": SURR_TRAIN / (t_ref / 1e3), "pod_fit_s": t_pod,
+            "pod_rank_resolved": int(sum(1 for v in sv[:SURR_CFG["rank"]] if v > 0)),
+            "train_ms_per_step": t_train / steps,
+            "train_tflops": 3 * MLP_FLOPS_PER_PATH * SURR_CFG["train_batch"] / (t_train / steps / 1e3) / 1e12,
+            "loss_first_epoch": float(h[0]), "loss_last_epoch": float(h[-1])}
+    del X, C
+    return s, info
+
+
+def surrogate_accuracy(msk, torch, solver, s, K, stream):
+    """Held-out accuracy against the Magnus solution it learned and against the
+    double-precision reference of the fixed-error protocol."""
+    w = solver.w
+    n = w.d * w.d
+    p0 = SURR_TRAIN
+    U = torch.empty(SURR_HELDOUT, n, device="cuda")
+    ref = torch.empty(SURR_HELDOUT, n, device="cuda")
+    msk.msk_surrogate_infer(s, p0, SURR_HELDOUT, U, None, 0, SURR_TOL, SURR_MAX_FAIL, stream)
+    msk.msk_surrogate_reference(s, p0, SURR_HELDOUT, ref, stream)
+    e = (torch.linalg.norm(U - ref, dim=1) / torch.linalg.norm(ref, dim=1)).double()
+    out = {"heldout_paths": SURR_HELDOUT, "vs_magnus_fp32_mean": float(e.mean()),
+           "vs_magnus_fp32_p95": float(e.quantile(0.95)), "vs_magnus_fp32_max": float(e.max()),
+           "frac_above_tol": float((e > SURR_TOL).double().mean())}
+    # Err against FP64 order-3 Magnus with REF_K steps on REF_PATHS held-out paths
+    import paper_2207_09776_b300 as _m
+    s64 = _m.Solver(w.with_(path_offset=w.path_offset + p0))
+    r64 = s64.magnus(ORDER, REF_K, paths=REF_PATHS, precision=_m.MSK_F64)
+    _, e_sur = s64.error(U[:REF_PATHS].view(REF_PATHS, w.d, w.d).contiguous(), _m.MSK_F32, ref=r64,
+                         ref_precision=_m.MSK_F64)
+    u32 = s64.magnus(ORDER, K, paths=REF_PATHS, precision=_m.MSK_F32)
+    _, e_mag = s64.error(u32, _m.MSK_F32, ref=r64, ref_precision=_m.MSK_F64)
+    out["err_vs_fp64_ref"] = {"surrogate": float(e_sur.cpu()[0]), f"magnus_fp32_K{K}": float(e_mag.cpu()[0]),
+                              "paths": REF_PATHS}
+    s64.close()
+    return out
+
+
+def surrogate_serve(msk, torch, solver, s, steps, warmup, stream):
+    """Timed serve steps (features, network, decode, 1% audit with fallback) and a component breakdown."""
+    w = solver.w
+    n = w.d * w.d
+    P = SURR_SERVE
+    U = torch.empty(P, n, device="cuda")
+    flags = torch.zeros(P, dtype=torch.int32, device="cuda")
+    base = SURR_TRAIN + SURR_HELDOUT
+    for i in range(max(warmup, 0)):
+        msk.msk_surrogate_infer(s, base, P, U, flags, SURR_AUDIT_EVERY, SURR_TOL, SURR_MAX_FAIL, stream)
+    torch.cuda.synchronize()
+    reps = []
+    a, b = _events(torch, stream)
+    a.record(stream)
+    for i in range(steps):
+        reps.append(msk.msk_surrogate_infer(s, base + i * P, P, U, flags, SURR_AUDIT_EVERY, SURR_TOL,
+                                            SURR_MAX_FAIL, stream))
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    # without the audit
+    a2, b2 = _events(torch, stream)
+    a2.record(stream)
+    for i in range(steps):
+        msk.msk_surrogate_infer(s, base + i * P, P, U, None, 0, SURR_TOL, SURR_MAX_FAIL, stream)
+    b2.record(stream)
+    torch.cuda.synchronize()
+    ms_noaudit = a2.elapsed_time(b2) / steps
+    # component breakdown (same work as one step)
+    X = torch.empty(P, 3 * SURR_CFG["steps"], dtype=torch.bfloat16, device="cuda")
+    C = torch.empty(P, SURR_CFG["rank"], device="cuda")
+    na = (P + SURR_AUDIT_EVERY - 1) // SURR_AUDIT_EVERY
+    Ua = torch.empty(na, n, device="cuda")
+
+    def timed(fn, reps=3):
+        fn()
+        a, b = _events(torch, stream)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    t_feat = timed(lambda: msk.msk_surrogate_features(s, base, P, X, stream))
+    t_mlp = timed(lambda: msk.msk_surrogate_forward(s, X, P, C, stream))
+    t_dec = timed(lambda: msk.msk_surrogate_decode(s, C, P, U, stream))
+    t_aud = timed(lambda: msk.msk_surrogate_reference(s, base, na, Ua, stream))
+    msk.msk_surrogate_sync_status(s, stream)
+    fails = sum(r[3] for r in reps)
+    audited = sum(r[0] for r in reps)
+    return {"ms": ms, "ms_no_audit": ms_noaudit, "paths_per_s": P / (ms / 1e3),
+            "paths_per_s_no_audit": P / (ms_noaudit / 1e3),
+            "audit": {"every": SURR_AUDIT_EVERY, "tol": SURR_TOL, "audited": audited, "failed": fails,
+                      "whole_batch_fallbacks": sum(r[4] for r in reps),
+                      "max_err": max(r[1] for r in reps), "mean_err": sum(r[2] for r in reps) / len(reps)},
+            "breakdown_ms": {"features": t_feat, "mlp": t_mlp, "decode": t_dec,
+                             "audit_magnus_contiguous": t_aud},
+            "decode_gbs": P * n * 4 / (t_dec / 1e3) / 1e9,
+            "mlp_tflops": P * MLP_FLOPS_PER_PATH / (t_mlp / 1e3) / 1e12}, U
 
 
 # ------------------------------------------------------------------ our implementation
@@ -338,6 +500,19 @@ def run_ours(a):
             comparators.setdefault("euler_fp32", {})[f"N{ne}"] = {
                 "paths_per_s": Pc / (msem / 1e3), "err": float(eem.cpu()[0])}
         comparators["magnus_fp32_sweep_err"] = {f"K{k}": v for k, v in sweep.items()}
+
+    # ---- learned surrogate of the same workload (setup untimed; own timed serve steps) ----------
+    if not a.no_surrogate and world == 1:
+        try:
+            s_sur, tinfo = train_surrogate(msk, torch, solver, K, stream)
+            acc = surrogate_accuracy(msk, torch, solver, s_sur, K, stream)
+            serve, _ = surrogate_serve(msk, torch, solver, s_sur, max(3, a.steps // 2), 2, stream)
+            comparators["surrogate"] = {"serve_paths": SURR_SERVE, **{k: serve[k] for k in (
+                "paths_per_s", "paths_per_s_no_audit", "ms", "audit", "breakdown_ms")},
+                "accuracy": acc, "training": tinfo}
+            msk.msk_surrogate_destroy(s_sur)
+        except Exception as exc:   # the Magnus line stands on its own
+            comparators["surrogate"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     # ---- roofline of the engine kernel ------------------------------------------------------
     peaks, peak_src = measured_peaks()
@@ -510,6 +685,138 @@ def run_batch(a):
         print(json.dumps(line), flush=True)
 
 
+def run_surrogate(a):
+    """The learned surrogate of the 128^2 workload: one step serves SURR_SERVE new paths
+    (features, BF16 network, tensor-core decode, 1% Magnus audit with fallback)."""
+    import numpy as np
+    import torch
+
+    import paper_2207_09776_b300 as msk
+    from paper_2207_09776_b300 import build as mbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    mbuild.build()
+    msk.load_library()
+    w = LANGEVIN_TRIG_128.with_(path_offset=rank * 10 ** 9)
+    solver = msk.Solver(w, device=local)
+    stream = torch.cuda.current_stream()
+    K = K_CANDIDATES[0]
+    s, tinfo = train_surrogate(msk, torch, solver, K, stream)
+    acc = surrogate_accuracy(msk, torch, solver, s, K, stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    serve, U = surrogate_serve(msk, torch, solver, s, a.steps, a.warmup, stream)
+    barrier()
+    clk = clocks.stop()
+    ms = serve["ms"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # end to end: the public call, solutions copied to pinned host memory every step
+    n = w.d * w.d
+    host = torch.empty(SURR_SERVE * n, dtype=torch.float32).pin_memory()
+    base = SURR_TRAIN + SURR_HELDOUT
+    msk.msk_surrogate_infer(s, base, SURR_SERVE, U, None, SURR_AUDIT_EVERY, SURR_TOL, SURR_MAX_FAIL, stream)
+    host.copy_(U.view(-1), non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch, stream)
+    n_e2e = max(2, a.steps // 3)
+    e0.record(stream)
+    for i in range(n_e2e):
+        msk.msk_surrogate_infer(s, base + i * SURR_SERVE, SURR_SERVE, U, None, SURR_AUDIT_EVERY, SURR_TOL,
+                                SURR_MAX_FAIL, stream)
+        host.copy_(U.view(-1), non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / n_e2e
+    # rooflines of the serve components
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    bf16 = float(peaks.get("bf16_tflops", 1800.0))
+    bd = serve["breakdown_ms"]
+    roofs = {
+        "decode": {"bound": "hbm", "achieved": serve["decode_gbs"], "peak": hbm, "unit": "GB/s",
+                   "frac": serve["decode_gbs"] / hbm, "traffic": None,
+                   "kernel": "gemm_tc_kernel<128, EPI_ADD_MEAN>",
+                   "algorithmic_bytes": SURR_SERVE * n * 4},
+        "mlp": {"bound": "tensor", "achieved": serve["mlp_tflops"], "peak": bf16, "unit": "TFLOP/s",
+                "frac": serve["mlp_tflops"] / bf16, "traffic": None, "kernel": "gemm_tc_kernel (5 layers)"},
+    }
+    dominant = max(("decode", "mlp"), key=lambda k: bd[k])
+    # CPU oracle of the same serve (features, bf16 network, decode) on a bounded sample
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        cpu = time_surrogate_oracle(msk, torch, solver, s, base, a.cpu_sample or 64)
+    line = {"metric": METRIC, "value": world * SURR_SERVE / (ms / 1e3), "unit": "paths/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "surrogate_" + w.name, "d": w.d, "serve_paths_per_gpu": SURR_SERVE,
+                       "network": "48 -> 4 x 512 GELU -> 64 (bf16 operands, fp32 accumulation)",
+                       "features": "dW, int W ds, int s dW per substep, K=16", "pod_rank": SURR_CFG["rank"],
+                       "audit": f"1 in {SURR_AUDIT_EVERY} paths re-solved by Magnus FP32 order {ORDER} K={K}; "
+                                f"replaced above {SURR_TOL} relative L2; whole batch above {SURR_MAX_FAIL:.0%} failures",
+                       "l2": "output 4.3 GB/step > 126 MB L2",
+                       "parallelism": f"replicas x{world} (path ranges)"},
+            "roofline": roofs[dominant], "roofline_components": roofs, "cpu_baseline": cpu,
+            "e2e": {"value": world * SURR_SERVE / (e2e_ms / 1e3), "unit": "paths/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": SURR_SERVE * n * 4},
+            "clocks": clk,
+            # per step: features, layers + 1 GEMMs, decode GEMM, audit (functionals, weights, engine, audit)
+            "gpu_launches": a.steps * (1 + (SURR_CFG["layers"] + 1) + 1 + 4),
+            "serve": serve, "accuracy": acc, "training": tinfo}
+    msk.msk_surrogate_destroy(s)
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def time_surrogate_oracle(msk, torch, solver, s, base, npaths):
+    """Paths/s of the CPU oracle serving the trained network: features from the
+    oracle's Brownian functionals, the bf16-rounded MLP, POD decode (float64)."""
+    import numpy as np
+    from oracle import surrogate as osg
+    w = solver.w
+    n = w.d * w.d
+    layers = SURR_CFG["layers"]
+    flat = torch.empty(msk.msk_surrogate_num_params(s), device="cuda")
+    msk.msk_surrogate_get_params(s, flat)
+    mean = torch.empty(n, device="cuda")
+    phi = torch.empty(SURR_CFG["rank"], n, device="cuda")
+    scale = msk.msk_surrogate_get_pod(s, mean, phi)
+    flat = flat.cpu().numpy()
+    dims = [48] + [SURR_CFG["hidden"]] * layers + [SURR_CFG["rank"]]
+    params = []
+    for l, (ow, ob) in enumerate(msk.msk_surrogate_param_layout(s, layers)):
+        params.append((flat[ow:ow + dims[l] * dims[l + 1]].reshape(dims[l + 1], dims[l]).astype(np.float64),
+                       flat[ob:ob + dims[l + 1]].astype(np.float64)))
+    m = mean.cpu().numpy().astype(np.float64)
+    P = phi.cpu().numpy().astype(np.float64)
+    wl = w.with_(path_offset=w.path_offset + base)
+    osg.features(wl, 16, range(2))   # warm
+    t0 = time.perf_counter()
+    X = osg.to_bf16(osg.features(wl, 16, range(npaths)))
+    c, _ = osg.forward(params, X, bf16=True)
+    u = m + scale * c @ P
+    dt = time.perf_counter() - t0
+    assert u.shape == (npaths, n)
+    return {"value": npaths / dt, "unit": "paths/s", "cores": host_cores(), "kind": "oracle",
+            "sample": f"{npaths} paths of the same serve (oracle features, bf16 MLP, POD decode), {dt:.1f} s"}
+
+
 def run_profile_case(a):
     """Two solves (functionals, weights, engine) of the workload on a small path count."""
     import torch
@@ -542,6 +849,8 @@ def main():
         run_reference(a)
     elif a.workload == "batch":
         run_batch(a)
+    elif a.workload == "surrogate":
+        run_surrogate(a)
     else:
         run_ours(a)
 
