@@ -68,6 +68,8 @@ struct msk_surrogate {
   double* aerr = nullptr;
   size_t aerr_bytes = 0;
   uint32_t* dev_err = nullptr;        // set by kernels whose bounded waits ran out
+  cudaStream_t aud = nullptr;         // audit stream (higher priority), overlaps the serve kernels
+  cudaEvent_t ev_in = nullptr, ev_aud = nullptr;
   std::map<std::tuple<uintptr_t, int, int, int, int>, CUtensorMap> maps;   // TMA descriptors
   std::string err;
 };
@@ -457,6 +459,9 @@ void free_all(msk_surrogate* s) {
     F(s->ih[i]);
   }
   F(s->dev_err);
+  if (s->ev_in) cudaEventDestroy(s->ev_in);
+  if (s->ev_aud) cudaEventDestroy(s->ev_aud);
+  if (s->aud) cudaStreamDestroy(s->aud);
   F(s->ws);
   F(s->partial);
   F(s->loss);
@@ -540,6 +545,13 @@ extern "C" msk_status msk_surrogate_create(msk_surrogate** out, msk_ctx* ctx, co
   if (st == MSK_OK) st = salloc(s, &s->w16, s->nparam, "bf16 parameters");
   if (st == MSK_OK) st = salloc(s, &s->w16T, s->nparam, "transposed bf16 weights");
   if (st == MSK_OK) st = salloc(s, &s->dev_err, 1, "error word");
+  if (st == MSK_OK) {
+    int lo = 0, hi = 0;
+    st = scuda(s, cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
+    if (st == MSK_OK) st = scuda(s, cudaStreamCreateWithPriority(&s->aud, cudaStreamNonBlocking, hi), "audit stream");
+  }
+  if (st == MSK_OK) st = scuda(s, cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming), "event");
+  if (st == MSK_OK) st = scuda(s, cudaEventCreateWithFlags(&s->ev_aud, cudaEventDisableTiming), "event");
   if (st == MSK_OK) st = scuda(s, cudaMemset(s->dev_err, 0, sizeof(uint32_t)), "error word");
   if (st == MSK_OK) st = salloc(s, &s->grad, s->nparam, "gradients");
   if (st == MSK_OK) st = salloc(s, &s->am, s->nparam, "Adam m");
@@ -985,25 +997,42 @@ extern "C" msk_status msk_surrogate_infer(msk_surrogate* s, int64_t path0, int64
   if (audit_every > 0)
     for (int64_t o = 0; o < paths; o += IB) na_total += (std::min(IB, paths - o) + audit_every - 1) / audit_every;
   if (st == MSK_OK && na_total > 0) st = sgrow(s, &s->aerr, &s->aerr_bytes, na_total * sizeof(double), "audit errors");
-  int64_t na_done = 0;
+  if (st == MSK_OK && na_total > 0)
+    st = sgrow(s, &s->uref, &s->uref_bytes, (size_t)na_total * s->n * sizeof(float), "audit solutions");
+  // The audit's Magnus solves depend only on the paths: they run on the audit
+  // stream (ordered after the caller's earlier work) while the serve kernels run
+  // on the caller's stream; the audit kernels join both.
+  if (st == MSK_OK && na_total > 0) {
+    st = scuda(s, cudaEventRecord(s->ev_in, stm), "event");
+    if (st == MSK_OK) st = scuda(s, cudaStreamWaitEvent(s->aud, s->ev_in, 0), "event");
+    int64_t na_off = 0;
+    for (int64_t o = 0; o < paths && st == MSK_OK; o += IB) {
+      const int64_t na = (std::min(IB, paths - o) + audit_every - 1) / audit_every;
+      st = reference_solve(s, first + (uint64_t)o, (uint64_t)audit_every, na, s->uref + (size_t)na_off * s->n, s->aud);
+      na_off += na;
+    }
+    if (st == MSK_OK) st = scuda(s, cudaEventRecord(s->ev_aud, s->aud), "event");
+  }
   for (int64_t o = 0; o < paths && st == MSK_OK; o += IB) {
     const int64_t P = std::min(IB, paths - o);
     float* U = U_dev + (size_t)o * s->n;
     st = features(s, first + (uint64_t)o, P, s->iX, stm);
     if (st == MSK_OK) st = forward_chain(s, s->iX, P, false, nullptr, stm, s->iA);
     if (st == MSK_OK) st = decode_split(s, P, U, stm);
-    if (st != MSK_OK || audit_every == 0) continue;
-    const int64_t na = (P + audit_every - 1) / audit_every;
-    st = sgrow(s, &s->uref, &s->uref_bytes, (size_t)na * s->n * sizeof(float), "audit solutions");
-    if (st == MSK_OK) st = reference_solve(s, first + (uint64_t)o, (uint64_t)audit_every, na, s->uref, stm);
-    if (st == MSK_OK) {
-      audit_kernel<<<(unsigned)na, 256, 0, stm>>>(U, s->uref, na, audit_every, s->n, tol, s->aerr + na_done,
-                                                  flags_dev ? flags_dev + o : nullptr);
-      st = scuda(s, cudaGetLastError(), "audit kernel");
-    }
-    na_done += na;
   }
   if (st != MSK_OK || audit_every == 0) return st;
+  st = scuda(s, cudaStreamWaitEvent(stm, s->ev_aud, 0), "event");
+  int64_t na_done = 0;
+  for (int64_t o = 0; o < paths && st == MSK_OK; o += IB) {
+    const int64_t P = std::min(IB, paths - o);
+    const int64_t na = (P + audit_every - 1) / audit_every;
+    audit_kernel<<<(unsigned)na, 256, 0, stm>>>(U_dev + (size_t)o * s->n, s->uref + (size_t)na_done * s->n, na,
+                                                audit_every, s->n, tol, s->aerr + na_done,
+                                                flags_dev ? flags_dev + o : nullptr);
+    st = scuda(s, cudaGetLastError(), "audit kernel");
+    na_done += na;
+  }
+  if (st != MSK_OK) return st;
   std::vector<double> e(na_total);
   st = scuda(s, cudaMemcpyAsync(e.data(), s->aerr, na_total * sizeof(double), cudaMemcpyDeviceToHost, stm), "copy");
   if (st == MSK_OK) st = scuda(s, cudaStreamSynchronize(stm), "audit sync");

@@ -16,17 +16,22 @@ using bf16 = __nv_bfloat16;
 // ------------------------------------------------------------------ features
 // Standard normals of fine cells 2j, 2j+1 in single precision: the same Philox
 // words as the double-precision generator (stream tag 0), uniforms
-// (hi + 1/2) 2^-32 from the high word of each pair, Box-Muller.
+// (hi + 1/2) 2^-32 from the high word of each pair, Box-Muller with the
+// hardware approximations of log2, sin and cos (absolute errors ~1e-6, far
+// below the bf16 rounding of the features).  The angle is evaluated in
+// (-pi, pi], where the hardware sin/cos are accurate: cos(2 pi u) =
+// -cos(2 pi (u - 1/2)) and sin(2 pi u) = -sin(2 pi (u - 1/2)).
 __device__ __forceinline__ void normal_pair_f32(uint64_t seed, uint64_t path, uint64_t j, float& z0, float& z1) {
   const uint4 w = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)path, (uint32_t)(path >> 32), 0u),
                                 make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
   const float u1 = fmaf((float)w.y, 0x1p-32f, 0x1p-33f);
   const float u2 = fmaf((float)w.w, 0x1p-32f, 0x1p-33f);
-  const float r = sqrtf(-2.0f * logf(u1));
+  const float r = sqrtf(-1.3862943611198906f * __log2f(u1));   // -2 ln u1 = -2 ln2 log2 u1
+  const float a = 6.283185307179586f * (u2 - 0.5f);
   float s, c;
-  sincospif(2.0f * u2, &s, &c);
-  z0 = r * c;
-  z1 = r * s;
+  __sincosf(a, &s, &c);
+  z0 = -r * c;
+  z1 = -r * s;
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
