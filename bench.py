@@ -392,7 +392,7 @@ def run_ours(a):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
 
     def step(i=None):
-        msk.msk_brownian_functionals(ctx, K, P, F, stream)
+        msk.msk_brownian_functionals_ex(ctx, K, P, msk.MSK_F32, F, stream)   # as msk_solve_magnus(F32)
         msk.msk_omega_weights(ctx, ORDER, K, P, msk.MSK_F32, F, Wt, stream)
         if i is not None:
             ev[i][0].record(stream)
@@ -832,7 +832,7 @@ def run_profile_case(a):
     Wt = torch.empty(P * K * msk.MSK_NWT, dtype=torch.float64, device="cuda")
     out = torch.empty(P * w.d * w.d, dtype=torch.float32, device="cuda")
     for _ in range(2):
-        msk.msk_brownian_functionals(s.ctx, K, P, F)
+        msk.msk_brownian_functionals_ex(s.ctx, K, P, msk.MSK_F32, F)
         msk.msk_omega_weights(s.ctx, ORDER, K, P, msk.MSK_F32, F, Wt)
         msk.msk_magnus_from_weights(s.ctx, K, P, msk.MSK_F32, Wt, out)
     torch.cuda.synchronize()

@@ -147,6 +147,16 @@ msk_status msk_philox_words(uint64_t seed, uint64_t path, uint32_t tag, int64_t 
 msk_status msk_brownian_functionals(msk_ctx* ctx, int steps, int64_t paths, double* F_dev,
                                     void* stream);
 
+/* As msk_brownian_functionals, with the standard normals of each Philox pair
+ * formed in double (normals = MSK_F64: identical to msk_brownian_functionals)
+ * or in single precision (MSK_F32: uniforms (hi + 1/2) 2^-32 from the high
+ * words, float Box-Muller; every functional still accumulated in double).
+ * The float solves (msk_solve_magnus / msk_solve_euler / msk_solve_magnus_noalloc
+ * with MSK_F32, batches, surrogate reference solutions) use MSK_F32 normals:
+ * they differ from the double ones by about 1e-7 relative. */
+msk_status msk_brownian_functionals_ex(msk_ctx* ctx, int steps, int64_t paths, int normals, double* F_dev,
+                                       void* stream);
+
 /* Brownian increments over `steps` equal steps: dW_dev[p * steps + n] (double). */
 msk_status msk_brownian_increments(msk_ctx* ctx, int steps, int64_t paths, double* dW_dev,
                                    void* stream);

@@ -75,6 +75,7 @@ SIGNATURES = {
     "msk_set_seed": (_INT, [_P, _U64, _U64, _I64, _DBL]),
     "msk_philox_words": (_INT, [_U64, _U64, ctypes.c_uint32, _I64, _I64, _P, _P]),
     "msk_brownian_functionals": (_INT, [_P, _INT, _I64, _P, _P]),
+    "msk_brownian_functionals_ex": (_INT, [_P, _INT, _I64, _INT, _P, _P]),
     "msk_brownian_increments": (_INT, [_P, _INT, _I64, _P, _P]),
     "msk_omega_weights": (_INT, [_P, _INT, _INT, _I64, _INT, _P, _P, _P]),
     "msk_apply_omega": (_INT, [_P, _P, _I64, _P, _P, _P]),
@@ -219,6 +220,12 @@ def msk_brownian_functionals(ctx, steps, paths, F, stream=None):
     import torch
     _need(F, paths * steps * MSK_NF, torch.float64, "F")
     _check(load_library().msk_brownian_functionals(ctx, steps, paths, _ptr(F), _stream(stream)), ctx)
+
+
+def msk_brownian_functionals_ex(ctx, steps, paths, normals, F, stream=None):
+    import torch
+    _need(F, paths * steps * MSK_NF, torch.float64, "F")
+    _check(load_library().msk_brownian_functionals_ex(ctx, steps, paths, normals, _ptr(F), _stream(stream)), ctx)
 
 
 def msk_brownian_increments(ctx, steps, paths, dW, stream=None):
@@ -511,11 +518,11 @@ class Solver:
         msk_explicit_solution(self.ctx, paths, u)
         return u
 
-    def functionals(self, steps, paths=None):
+    def functionals(self, steps, paths=None, normals=MSK_F64):
         import torch
         paths = self.w.paths if paths is None else paths
         F = self._empty(paths * steps * MSK_NF, torch.float64)
-        msk_brownian_functionals(self.ctx, steps, paths, F)
+        msk_brownian_functionals_ex(self.ctx, steps, paths, normals, F)
         return F.view(paths, steps, MSK_NF)
 
     def increments(self, steps, paths=None):
@@ -526,9 +533,10 @@ class Solver:
         return dW.view(paths, steps)
 
     def weights(self, order, steps, paths=None, precision=MSK_F64):
+        """Weights of the functionals the solve of this precision uses (float solves: float normals)."""
         import torch
         paths = self.w.paths if paths is None else paths
-        F = self.functionals(steps, paths)
+        F = self.functionals(steps, paths, normals=precision)
         Wt = self._empty(paths * steps * MSK_NWT, torch.float64)
         msk_omega_weights(self.ctx, order, steps, paths, precision, F, Wt)
         return Wt.view(paths, steps, MSK_NWT)

@@ -207,7 +207,7 @@ msk_status enqueue(msk_batch* b, cudaStream_t s) {
     if (it.paths == 0) continue;
     double* F = b->scratch + b->f_off[k];
     double* Wt = b->scratch + b->w_off[k];
-    st = launch_brownian(it.ctx, it.steps, it.paths, F, false, s);
+    st = launch_brownian(it.ctx, it.steps, it.paths, F, false, s, true);   // float solves: float normals
     if (st == MSK_OK) st = launch_omega(it.ctx, it.order, it.steps, it.paths, MSK_F32, F, Wt, s);
     if (st != MSK_OK) b->err = it.ctx->err;
   }

@@ -71,7 +71,7 @@ __device__ __forceinline__ double warp_excl_scan(double v, int lane) {
   return x - v;
 }
 
-template <bool FULL, bool TRIG>
+template <bool FULL, bool TRIG, bool NF32>
 __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, double* __restrict__ out) {
   __shared__ double stage[kWarps][32 * kChunk];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -100,7 +100,10 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
     double sw = 0.0, so = 0.0, z0 = 0.0, z1 = 0.0;
     for (int q = 0; q < cnt; ++q) {
       const int64_t fi = f0 + c0 + q;
-      if (q == 0 || (fi & 1) == 0) brownian_pair(a.seed, gpath, 0u, (uint64_t)(fi >> 1), z0, z1);
+      if (q == 0 || (fi & 1) == 0) {
+        if (NF32) brownian_pair_f32(a.seed, gpath, 0u, (uint64_t)(fi >> 1), z0, z1);
+        else brownian_pair(a.seed, gpath, 0u, (uint64_t)(fi >> 1), z0, z1);
+      }
       const double dw = sq * ((fi & 1) ? z1 : z0);
       st[q * 32 + lane] = dw;
       sw += dw;
@@ -193,8 +196,25 @@ static msk_status ensure_cell_table(msk_ctx* ctx, cudaStream_t stream) {
   return MSK_OK;
 }
 
+// One launch of the kernel variant for (functionals or increments, coefficient kind, normal precision).
+static void dispatch_brownian(const BrownArgs& a, bool full, bool trig, bool nf32, double* out, cudaStream_t stream) {
+  const int64_t n = a.paths * a.steps;
+  const unsigned blocks = (unsigned)((n + kWarps - 1) / kWarps);
+  const unsigned t = 32 * kWarps;
+  if (!full) {
+    if (nf32) brownian_kernel<false, false, true><<<blocks, t, 0, stream>>>(a, out);
+    else brownian_kernel<false, false, false><<<blocks, t, 0, stream>>>(a, out);
+  } else if (trig) {
+    if (nf32) brownian_kernel<true, true, true><<<blocks, t, 0, stream>>>(a, out);
+    else brownian_kernel<true, true, false><<<blocks, t, 0, stream>>>(a, out);
+  } else {
+    if (nf32) brownian_kernel<true, false, true><<<blocks, t, 0, stream>>>(a, out);
+    else brownian_kernel<true, false, false><<<blocks, t, 0, stream>>>(a, out);
+  }
+}
+
 msk_status launch_brownian(msk_ctx* ctx, int steps, int64_t paths, double* out, bool increments_only,
-                           cudaStream_t stream) {
+                           cudaStream_t stream, bool nf32) {
   const int64_t n = paths * steps;
   if (n == 0) return MSK_OK;
   const bool trig = ctx->coef.kind == MSK_COEF_TRIG;
@@ -204,16 +224,13 @@ msk_status launch_brownian(msk_ctx* ctx, int steps, int64_t paths, double* out, 
   }
   BrownArgs a{ctx->seed, ctx->path_offset, 1, ctx->n_fine, paths, steps, ctx->T, coef_dev(ctx->coef),
               trig ? ctx->tab : nullptr};
-  const unsigned blocks = (unsigned)((n + kWarps - 1) / kWarps);
-  if (increments_only) brownian_kernel<false, false><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
-  else if (trig) brownian_kernel<true, true><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
-  else brownian_kernel<true, false><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
+  dispatch_brownian(a, !increments_only, trig, nf32, out, stream);
   return msk_cuda(ctx, cudaGetLastError(), "brownian kernel");
 }
 
 // Functionals of the global paths first, first + stride, ... (paths of them).
 msk_status launch_brownian_strided(msk_ctx* ctx, int steps, int64_t paths, double* out, uint64_t first,
-                                   uint64_t stride, cudaStream_t stream) {
+                                   uint64_t stride, cudaStream_t stream, bool nf32) {
   const int64_t n = paths * steps;
   if (n == 0) return MSK_OK;
   const bool trig = ctx->coef.kind == MSK_COEF_TRIG;
@@ -223,9 +240,7 @@ msk_status launch_brownian_strided(msk_ctx* ctx, int steps, int64_t paths, doubl
   }
   BrownArgs a{ctx->seed, first, stride, ctx->n_fine, paths, steps, ctx->T, coef_dev(ctx->coef),
               trig ? ctx->tab : nullptr};
-  const unsigned blocks = (unsigned)((n + kWarps - 1) / kWarps);
-  if (trig) brownian_kernel<true, true><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
-  else brownian_kernel<true, false><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
+  dispatch_brownian(a, true, trig, nf32, out, stream);
   return msk_cuda(ctx, cudaGetLastError(), "brownian kernel");
 }
 
@@ -238,15 +253,13 @@ msk_status launch_cell_table_into(msk_ctx* ctx, double* tab, cudaStream_t stream
 }
 
 msk_status launch_brownian_with_table(msk_ctx* ctx, int steps, int64_t paths, double* out, const double* tab,
-                                      cudaStream_t stream) {
+                                      cudaStream_t stream, bool nf32) {
   const int64_t n = paths * steps;
   if (n == 0) return MSK_OK;
   const bool trig = ctx->coef.kind == MSK_COEF_TRIG;
   BrownArgs a{ctx->seed, ctx->path_offset, 1, ctx->n_fine, paths, steps, ctx->T, coef_dev(ctx->coef),
               trig ? tab : nullptr};
-  const unsigned blocks = (unsigned)((n + kWarps - 1) / kWarps);
-  if (trig) brownian_kernel<true, true><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
-  else brownian_kernel<true, false><<<blocks, 32 * kWarps, 0, stream>>>(a, out);
+  dispatch_brownian(a, true, trig, nf32, out, stream);
   return msk_cuda(ctx, cudaGetLastError(), "brownian kernel");
 }
 

@@ -162,6 +162,19 @@ extern "C" msk_status msk_brownian_functionals(msk_ctx* ctx, int steps, int64_t 
   return launch_brownian(ctx, steps, paths, F_dev, false, (cudaStream_t)stream);
 }
 
+extern "C" msk_status msk_brownian_functionals_ex(msk_ctx* ctx, int steps, int64_t paths, int normals, double* F_dev,
+                                                 void* stream) {
+  if (!ctx) return MSK_ERR_ARG;
+  if (normals != MSK_F64 && normals != MSK_F32) return msk_fail(ctx, MSK_ERR_ARG, "normals must be MSK_F64 or MSK_F32");
+  msk_status st = check_steps(ctx, steps, paths);
+  if (st != MSK_OK) return st;
+  if (paths == 0) return MSK_OK;
+  if (!F_dev) return msk_fail(ctx, MSK_ERR_ARG, "null buffer");
+  st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
+  if (st != MSK_OK) return st;
+  return launch_brownian(ctx, steps, paths, F_dev, false, (cudaStream_t)stream, normals == MSK_F32);
+}
+
 extern "C" msk_status msk_brownian_increments(msk_ctx* ctx, int steps, int64_t paths, double* dW_dev, void* stream) {
   if (!ctx) return MSK_ERR_ARG;
   msk_status st = check_steps(ctx, steps, paths);
@@ -190,7 +203,7 @@ extern "C" msk_status msk_solve_magnus(msk_ctx* ctx, int order, int steps, int64
   if (st != MSK_OK) return st;
   double* F = reinterpret_cast<double*>(ctx->scratch);
   double* Wt = F + nF;
-  st = launch_brownian(ctx, steps, paths, F, false, s);
+  st = launch_brownian(ctx, steps, paths, F, false, s, precision == MSK_F32);
   if (st == MSK_OK) st = launch_omega(ctx, order, steps, paths, precision, F, Wt, s);
   if (st == MSK_OK) st = launch_engine(ctx, false, steps, paths, precision, Wt, nullptr, u_out_dev, path_status_dev, s);
   return st;
@@ -210,7 +223,7 @@ extern "C" msk_status msk_solve_euler(msk_ctx* ctx, int steps, int64_t paths, in
   st = msk_ensure_scratch(ctx, (size_t)paths * steps * sizeof(double));
   if (st != MSK_OK) return st;
   double* dW = reinterpret_cast<double*>(ctx->scratch);
-  st = launch_brownian(ctx, steps, paths, dW, true, s);
+  st = launch_brownian(ctx, steps, paths, dW, true, s, precision == MSK_F32);
   if (st == MSK_OK) st = launch_engine(ctx, true, steps, paths, precision, nullptr, dW, u_out_dev, path_status_dev, s);
   return st;
 }

@@ -65,10 +65,12 @@ bool msk_supported_d(int d);
 // Launchers implemented in the .cu files (all asynchronous on `stream`).
 msk_status launch_band_tables(msk_ctx* ctx, cudaStream_t stream);
 msk_status launch_gaussian_u0(msk_ctx* ctx, cudaStream_t stream);
+// nf32: normals of each Philox pair formed in single precision (the float
+// solves); the functionals are accumulated in double either way.
 msk_status launch_brownian(msk_ctx* ctx, int steps, int64_t paths, double* out, bool increments_only,
-                           cudaStream_t stream);
+                           cudaStream_t stream, bool nf32 = false);
 msk_status launch_brownian_strided(msk_ctx* ctx, int steps, int64_t paths, double* out, uint64_t first,
-                                   uint64_t stride, cudaStream_t stream);
+                                   uint64_t stride, cudaStream_t stream, bool nf32 = false);
 msk_status launch_omega(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
                         const double* F, double* Wt, cudaStream_t stream);
 msk_status launch_engine(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,

@@ -32,7 +32,7 @@
 
 msk_status launch_cell_table_into(msk_ctx* ctx, double* tab, cudaStream_t stream);
 msk_status launch_brownian_with_table(msk_ctx* ctx, int steps, int64_t paths, double* out, const double* tab,
-                                      cudaStream_t stream);
+                                      cudaStream_t stream, bool nf32);
 
 namespace {
 
@@ -90,7 +90,7 @@ extern "C" msk_status msk_solve_magnus_noalloc(msk_ctx* ctx, int order, int step
   double* Wt = F + nF;
   double* tab = Wt + nW;
   if (trig) st = launch_cell_table_into(ctx, tab, s);
-  if (st == MSK_OK) st = launch_brownian_with_table(ctx, steps, paths, F, tab, s);
+  if (st == MSK_OK) st = launch_brownian_with_table(ctx, steps, paths, F, tab, s, precision == MSK_F32);
   if (st == MSK_OK) st = launch_omega(ctx, order, steps, paths, precision, F, Wt, s);
   if (st == MSK_OK) st = launch_engine(ctx, false, steps, paths, precision, Wt, nullptr, u_out_dev, path_status_dev, s);
   return st;

@@ -388,7 +388,7 @@ msk_status reference_solve(msk_surrogate* s, uint64_t first, uint64_t stride, in
     if (st != MSK_OK) return st;
     double* F = reinterpret_cast<double*>(s->rs);
     double* Wt = F + nF;
-    st = from_ctx(s, launch_brownian_strided(ctx, steps, P, F, first + (uint64_t)o * stride, stride, stream));
+    st = from_ctx(s, launch_brownian_strided(ctx, steps, P, F, first + (uint64_t)o * stride, stride, stream, true));
     if (st == MSK_OK) st = from_ctx(s, launch_omega(ctx, order, steps, P, MSK_F32, F, Wt, stream));
     if (st == MSK_OK)
       st = from_ctx(s, launch_engine(ctx, false, steps, P, MSK_F32, Wt, nullptr, U + (size_t)o * s->n, nullptr, stream));

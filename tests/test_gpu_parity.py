@@ -66,6 +66,31 @@ def test_brownian_functionals(w, K):
     s.close()
 
 
+@pytest.mark.parametrize("w,K", [(LANGEVIN_TRIG_128.with_(paths=4, n_fine=2048), 16),
+                                 (LANGEVIN_32.with_(paths=3, n_fine=999), 3)])
+def test_brownian_functionals_float_normals(w, K):
+    """The float solves' functionals: float Box-Muller, double accumulation -- within
+    ~1e-6 of the double-normal functionals; the double variant is the plain call."""
+    s = solver(w)
+    F = torch.empty(w.paths * K * msk.MSK_NF, dtype=torch.float64, device="cuda")
+    msk.msk_brownian_functionals(s.ctx, K, w.paths, F)
+    F64 = s.functionals(K, normals=msk.MSK_F64)
+    F32 = s.functionals(K, normals=msk.MSK_F32).cpu().numpy()
+    assert torch.equal(F.view_as(F64), F64)
+    F64 = F64.cpu().numpy()
+    scale = np.abs(F64).max(axis=(0, 1))
+    np.testing.assert_allclose(F32, F64, rtol=0, atol=1e-6 * scale.max())
+    assert not np.array_equal(F32, F64)
+    # a float solve is functionals (float normals) -> weights -> engine, bit for bit
+    u = s.magnus(3, K, precision=msk.MSK_F32)
+    Wt = s.weights(3, K, precision=msk.MSK_F32)
+    u2 = s.state(w.paths, msk.MSK_F32)
+    msk.msk_magnus_from_weights(s.ctx, K, w.paths, msk.MSK_F32, Wt, u2)
+    torch.cuda.synchronize()
+    assert torch.equal(u, u2)
+    s.close()
+
+
 # ---------------------------------------------------------------- widened-stencil operator
 
 @pytest.mark.parametrize("w,order,K", [(LANGEVIN_32.with_(paths=3), 3, 1),
