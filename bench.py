@@ -60,6 +60,10 @@ def parse():
                         "in ratio 4:2:1 of 16384 paths in one persistent launch; surrogate: the learned "
                         "surrogate of the 128^2 workload served 65536 paths per step with a 1%% Magnus audit")
     p.add_argument("--no-surrogate", action="store_true", help="skip the surrogate summary of the default line")
+    p.add_argument("--surrogate-profile-case", type=int, default=0, metavar="PATHS",
+                   help="serve PATHS paths twice with an untrained surrogate of the 128^2 workload (random "
+                        "weights, random orthonormal POD basis; features, network, decode; no audit) -- a "
+                        "small case for ncu captures of the surrogate kernels -- and exit")
     p.add_argument("--profile-case", type=int, default=0, metavar="PATHS",
                    help="run two plain solves of the benchmark workload with PATHS paths at K = 8 "
                         "(a small case for ncu captures) and exit")
@@ -817,6 +821,33 @@ def time_surrogate_oracle(msk, torch, solver, s, base, npaths):
             "sample": f"{npaths} paths of the same serve (oracle features, bf16 MLP, POD decode), {dt:.1f} s"}
 
 
+def run_surrogate_profile_case(a):
+    """Two serves of PATHS paths by a surrogate with random parameters (kernel timing only)."""
+    import torch
+
+    import paper_2207_09776_b300 as msk
+    from paper_2207_09776_b300 import build as mbuild
+    mbuild.build()
+    msk.load_library()
+    P = a.surrogate_profile_case
+    w = LANGEVIN_TRIG_128
+    solver = msk.Solver(w)
+    cfg = dict(SURR_CFG, infer_batch=P)
+    s = msk.msk_surrogate_create(solver.ctx, ref_order=ORDER, ref_steps=K_CANDIDATES[0], init_seed=1, **cfg)
+    n, r = w.d * w.d, SURR_CFG["rank"]
+    g = torch.Generator(device="cuda").manual_seed(3)
+    phi = torch.linalg.qr(torch.randn(n, r, device="cuda", generator=g))[0].T.contiguous()
+    mean = torch.randn(n, device="cuda", generator=g) * 1e-3
+    msk.msk_surrogate_set_pod(s, mean, phi, 1e-2)
+    U = torch.empty(P, n, device="cuda")
+    for _ in range(2):
+        msk.msk_surrogate_infer(s, 0, P, U)
+    msk.msk_surrogate_sync_status(s)
+    print(json.dumps({"surrogate_profile_case": P, "finite": bool(torch.isfinite(U).all())}))
+    msk.msk_surrogate_destroy(s)
+    solver.close()
+
+
 def run_profile_case(a):
     """Two solves (functionals, weights, engine) of the workload on a small path count."""
     import torch
@@ -844,6 +875,9 @@ def main():
     a = parse()
     if a.profile_case:
         run_profile_case(a)
+        return
+    if a.surrogate_profile_case:
+        run_surrogate_profile_case(a)
         return
     if a.impl == "reference":
         run_reference(a)

@@ -55,19 +55,24 @@ __global__ void __launch_bounds__(256) features_kernel(uint64_t seed, uint64_t f
   const int64_t p = idx / K;
   const int k = (int)(idx % K);
   const uint64_t gpath = first + (uint64_t)p * stride;
-  const int64_t m = n_fine / K, c0 = (int64_t)k * m, c1 = c0 + m;
+  // 32-bit cell arithmetic (n_fine <= 2^32): a 64-bit integer to float
+  // conversion would run on the double-precision pipe.
+  const uint32_t m = (uint32_t)(n_fine / K), c0 = (uint32_t)k * m;
+  const int odd = (int)(c0 & 1u);                     // cell c0 is the second of its pair
+  const uint32_t npair = (m + odd + 1) >> 1;          // pairs touching [c0, c0 + m)
   float A = 0.f, B = 0.f;
-  for (int64_t j = (c0 >> 1) + lane; 2 * j < c1; j += 32) {
+  for (uint32_t q = lane; q < npair; q += 32) {
     float z0, z1;
-    normal_pair_f32(seed, gpath, (uint64_t)j, z0, z1);
-    const int64_t a = 2 * j;
-    if (a >= c0) {
+    normal_pair_f32(seed, gpath, (uint64_t)((c0 >> 1) + q), z0, z1);
+    const int i0 = 2 * (int)q - odd;                  // cell index within the step of z0
+    const float t0 = (float)i0 + 0.5f;
+    if (i0 >= 0) {
       A += z0;
-      B = fmaf(z0, (float)(a - c0) + 0.5f, B);
+      B = fmaf(z0, t0, B);
     }
-    if (a + 1 < c1) {
+    if (i0 + 1 < (int)m) {
       A += z1;
-      B = fmaf(z1, (float)(a + 1 - c0) + 0.5f, B);
+      B = fmaf(z1, t0 + 1.0f, B);
     }
   }
   A = warp_sum_f(A);
