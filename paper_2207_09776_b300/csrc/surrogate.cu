@@ -137,32 +137,40 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// TMA descriptor of a K-major bf16 operand [rows][cols] (row stride ld
-// elements), box of box_rows x 64 with the 128-byte swizzle; cached per shape.
-msk_status tensor_map(msk_surrogate* s, const bf16* ptr, int rows, int cols, int ld, int box_rows, CUtensorMap* out) {
-  const auto key = std::make_tuple(reinterpret_cast<uintptr_t>(ptr), rows, cols, ld, box_rows);
+// TMA descriptor of a row-major matrix [rows][cols] (row stride ld elements of
+// esize bytes), box of box_rows x box_cols (box_cols * esize = 128 bytes) with
+// the 128-byte swizzle; cached per shape.  bf16 operands use 64-column boxes;
+// the decode's float output uses 32 x 32 boxes.
+msk_status tensor_map_any(msk_surrogate* s, const void* ptr, int esize, int rows, int cols, int ld, int box_cols,
+                          int box_rows, CUtensorMap* out) {
+  const auto key = std::make_tuple(reinterpret_cast<uintptr_t>(ptr), rows, cols, ld * esize, box_rows);
   const auto it = s->maps.find(key);
   if (it != s->maps.end()) {
     *out = it->second;
     return MSK_OK;
   }
-  if (!aligned16(ptr) || ld % 8 != 0 || ld < cols)
-    return sfail(s, MSK_ERR_UNSUPPORTED, "GEMM operand must be 16-byte aligned with a row stride of 8k elements");
+  if (!aligned16(ptr) || ((int64_t)ld * esize) % 16 != 0 || ld < cols)
+    return sfail(s, MSK_ERR_UNSUPPORTED, "GEMM operand must be 16-byte aligned with a 16-byte multiple row stride");
   const EncodeTiledFn fn = encode_tiled();
   if (!fn) return sfail(s, MSK_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(bf16)};
-  const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * esize};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   CUtensorMap m;
-  const CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(ptr), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  const CUresult r = fn(&m, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                        const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return sfail(s, MSK_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   if (s->maps.size() > 4096) s->maps.clear();
   s->maps.emplace(key, m);
   *out = m;
   return MSK_OK;
+}
+
+msk_status tensor_map(msk_surrogate* s, const bf16* ptr, int rows, int cols, int ld, int box_rows, CUtensorMap* out) {
+  return tensor_map_any(s, ptr, (int)sizeof(bf16), rows, cols, ld, TC_BK, box_rows, out);
 }
 
 struct TcOut {
@@ -178,17 +186,27 @@ struct TcOut {
 };
 
 constexpr int kStages = 4;        // pipeline depth of the MLP GEMMs
-constexpr int kDecodeStages = 3;  // decode: K = 3r <= 192, two CTAs per SM
+constexpr int kDecodeStages = 3;  // decode: K = 3r <= 192 is three k-blocks per tile
 
+// Persistent launch: as many CTAs as fit (at most one per tile).
 template <int BN, int EPI, int ST>
-void launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& g, dim3 grid, cudaStream_t stream) {
-  gemm_tc_kernel<BN, EPI, ST><<<grid, 128, tc_smem_bytes(BN, ST), stream>>>(ta, tb, g);
+cudaError_t launch_tc(msk_surrogate* s, const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc,
+                      const TcArgs& g, int tiles_m, int tiles_n, int splits, cudaStream_t stream) {
+  auto kern = gemm_tc_kernel<BN, EPI, ST>;
+  const size_t smem = tc_smem_bytes(BN, ST, EPI);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t ntiles = (int64_t)tiles_m * tiles_n * splits;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)std::max(per_sm, 1) * s->ctx->num_sms));
+  kern<<<grid, TC_THREADS, smem, stream>>>(ta, tb, tc, g, tiles_m, tiles_n, splits);
+  return cudaGetLastError();
 }
 
 template <int BN, int EPI, int ST>
 cudaError_t tc_attribute() {
   return cudaFuncSetAttribute(gemm_tc_kernel<BN, EPI, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tc_smem_bytes(BN, ST));
+                              (int)tc_smem_bytes(BN, ST, EPI));
 }
 
 template <int BN>
@@ -214,7 +232,6 @@ msk_status gemm(msk_surrogate* s, const bf16* A, int lda, int M, const bf16* B, 
   const int sms = std::max(1, s->ctx->num_sms);
   const int bm = (M + TC_BM - 1) / TC_BM;
   int BN = N > 128 ? 256 : (N > 64 ? 128 : 64);
-  if (EPI == EPI_ADD_MEAN) BN = std::min(BN, 128);
   while (BN > 64 && (int64_t)bm * ((N + BN - 1) / BN) < sms) BN /= 2;
   const int bn = (N + BN - 1) / BN;
   const auto rup = [](int64_t x, int64_t m) { return (x + m - 1) / m * m; };
@@ -229,9 +246,17 @@ msk_status gemm(msk_surrogate* s, const bf16* A, int lda, int M, const bf16* B, 
       kchunk = (int)rup(K, TC_BK);
     }
   }
-  CUtensorMap ta, tb;
+  CUtensorMap ta, tb, tc;
   msk_status st = tensor_map(s, A, M, K, lda, TC_BM, &ta);
   if (st == MSK_OK) st = tensor_map(s, B, N, K, ldb, BN, &tb);
+  if (st == MSK_OK) {
+    if (EPI == EPI_ADD_MEAN) {   // float output written by 32 x 32 TMA stores
+      if (N % 32 != 0) return sfail(s, MSK_ERR_UNSUPPORTED, "decode width must be a multiple of 32");
+      st = tensor_map_any(s, o.C, (int)sizeof(float), M, N, o.ldc, 32, 32, &tc);
+    } else {
+      tc = ta;   // unused
+    }
+  }
   if (st != MSK_OK) return st;
   TcArgs g{};
   g.M = M;
@@ -253,12 +278,12 @@ msk_status gemm(msk_surrogate* s, const bf16* A, int lda, int M, const bf16* B, 
     g.ldc = N;
     g.split_stride = (int64_t)M * N;
   }
-  const dim3 grid(bn, bm, splits);
   constexpr int ST = EPI == EPI_ADD_MEAN ? kDecodeStages : kStages;
-  if (BN == 256) launch_tc<256, EPI, ST>(ta, tb, g, grid, stream);
-  else if (BN == 128) launch_tc<128, EPI, ST>(ta, tb, g, grid, stream);
-  else launch_tc<64, EPI, ST>(ta, tb, g, grid, stream);
-  st = scuda(s, cudaGetLastError(), "tensor-core GEMM");
+  cudaError_t e;
+  if (BN == 256) e = launch_tc<256, EPI, ST>(s, ta, tb, tc, g, bm, bn, splits, stream);
+  else if (BN == 128) e = launch_tc<128, EPI, ST>(s, ta, tb, tc, g, bm, bn, splits, stream);
+  else e = launch_tc<64, EPI, ST>(s, ta, tb, tc, g, bm, bn, splits, stream);
+  st = scuda(s, e, "tensor-core GEMM");
   if (st != MSK_OK || splits == 1) return st;
   reduce_splits_kernel<<<blocks_for((int64_t)M * N), 256, 0, stream>>>(s->ws, splits, (int64_t)M * N, o.C);
   return scuda(s, cudaGetLastError(), "split-K reduction");

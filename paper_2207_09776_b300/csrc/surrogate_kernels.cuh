@@ -94,13 +94,11 @@ __device__ __forceinline__ float gelu_prime(float z) {
 
 // ------------------------------------------------------------------ BF16 GEMM (tcgen05)
 // C[M][N] = sum_k A[m][k] B[n][k]: both operands K-major bf16 in global memory
-// (row strides multiples of 8 elements), fp32 accumulation in tensor memory.
-// One 128 x BN output tile per CTA of 4 warps: warp 0 lane 0 streams 128 x 64
-// and BN x 64 operand tiles by TMA (128-byte swizzle) through a 4-stage
-// shared-memory ring, warp 1 lane 0 issues tcgen05.mma (128 x BN x 16 per
-// instruction) into a BN-column TMEM accumulator, and all four warps run the
-// epilogue (warp w owns TMEM lanes = tile rows 32w .. 32w + 31).
-// blockIdx.z selects a K range (split-K; EPI_F32 writes C + z * split_stride).
+// (row strides multiples of 8 elements), fp32 accumulation in tensor memory,
+// 128 x BN output tiles fed by TMA (128-byte swizzle) and tcgen05.mma
+// (128 x BN x 16 per instruction); see gemm_tc_kernel below.  With split-K the
+// K range is divided into `splits` parts and EPI_F32 writes part z to
+// C + z * split_stride.
 enum { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_GELU = 2, EPI_GELU_BWD = 3, EPI_BIAS_SPLIT = 4, EPI_ADD_MEAN = 5 };
 
 struct TcArgs {
@@ -122,8 +120,12 @@ struct TcArgs {
 constexpr int TC_BM = 128, TC_BK = 64;
 constexpr uint32_t kTcWaitLimit = 1u << 24;   // polls of one mbarrier before giving up
 
-__host__ __device__ constexpr size_t tc_smem_bytes(int BN, int stages) {
-  return 1024 + (size_t)stages * (TC_BM + BN) * TC_BK * 2 + (2 * stages + 1) * 8 + 16;
+// EPI_ADD_MEAN stages each epilogue warp's 32 x 32 float chunks in two 4 KB
+// buffers (128-byte swizzle) for TMA stores.
+constexpr int TC_STAGE_BYTES = 8 * 2 * 4096;
+
+__host__ __device__ constexpr size_t tc_smem_bytes(int BN, int stages, int epi) {
+  return 1024 + (size_t)stages * (TC_BM + BN) * TC_BK * 2 + 1024 + (epi == EPI_ADD_MEAN ? TC_STAGE_BYTES : 0);
 }
 
 __device__ __forceinline__ void store_row_f32(float* dst, const float (&v)[32], int nn) {
@@ -177,9 +179,9 @@ __device__ __forceinline__ void store_col_bf16(bf16* CT, int ldct, int nb, int m
 }
 
 template <int EPI>
-__device__ __forceinline__ void tc_epilogue_chunk(const TcArgs& g, float (&v)[32], int m, int nb, int nn) {
+__device__ __forceinline__ void tc_epilogue_chunk(const TcArgs& g, float (&v)[32], int m, int nb, int nn, int z) {
   if (EPI == EPI_F32) {
-    store_row_f32(g.C + (size_t)blockIdx.z * g.split_stride + (size_t)m * g.ldc + nb, v, nn);
+    store_row_f32(g.C + (size_t)z * g.split_stride + (size_t)m * g.ldc + nb, v, nn);
   } else if (EPI == EPI_BIAS_F32) {
 #pragma unroll
     for (int j = 0; j < 32; ++j)
@@ -239,9 +241,31 @@ __device__ __forceinline__ void tc_epilogue_chunk(const TcArgs& g, float (&v)[32
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_u32(bar)) : "memory");
+}
+
+// Persistent, warp-specialised tcgen05 GEMM.  The grid holds at most one CTA
+// per resident slot; CTA b computes tiles b, b + gridDim.x, ... of the
+// (split, m-tile, n-tile) enumeration (n fastest).  Warps:
+//   0       TMA producer (lane 0): 128 x 64 and BN x 64 operand boxes through a
+//           TC_STAGES-deep shared-memory ring (full/empty mbarriers);
+//   1       TMEM owner and MMA issuer (lane 0): tcgen05.mma into one of two
+//           BN-column accumulators (double buffer), commit to tmem_full[b];
+//   2 .. 9  epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its tile rows)
+//           and half of the tile's columns, then frees the accumulator
+//           (tmem_empty[b], eight arrivals), so the next tile's MMAs overlap
+//           this tile's epilogue.
+// Every mbarrier wait is bounded (kTcWaitLimit polls); on expiry the thread sets
+// g.err and the pipeline drains without further waits.
+constexpr int TC_THREADS = 320;
+
 template <int BN, int EPI, int TC_STAGES>
-__global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                          const __grid_constant__ CUtensorMap tmB, const TcArgs g) {
+__global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                 const __grid_constant__ CUtensorMap tmB,
+                                                                 const __grid_constant__ CUtensorMap tmC,
+                                                                 const TcArgs g, int tiles_m, int tiles_n,
+                                                                 int splits) {
   static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
   static_assert(TC_STAGES >= 2 && TC_STAGES <= 6, "pipeline depth");
   constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
@@ -251,93 +275,160 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const __grid_constant__
   uint8_t* sB = base + TC_STAGES * A_BYTES;
   uint64_t* full = reinterpret_cast<uint64_t*>(sB + TC_STAGES * B_BYTES);
   uint64_t* empty = full + TC_STAGES;
-  uint64_t* done = empty + TC_STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* tfull = empty + TC_STAGES;     // [2]
+  uint64_t* tempty = tfull + 2;            // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint8_t* stage_out = sB + TC_STAGES * B_BYTES + 1024;   // EPI_ADD_MEAN: [8 warps][2][32 rows x 128 B]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * BN;
-  const int kbeg = blockIdx.z * g.kchunk;
-  const int kend = min(g.K, kbeg + g.kchunk);
-  const int nk = (kend - kbeg + TC_BK - 1) / TC_BK;   // >= 1: every split owns a non-empty K range
+  const int per_split = tiles_m * tiles_n, ntiles = per_split * splits;
 
   if (threadIdx.x == 0) {
     umma::prefetch_tensormap(&tmA);
     umma::prefetch_tensormap(&tmB);
+    if (EPI == EPI_ADD_MEAN) umma::prefetch_tensormap(&tmC);
     for (int s = 0; s < TC_STAGES; ++s) {
       umma::mbar_init(full + s, 1);
       umma::mbar_init(empty + s, 1);
     }
-    umma::mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      umma::mbar_init(tfull + b, 1);
+      umma::mbar_init(tempty + b, 8);
+    }
     umma::fence_barrier_init();
   }
-  if (warp == 0) umma::tmem_alloc(tmem_slot, BN);
+  if (warp == 1) umma::tmem_alloc(tmem_slot, 2 * BN);
   umma::tc_fence_before();
   __syncthreads();
   umma::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  bool fail = false;
-  if (warp == 0 && lane == 0) {
-    // ---- TMA producer
-    int issued = 0;
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % TC_STAGES;
-      if (!umma::mbar_wait(empty + s, ((it / TC_STAGES) & 1) ^ 1, kTcWaitLimit)) {
-        fail = true;
-        break;
-      }
-      umma::mbar_arrive_expect_tx(full + s, A_BYTES + B_BYTES);
-      const int kc = kbeg + it * TC_BK;
-      umma::tma_load_2d(sA + s * A_BYTES, &tmA, full + s, kc, m0);
-      umma::tma_load_2d(sB + s * B_BYTES, &tmB, full + s, kc, n0);
-      issued = it + 1;
-    }
-    // the last load of every stage has landed before the CTA can leave
-    for (int it = max(0, issued - TC_STAGES); it < issued; ++it)
-      if (!umma::mbar_wait(full + it % TC_STAGES, (it / TC_STAGES) & 1, kTcWaitLimit)) fail = true;
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
-    constexpr uint32_t idesc = umma::idesc_bf16_f32(TC_BM, BN);
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % TC_STAGES;
-      if (!umma::mbar_wait(full + s, (it / TC_STAGES) & 1, kTcWaitLimit)) {
-        fail = true;
-        break;
-      }
-      umma::tc_fence_after();
-      const uint64_t da = umma::desc_sw128_kmajor(sA + s * A_BYTES);
-      const uint64_t db = umma::desc_sw128_kmajor(sB + s * B_BYTES);
-#pragma unroll
-      for (int kk = 0; kk < TC_BK / 16; ++kk)   // advance 16 bf16 = 32 bytes along K inside the swizzle atom
-        umma::mma_bf16(tmem, da + 2 * kk, db + 2 * kk, idesc, (it | kk) ? 1u : 0u);
-      umma::mma_commit(empty + s);
-    }
-    umma::mma_commit(done);
-  }
-  __syncwarp();
-  if (fail) atomicOr(g.err, 1u);
+  auto k_range = [&](int z, int& kbeg, int& nk) {
+    kbeg = z * g.kchunk;
+    const int kend = min(g.K, kbeg + g.kchunk);
+    nk = (kend - kbeg + TC_BK - 1) / TC_BK;   // >= 1: every split owns a non-empty K range
+  };
 
-  // ---- epilogue: TMEM -> registers -> global
-  const bool ready = __all_sync(0xffffffffu, umma::mbar_wait(done, 0, kTcWaitLimit));
-  umma::tc_fence_after();
-  if (!ready) {
-    if (lane == 0) atomicOr(g.err, 1u);
-  } else {
-    const int m = m0 + warp * 32 + lane;
-#pragma unroll 1
-    for (int c = 0; c < BN / 32; ++c) {
-      const int nb = n0 + c * 32;
-      if (nb >= g.N) break;                                   // same for the whole CTA
-      uint32_t r[32];
-      umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
-      float v[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-      if (m < g.M) tc_epilogue_chunk<EPI>(g, v, m, nb, min(32, g.N - nb));
+  bool fail = false;
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      uint32_t it = 0;
+      for (int t = blockIdx.x; t < ntiles && !fail; t += gridDim.x) {
+        const int z = t / per_split, rem = t % per_split;
+        const int m0 = (rem / tiles_n) * TC_BM, n0 = (rem % tiles_n) * BN;
+        int kbeg, nk;
+        k_range(z, kbeg, nk);
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % TC_STAGES;
+          if (!umma::mbar_wait(empty + s, ((it / TC_STAGES) & 1) ^ 1, kTcWaitLimit)) {
+            fail = true;
+            break;
+          }
+          umma::mbar_arrive_expect_tx(full + s, A_BYTES + B_BYTES);
+          const int kc = kbeg + kb * TC_BK;
+          umma::tma_load_2d(sA + s * A_BYTES, &tmA, full + s, kc, m0);
+          umma::tma_load_2d(sB + s * B_BYTES, &tmB, full + s, kc, n0);
+        }
+      }
+      // the last load of every stage has landed before the CTA can leave
+      for (uint32_t j = it > (uint32_t)TC_STAGES ? it - TC_STAGES : 0; j < it; ++j)
+        if (!umma::mbar_wait(full + j % TC_STAGES, (j / TC_STAGES) & 1, kTcWaitLimit)) fail = true;
     }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      constexpr uint32_t idesc = umma::idesc_bf16_f32(TC_BM, BN);
+      uint32_t it = 0, i = 0;
+      for (int t = blockIdx.x; t < ntiles && !fail; t += gridDim.x, ++i) {
+        const int z = t / per_split;
+        int kbeg, nk;
+        k_range(z, kbeg, nk);
+        const uint32_t ab = i & 1;
+        if (!umma::mbar_wait(tempty + ab, ((i >> 1) & 1) ^ 1, kTcWaitLimit)) {
+          fail = true;
+          break;
+        }
+        umma::tc_fence_after();
+        const uint32_t d = tmem + ab * BN;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % TC_STAGES;
+          if (!umma::mbar_wait(full + s, (it / TC_STAGES) & 1, kTcWaitLimit)) {
+            fail = true;
+            break;
+          }
+          umma::tc_fence_after();
+          const uint64_t da = umma::desc_sw128_kmajor(sA + s * A_BYTES);
+          const uint64_t db = umma::desc_sw128_kmajor(sB + s * B_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 16; ++kk)   // 16 bf16 = 32 bytes along K inside the swizzle atom
+            umma::mma_bf16(d, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) ? 1u : 0u);
+          umma::mma_commit(empty + s);
+        }
+        umma::mma_commit(tfull + ab);   // arrives when this tile's MMAs are complete
+      }
+    }
+  } else {
+    // ---- epilogue warps
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    constexpr int CH = BN / 32 / 2;                     // 32-column chunks per warp
+    uint8_t* my_stage = stage_out + (warp - 2) * 2 * 4096;
+    uint32_t i = 0, nchunk = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int z = t / per_split, rem = t % per_split;
+      const int m0 = (rem / tiles_n) * TC_BM, n0 = (rem % tiles_n) * BN;
+      const uint32_t ab = i & 1;
+      const bool ready = __all_sync(0xffffffffu, umma::mbar_wait(tfull + ab, (i >> 1) & 1, kTcWaitLimit));
+      umma::tc_fence_after();
+      if (!ready) {
+        fail = true;
+        break;
+      }
+      const int m = m0 + quarter * 32 + lane;
+#pragma unroll 1
+      for (int c = half * CH; c < (half + 1) * CH; ++c) {
+        const int nb = n0 + c * 32;
+        if (nb >= g.N) break;                                 // same for the whole warp
+        uint32_t r[32];
+        umma::tmem_ld32(tmem + ab * BN + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(c * 32), r);
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+        if constexpr (EPI == EPI_ADD_MEAN) {
+          // u = acc + mean, staged row-per-lane in a 128B-swizzled 32 x 32 box and
+          // written by one TMA store (rows beyond M are clipped by the tensor map)
+          const float4* mv = reinterpret_cast<const float4*>(g.bias + nb);
+          uint8_t* sb = my_stage + (nchunk & 1) * 4096;
+          if (lane == 0) umma::bulk_wait_read<1>();     // the store issued from this buffer two chunks ago
+          __syncwarp();
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 mm = __ldg(mv + q);
+            const float4 o = make_float4(v[4 * q] + mm.x, v[4 * q + 1] + mm.y, v[4 * q + 2] + mm.z,
+                                         v[4 * q + 3] + mm.w);
+            *reinterpret_cast<float4*>(sb + lane * 128 + ((q ^ (lane & 7)) << 4)) = o;
+          }
+          umma::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            umma::tma_store_2d(&tmC, sb, nb, m0 + quarter * 32);
+            umma::bulk_commit();
+          }
+          ++nchunk;
+        } else {
+          if (m < g.M) tc_epilogue_chunk<EPI>(g, v, m, nb, min(32, g.N - nb), z);
+        }
+      }
+      umma::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty + ab);
+    }
+    if (EPI == EPI_ADD_MEAN && lane == 0) umma::bulk_wait_all();
   }
+  if (fail) atomicOr(g.err, 1u);
+  __syncwarp();
   umma::tc_fence_before();
   __syncthreads();
-  if (warp == 0) umma::tmem_dealloc(tmem, BN);
+  if (warp == 1) umma::tmem_dealloc(tmem, 2 * BN);
 }
 
 // A' [P][ld] = [hi | hi | lo] of fp32 coefficients C [P][r] (see EPI_BIAS_SPLIT).
