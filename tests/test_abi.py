@@ -63,6 +63,20 @@ def test_argument_validation_needs_no_device(lib):
     assert lib.msk_philox_words(1, 1, 0, 0, 0, None, None) == msk.MSK_OK
     lib.msk_destroy(None)
     assert lib.msk_last_error(None) == b"null context"
+    assert lib.msk_brownian_functionals_ex(None, 1, 1, 0, None, None) == msk.MSK_ERR_ARG
+    # surrogate: NULL handles and missing arguments are rejected before any device work
+    cfg = msk.msk_surrogate_config(16, 64, 512, 4, 4096, 65536, 3, 8, 0)
+    assert lib.msk_surrogate_create(ctypes.byref(h), None, ctypes.byref(cfg)) == msk.MSK_ERR_ARG
+    assert h.value is None
+    assert lib.msk_surrogate_create(None, None, ctypes.byref(cfg)) == msk.MSK_ERR_ARG
+    assert lib.msk_surrogate_num_params(None) == -1
+    assert lib.msk_surrogate_infer(None, 0, 1, None, None, 0, 0.01, 0.05, None, None) == msk.MSK_ERR_ARG
+    assert lib.msk_surrogate_train(None, None, None, 1, 1, 1e-3, None, None) == msk.MSK_ERR_ARG
+    assert lib.msk_surrogate_fit_pod(None, None, 1, None, None) == msk.MSK_ERR_ARG
+    assert lib.msk_surrogate_sync_status(None, None) == msk.MSK_ERR_ARG
+    assert lib.msk_surrogate_param_layout(None, None) == msk.MSK_ERR_ARG
+    lib.msk_surrogate_destroy(None)
+    assert lib.msk_surrogate_last_error(None) == b"null surrogate"
 
 
 def test_create_without_a_device_reports_a_cuda_error(lib):
