@@ -222,9 +222,9 @@ def measured_peaks():
 # ------------------------------------------------------------------ learned surrogate
 
 SURR_CFG = dict(steps=16, rank=64, hidden=512, layers=4, train_batch=4096, infer_batch=65536)
-SURR_TRAIN = 196608          # Magnus solutions the surrogate is trained on
-SURR_EPOCHS = 300
-SURR_LR = 1e-3               # cosine decay to zero over the epochs
+SURR_TRAIN = 393216          # Magnus solutions the surrogate is trained on
+SURR_EPOCHS = 800
+SURR_LR = 6e-4               # cosine decay to zero over the epochs
 SURR_SERVE = 65536           # paths per serve step
 SURR_AUDIT_EVERY = 100       # 1% Magnus audit
 SURR_TOL = 1e-2              # per-path relative L2 fallback threshold
