@@ -55,10 +55,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-comparators", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=0, help="paths in the CPU-oracle sample (0 = auto)")
-    p.add_argument("--workload", default="trig128", choices=("trig128", "batch", "surrogate"),
+    p.add_argument("--workload", default="trig128", choices=("trig128", "batch", "surrogate", "large512"),
                    help="trig128: the time-dependent 128^2 workload (default); batch: grids 64/128/256 "
                         "in ratio 4:2:1 of 16384 paths in one persistent launch; surrogate: the learned "
-                        "surrogate of the 128^2 workload served 65536 paths per step with a 1%% Magnus audit")
+                        "surrogate of the 128^2 workload served 65536 paths per step with a 1%% Magnus audit; "
+                        "large512: the 512^2 constant-coefficient grids, sigma = 0.25 / 0.5 / 1, 1024 paths, m2")
     p.add_argument("--no-surrogate", action="store_true", help="skip the surrogate summary of the default line")
     p.add_argument("--surrogate-profile-case", type=int, default=0, metavar="PATHS",
                    help="serve PATHS paths twice with an untrained surrogate of the 128^2 workload (random "
@@ -535,6 +536,11 @@ def run_ours(a):
             comparators.setdefault("euler_fp32", {})[f"N{ne}"] = {
                 "paths_per_s": Pc / (msem / 1e3), "err": float(eem.cpu()[0])}
         comparators["magnus_fp32_sweep_err"] = {f"K{k}": v for k, v in sweep.items()}
+        for Kc in K_CANDIDATES:   # order 2 on the same paths and reference
+            u2, ms2 = timed(lambda: solver.magnus(2, Kc, paths=Pc, precision=msk.MSK_F32))
+            _, e2 = solver.error(u2[:n].contiguous(), msk.MSK_F32, ref=refc, ref_precision=msk.MSK_F64)
+            comparators.setdefault("magnus_fp32_m2", {})[f"K{Kc}"] = {
+                "paths_per_s": Pc / (ms2 / 1e3), "err": float(e2.cpu()[0])}
 
     # ---- learned surrogate of the same workload (setup untimed; own timed serve steps) ----------
     if not a.no_surrogate and world == 1:
@@ -873,6 +879,99 @@ def time_surrogate_oracle(msk, torch, solver, s, base, npaths):
                       f"POD decode), {dt:.1f} s"}
 
 
+def run_large512(a):
+    """512^2 grids (262144 unknowns) on [-8, 8]^2, a = 1, sigma in {0.25, 0.5, 1}: order-2
+    float Magnus on 1024 paths each at the cheapest K in {8, 16, 32, 64} whose Err against the
+    closed-form solution is <= 1e-3 with no path flagged (non-finite / blow-up) on a 128-path
+    subset; sigma = 1 (a = sigma^2, degenerate) is reported at K = 64 without a gate."""
+    import torch
+
+    import paper_2207_09776_b300 as msk
+    from paper_2207_09776_b300 import build as mbuild
+    from workloads import LARGE_512
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    mbuild.build()
+    msk.load_library()
+    stream = torch.cuda.current_stream()
+    order, sub = 2, 128
+    peaks, peak_src = measured_peaks()
+    fp32_peak = 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    per_sigma = {}
+    total_ms, total_paths, total_flops = 0.0, 0, 0.0
+    clocks = ClockSampler(local)
+    started = False
+    reps = max(1, a.steps // 3)
+    for w0 in LARGE_512:
+        w = w0.with_(path_offset=rank * w0.paths)
+        s = msk.Solver(w, device=local)
+        sweep, chosen = {}, None
+        for Kc in K_CANDIDATES:
+            u, stv = s.magnus(order, Kc, paths=sub, precision=msk.MSK_F32, status=True)
+            e = float(s.error(u, msk.MSK_F32)[1].cpu()[0])
+            flagged = int((stv != 0).sum())
+            sweep[f"K{Kc}"] = {"err": e, "flagged_paths": flagged}
+            if chosen is None and flagged == 0 and e <= 1e-3 and w.s0 < 1.0:
+                chosen = Kc
+        K = chosen if chosen is not None else K_CANDIDATES[-1]
+        P = w.paths
+        out = s.state(P, msk.MSK_F32)
+        st = torch.zeros(P, dtype=torch.int32, device="cuda")
+        for _ in range(max(a.warmup, 1)):
+            msk.msk_solve_magnus(s.ctx, order, K, P, msk.MSK_F32, out, st, stream)
+        torch.cuda.synchronize()
+        msk.msk_work_counter(s.ctx, reset=True, stream=stream)
+        if not started:
+            clocks.start()
+            started = True
+        e0, e1 = _events(torch, stream)
+        e0.record(stream)
+        for _ in range(reps):
+            msk.msk_solve_magnus(s.ctx, order, K, P, msk.MSK_F32, out, st, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        mv = msk.msk_work_counter(s.ctx, reset=True, stream=stream) / reps
+        errs, _ = s.error(out, msk.MSK_F32)
+        errs = errs.cpu()
+        ok = torch.isfinite(errs)
+        per_sigma[f"sigma{w.s0}"] = {
+            "K": K, "gated": w.s0 < 1.0 and chosen is not None, "paths_per_s": P / (ms / 1e3), "ms": ms,
+            "err_vs_closed_form_mean_finite": float(errs[ok].mean()) if bool(ok.any()) else None,
+            "flagged_paths": int((st != 0).sum()), "matvecs_per_path": mv / P,
+            "tflops": mv * w.d * w.d * FLOPS_PER_POINT / (ms / 1e3) / 1e12, f"sweep_{sub}_paths": sweep}
+        total_ms += ms
+        total_paths += P
+        total_flops += mv * w.d * w.d * FLOPS_PER_POINT
+        s.close()
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    achieved = total_flops / (total_ms / 1e3) / 1e12
+    line = {"metric": METRIC, "value": world * total_paths / (total_ms / 1e3), "unit": "paths/s", "n_gpus": world,
+            "steps": reps, "warmup": max(a.warmup, 1), "ms_per_step": total_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "langevin_const_d512_sigma_0.25_0.5_1", "d": 512, "paths_per_gpu": total_paths,
+                       "order": order, "n_fine": LARGE_512[0].n_fine,
+                       "step": "one float solve of 1024 paths for each of the three sigma, at each one's K",
+                       "err_target": "1e-3 vs the closed form, no flagged path (sigma = 1 not gated)",
+                       "double_precision": "not built at 512^2 (two double slabs exceed 16 CTAs' shared memory)",
+                       "parallelism": f"replicas x{world} (path ranges)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "traffic": None,
+                         "kernel": "engine_kernel<float,512,16,512> (16-CTA clusters, DSMEM halos)"},
+            "per_sigma": per_sigma, "clocks": clk, "gpu_launches": 3 * 3 * reps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_surrogate_profile_case(a):
     """Two serves of PATHS paths by a surrogate with random parameters (kernel timing only)."""
     import torch
@@ -937,6 +1036,8 @@ def main():
         run_batch(a)
     elif a.workload == "surrogate":
         run_surrogate(a)
+    elif a.workload == "large512":
+        run_large512(a)
     else:
         run_ours(a)
 
