@@ -65,6 +65,9 @@ def parse():
                    help="serve PATHS paths twice with an untrained surrogate of the 128^2 workload (random "
                         "weights, random orthonormal POD basis; features, network, decode; no audit) -- a "
                         "small case for ncu captures of the surrogate kernels -- and exit")
+    p.add_argument("--profile-grid", type=int, default=128, choices=(128, 512),
+                   help="grid of --profile-case: 128 (the bench workload, m3, K = 8) or 512 "
+                        "(sigma = 0.5, m2, K = 64)")
     p.add_argument("--profile-case", type=int, default=0, metavar="PATHS",
                    help="run two plain solves of the benchmark workload with PATHS paths at K = 8 "
                         "(a small case for ncu captures) and exit")
@@ -921,9 +924,13 @@ def run_large512(a):
         P = w.paths
         out = s.state(P, msk.MSK_F32)
         st = torch.zeros(P, dtype=torch.int32, device="cuda")
-        for _ in range(max(a.warmup, 1)):
-            msk.msk_solve_magnus(s.ctx, order, K, P, msk.MSK_F32, out, st, stream)
-        torch.cuda.synchronize()
+        while True:   # the whole batch must be free of flagged paths, else the next K
+            for _ in range(max(a.warmup, 1)):
+                msk.msk_solve_magnus(s.ctx, order, K, P, msk.MSK_F32, out, st, stream)
+            torch.cuda.synchronize()
+            if not bool((st != 0).any()) or K >= K_CANDIDATES[-1] or w.s0 >= 1.0:
+                break
+            K = K_CANDIDATES[K_CANDIDATES.index(K) + 1]
         msk.msk_work_counter(s.ctx, reset=True, stream=stream)
         if not started:
             clocks.start()
@@ -1007,15 +1014,19 @@ def run_profile_case(a):
     from paper_2207_09776_b300 import build as mbuild
     mbuild.build()
     msk.load_library()
-    P, K = a.profile_case, K_CANDIDATES[0]
-    w = LANGEVIN_TRIG_128.with_(paths=P)
+    P = a.profile_case
+    if a.profile_grid == 512:
+        from workloads import LARGE_512
+        w, K, order = LARGE_512[1].with_(paths=P), 64, 2
+    else:
+        w, K, order = LANGEVIN_TRIG_128.with_(paths=P), K_CANDIDATES[0], ORDER
     s = msk.Solver(w)
     F = torch.empty(P * K * msk.MSK_NF, dtype=torch.float64, device="cuda")
     Wt = torch.empty(P * K * msk.MSK_NWT, dtype=torch.float64, device="cuda")
     out = torch.empty(P * w.d * w.d, dtype=torch.float32, device="cuda")
     for _ in range(2):
         msk.msk_brownian_functionals_ex(s.ctx, K, P, msk.MSK_F32, F)
-        msk.msk_omega_weights(s.ctx, ORDER, K, P, msk.MSK_F32, F, Wt)
+        msk.msk_omega_weights(s.ctx, order, K, P, msk.MSK_F32, F, Wt)
         msk.msk_magnus_from_weights(s.ctx, K, P, msk.MSK_F32, Wt, out)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": P, "matvecs": msk.msk_work_counter(s.ctx)}))

@@ -251,14 +251,16 @@ msk_status msk_batch_create(msk_batch** out, const msk_batch_item* items, int n_
  * every run launches that graph on `stream`. */
 msk_status msk_batch_run(msk_batch* b, void* stream);
 
-/* Autotune: time every variant (queue order x 64^2 packing) on this batch,
- * keep the fastest, append it to `tune_cache` (if given), report the chosen
- * variant and the four times in milliseconds (ms_out[4], nullable). */
+/* Autotune: time every variant (queue order x 64^2 packing of the megakernel,
+ * and per-item engine launches) on this batch, keep the fastest, append it to
+ * `tune_cache` (if given), report the chosen variant and the five times in
+ * milliseconds (ms_out[5], nullable). */
 msk_status msk_batch_tune(msk_batch* b, void* stream, const char* tune_cache, int* variant_out,
                           float* ms_out);
 
-/* Current variant of the batch (bit 0: interleaved queue, bit 1: one 64^2 path per
- * CTA), and setting it explicitly (0..3; the next run re-captures the graph). */
+/* Current variant of the batch (0..3 megakernel: bit 0 interleaved queue, bit 1
+ * one 64^2 path per CTA; 4: each item's own engine launch), and setting it
+ * explicitly (0..4; the next run re-captures the graph). */
 int msk_batch_variant(const msk_batch* b);
 msk_status msk_batch_set_variant(msk_batch* b, int variant);
 

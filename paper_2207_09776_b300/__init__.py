@@ -318,7 +318,7 @@ def msk_batch_run(b, stream=None):
 
 def msk_batch_tune(b, tune_cache=None, stream=None):
     v = _INT(0)
-    ms = (ctypes.c_float * 4)()
+    ms = (ctypes.c_float * 5)()
     rc = load_library().msk_batch_tune(b, _stream(stream), tune_cache.encode() if tune_cache else None,
                                        ctypes.byref(v), ms)
     if rc != MSK_OK:

@@ -15,9 +15,11 @@
 // points (16384), so units differ in length only by their Taylor work, which
 // grows with the grid (the operator norm scales like 1/Delta^2).
 //
-// Tuned choices (the "variant"): bit 0 orders the queue by decreasing unit
-// length (largest grids first) or interleaves the items; bit 1 packs 64^2
-// paths two per CTA or one per CTA.  msk_batch_tune times all four on the
+// Tuned choices (the "variant"): for 0..3, bit 0 orders the queue by
+// decreasing unit length (largest grids first) or interleaves the items, and
+// bit 1 packs 64^2 paths two per CTA or one per CTA; variant 4 replaces the
+// megakernel by each item's own engine launch (its best per-grid
+// configuration) inside the same graph.  msk_batch_tune times all five on the
 // batch itself and keeps the fastest; the result can be cached in a text file
 // keyed by device name and batch shape.
 #include <stdio.h>
@@ -138,6 +140,10 @@ msk_status bcuda(msk_batch* b, cudaError_t e, const char* what) {
                std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Variant 4: no megakernel; the graph holds each item's own engine launch.
+constexpr int kPerGridVariant = 4;
+constexpr int kVariants = 5;
+
 std::vector<BatchUnit> build_units(const msk_batch* b, int variant) {
   const bool interleave = variant & 1, one64 = variant & 2;
   std::vector<std::vector<BatchUnit>> per(b->items.size());
@@ -212,6 +218,16 @@ msk_status enqueue(msk_batch* b, cudaStream_t s) {
     if (st != MSK_OK) b->err = it.ctx->err;
   }
   if (st != MSK_OK || b->n_units == 0) return st;
+  if (b->variant == kPerGridVariant) {   // each item's own engine launch, one after another
+    for (size_t k = 0; k < b->items.size() && st == MSK_OK; ++k) {
+      const msk_batch_item& it = b->items[k];
+      if (it.paths == 0) continue;
+      st = launch_engine(it.ctx, false, it.steps, it.paths, MSK_F32, b->scratch + b->w_off[k], nullptr, it.u_out_dev,
+                         it.status_dev, s);
+      if (st != MSK_OK) b->err = it.ctx->err;
+    }
+    return st;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(148 * 4, 1, 1);
   cfg.blockDim = dim3(kNT, 1, 1);
@@ -337,7 +353,7 @@ extern "C" msk_status msk_batch_create(msk_batch** out, const msk_batch_item* it
   if (st == MSK_OK) {
     b->key = batch_key(b);
     const int v = cached_variant(tune_cache, b->key);
-    st = set_variant(b, v >= 0 && v < 4 ? v : 0);
+    st = set_variant(b, v >= 0 && v < kVariants ? v : 0);
   }
   if (st != MSK_OK) {
     msk_batch_destroy(b);
@@ -384,9 +400,9 @@ extern "C" msk_status msk_batch_tune(msk_batch* b, void* stream, const char* tun
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f, times[4] = {0, 0, 0, 0};
+  float best = 1e30f, times[kVariants] = {0, 0, 0, 0, 0};
   int best_v = 0;
-  for (int v = 0; v < 4 && st == MSK_OK; ++v) {
+  for (int v = 0; v < kVariants && st == MSK_OK; ++v) {
     st = set_variant(b, v);
     if (st == MSK_OK) st = msk_batch_run(b, stream);            // capture + warm-up
     if (st != MSK_OK) break;
@@ -409,7 +425,7 @@ extern "C" msk_status msk_batch_tune(msk_batch* b, void* stream, const char* tun
   if (st != MSK_OK) return st;
   if (variant_out) *variant_out = best_v;
   if (ms_out)
-    for (int v = 0; v < 4; ++v) ms_out[v] = times[v];
+    for (int v = 0; v < kVariants; ++v) ms_out[v] = times[v];
   if (tune_cache && *tune_cache) {
     FILE* f = fopen(tune_cache, "a");
     if (f) {
@@ -424,7 +440,7 @@ extern "C" int msk_batch_variant(const msk_batch* b) { return b ? b->variant : -
 
 extern "C" msk_status msk_batch_set_variant(msk_batch* b, int variant) {
   if (!b) return MSK_ERR_ARG;
-  if (variant < 0 || variant > 3) return bfail(b, MSK_ERR_ARG, "variant must be 0..3");
+  if (variant < 0 || variant >= kVariants) return bfail(b, MSK_ERR_ARG, "variant must be 0..4");
   msk_status st = bcuda(b, cudaSetDevice(b->device), "set device");
   if (st != MSK_OK) return st;
   return set_variant(b, variant);

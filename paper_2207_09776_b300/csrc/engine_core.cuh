@@ -83,7 +83,13 @@ struct Cfg {
   static constexpr size_t OFF_B0 = OFF_COEF + 5 * MSK_NCOEF;      // RS: centre of V1 per local row
   static constexpr size_t OFF_SCALE = OFF_B0 + RS;                // kMaxTerms + 1: 1/(s k)
   static constexpr size_t OFF_SLOT = OFF_SCALE + kMaxTerms + 1;   // 2 x NW x 2 norm slots
-  static constexpr size_t NELEM = OFF_SLOT + 4 * NW;
+  // Clustered slabs keep the Taylor partial sum in shared memory ([RS][D], each
+  // thread's own points) instead of registers: their halo-exchange code needs
+  // the registers, and the register-resident sum spills there.
+  static constexpr bool ACC_SMEM = C > 1;
+  static constexpr size_t OFF_CSLOT = OFF_SLOT + 4 * NW;           // 2 x 2 CTA-level norm slots
+  static constexpr size_t OFF_ACC = (OFF_CSLOT + 4 + 3) / 4 * 4;
+  static constexpr size_t NELEM = ACC_SMEM ? OFF_ACC + (size_t)RS * D : OFF_CSLOT + 4;
   static constexpr size_t SMEM = NELEM * sizeof(T);
   static_assert(SMEM <= 232448, "slab does not fit the 227 KB of shared memory per CTA");
 };
@@ -142,6 +148,35 @@ struct CtaSync {
   __device__ __forceinline__ void operator()() const { __syncthreads(); }
   __device__ __forceinline__ void local() const { __syncthreads(); }
 };
+// Distributed shared memory through explicit shared::cluster addresses (mapa):
+// the same offset in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t dsmem_addr(const void* p, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void dsmem_st4(uint32_t addr, const V4<float>& v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void dsmem_st4(uint32_t addr, const V4<double>& v) {
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(addr), "d"(v.x), "d"(v.y) : "memory");
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(addr + 16u), "d"(v.z), "d"(v.w) : "memory");
+}
+__device__ __forceinline__ float dsmem_ld(uint32_t addr, float) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ double dsmem_ld(uint32_t addr, double) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+  return v;
+}
+
 struct ClusterSync {
   __device__ __forceinline__ void operator()() const { cg::this_cluster().sync(); }
   __device__ __forceinline__ void local() const { __syncthreads(); }
@@ -236,33 +271,37 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
   };
 
   // store the four own columns of local row p into buffer b, and into the facing
-  // halo row of the neighbouring CTA
+  // halo row of the neighbouring CTA (shared::cluster stores)
+  const uint32_t peer_lo = (C > 1 && rank > 0) ? dsmem_addr(sm, rank - 1) : 0u;
+  const uint32_t peer_hi = (C > 1 && rank < C - 1) ? dsmem_addr(sm, rank + 1) : 0u;
   auto store_row = [&](int b, int p, const V4<T>& v) {
     st4(sm + b * K::BUF + at(p, i0), v);
     if constexpr (C > 1) {
-      if (p < 2 && rank > 0) {
-        T* peer = cg::this_cluster().map_shared_rank(sm, rank - 1);
-        st4(peer + b * K::BUF + at(RS + p, i0), v);
-      }
-      if (p >= RS - 2 && rank < C - 1) {
-        T* peer = cg::this_cluster().map_shared_rank(sm, rank + 1);
-        st4(peer + b * K::BUF + at(p - RS, i0), v);
-      }
+      if (p < 2 && rank > 0) dsmem_st4(peer_lo + (uint32_t)((b * K::BUF + at(RS + p, i0)) * sizeof(T)), v);
+      if (p >= RS - 2 && rank < C - 1)
+        dsmem_st4(peer_hi + (uint32_t)((b * K::BUF + at(p - RS, i0)) * sizeof(T)), v);
     }
   };
 
-  // gather the per-warp maxima of all CTAs of the cluster (identical in every thread)
+  // Norms: every warp publishes its maxima; with clusters, warp 0 of each CTA
+  // folds them into one CTA-level slot (after a CTA barrier), and after the
+  // cluster barrier every warp reads the C CTA slots (one remote load per lane).
+  // The result is identical in every thread of the cluster.
+  T* cslot = sm + K::OFF_CSLOT;
   auto gather = [&](int par, T& gn, T& ga) {
     gn = T(0);
     ga = T(0);
-    for (int q = lane; q < C * NW; q += 32) {
-      const int cr = q / NW, wq = q % NW;
-      const T* sl = slots;
-      if constexpr (C > 1) {
-        if (cr != rank) sl = cg::this_cluster().map_shared_rank(slots, cr);
+    if constexpr (C > 1) {
+      if (lane < C) {
+        const uint32_t q = dsmem_addr(cslot + par * 2, lane);
+        gn = dsmem_ld(q, T(0));
+        ga = dsmem_ld(q + (uint32_t)sizeof(T), T(0));
       }
-      gn = tmax(gn, sl[(par * NW + wq) * 2 + 0]);
-      ga = tmax(ga, sl[(par * NW + wq) * 2 + 1]);
+    } else {
+      for (int q = lane; q < NW; q += 32) {
+        gn = tmax(gn, slots[(par * NW + q) * 2 + 0]);
+        ga = tmax(ga, slots[(par * NW + q) * 2 + 1]);
+      }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -280,19 +319,51 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
       slots[(par * NW + warp) * 2 + 0] = mn;
       slots[(par * NW + warp) * 2 + 1] = ma;
     }
+    if constexpr (C > 1) {
+      sync_all.local();
+      if (warp == 0) {
+        T a = T(0), b = T(0);
+        for (int q = lane; q < NW; q += 32) {
+          a = tmax(a, slots[(par * NW + q) * 2 + 0]);
+          b = tmax(b, slots[(par * NW + q) * 2 + 1]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          a = tmax(a, __shfl_xor_sync(0xffffffffu, a, off));
+          b = tmax(b, __shfl_xor_sync(0xffffffffu, b, off));
+        }
+        if (lane == 0) {
+          cslot[par * 2 + 0] = a;
+          cslot[par * 2 + 1] = b;
+        }
+      }
+    }
   };
 
   {
-    V4<T> acc[R];
+    // partial sum of the Taylor series (and the state between steps): registers
+    // or, for clustered slabs, shared memory at the thread's own points
+    constexpr bool AS = K::ACC_SMEM;
+    V4<T> accr[AS ? 1 : R];
+    T* accS = sm + K::OFF_ACC;
+    auto acc_get = [&](int r) -> V4<T> {
+      if constexpr (AS) return ld4(accS + (size_t)(j0 + r) * D + i0);
+      else return accr[r];
+    };
+    auto acc_put = [&](int r, const V4<T>& v) {
+      if constexpr (AS) st4(accS + (size_t)(j0 + r) * D + i0, v);
+      else accr[r] = v;
+    };
     int cur = 0, par = 0;
     // ---- initial datum: own rows, plus the halo rows facing other CTAs ----------
     T m0 = T(0);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const double* src = a.u0 + (size_t)(r0 + j0 + r) * D + i0;
-      acc[r] = {(T)src[0], (T)src[1], (T)src[2], (T)src[3]};
-      st4(sm + at(j0 + r, i0), acc[r]);
-      m0 = tmax(m0, tmax(tmax(absnan(acc[r].x), absnan(acc[r].y)), tmax(absnan(acc[r].z), absnan(acc[r].w))));
+      const V4<T> v = {(T)src[0], (T)src[1], (T)src[2], (T)src[3]};
+      acc_put(r, v);
+      st4(sm + at(j0 + r, i0), v);
+      m0 = tmax(m0, tmax(tmax(absnan(v.x), absnan(v.y)), tmax(absnan(v.z), absnan(v.w))));
     }
     if (j0 == 0 || j0 + R == RS) {
       for (int h = 0; h < 2; ++h) {
@@ -398,14 +469,16 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
             }
             store_row(nxt, p, out);
             if constexpr (EULER) {
-              acc[r] = out;
+              acc_put(r, out);
             } else {
-              acc[r].x += out.x;
-              acc[r].y += out.y;
-              acc[r].z += out.z;
-              acc[r].w += out.w;
+              V4<T> ac = acc_get(r);
+              ac.x += out.x;
+              ac.y += out.y;
+              ac.z += out.z;
+              ac.w += out.w;
+              acc_put(r, ac);
               mn = tmax(mn, amax4(out));
-              ma = tmax(ma, amax4(acc[r]));
+              ma = tmax(ma, amax4(ac));
             }
             cw0 = cw1; cw1 = cw2; cw2 = cw3; cw3 = cw4;
             d10 = d11; s20 = s21; d11 = d12; s21 = s22;
@@ -431,11 +504,13 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
           // u <- e^{mu/s} (partial sum), into the buffer not holding the last term
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            acc[r].x *= te;
-            acc[r].y *= te;
-            acc[r].z *= te;
-            acc[r].w *= te;
-            store_row(cur ^ 1, j0 + r, acc[r]);
+            V4<T> ac = acc_get(r);
+            ac.x *= te;
+            ac.y *= te;
+            ac.z *= te;
+            ac.w *= te;
+            acc_put(r, ac);
+            store_row(cur ^ 1, j0 + r, ac);
           }
           unorm = unorm * te;
           sync_all();
@@ -448,8 +523,9 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
     T mfin = T(0);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      st4(reinterpret_cast<T*>(a.out) + (size_t)path * D * D + (size_t)(r0 + j0 + r) * D + i0, acc[r]);
-      mfin = tmax(mfin, tmax(tmax(absnan(acc[r].x), absnan(acc[r].y)), tmax(absnan(acc[r].z), absnan(acc[r].w))));
+      const V4<T> v = acc_get(r);
+      st4(reinterpret_cast<T*>(a.out) + (size_t)path * D * D + (size_t)(r0 + j0 + r) * D + i0, v);
+      mfin = tmax(mfin, tmax(tmax(absnan(v.x), absnan(v.y)), tmax(absnan(v.z), absnan(v.w))));
     }
     if (a.work && rank == 0 && tid == 0) atomicAdd(a.work, nmv);
     publish(par, mfin, mfin);

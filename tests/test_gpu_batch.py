@@ -61,7 +61,7 @@ def test_autotuner_picks_and_caches_a_variant(tmp_path):
     ws, solvers, outs, sts, items = _items(paths=(17, 5, 2))
     b = msk.msk_batch_create(items, cache)
     v, times = msk.msk_batch_tune(b, cache)
-    assert 0 <= v < 4 and all(t > 0 for t in times) and times[v] == min(times)
+    assert 0 <= v < 5 and len(times) == 5 and all(t > 0 for t in times) and times[v] == min(times)
     assert msk.msk_batch_variant(b) == v
     msk.msk_batch_run(b)
     torch.cuda.synchronize()
@@ -77,7 +77,7 @@ def test_autotuner_picks_and_caches_a_variant(tmp_path):
         s.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_every_variant_gives_the_same_answer(variant):
     ws, solvers, outs, sts, items = _items(paths=(11, 6, 1))
     b = msk.msk_batch_create(items)
@@ -89,7 +89,7 @@ def test_every_variant_gives_the_same_answer(variant):
         ref = s.magnus(3, 4, precision=msk.MSK_F32)
         assert rel_l2(o.cpu().numpy(), ref.cpu().numpy()).max() <= 1e-6
     with pytest.raises(msk.MskError):
-        msk.msk_batch_set_variant(b, 4)
+        msk.msk_batch_set_variant(b, 5)
     msk.msk_batch_destroy(b)
     for s in solvers:
         s.close()
