@@ -335,7 +335,7 @@ extern "C" msk_status msk_batch_create(msk_batch** out, const msk_batch_item* it
     a.dx = c->dx;
     a.T = c->T;
     a.s_cap = kMskScaleCap;
-    a.tol32 = 0x1p-24f;
+    a.tol32 = 0x1p-20f;   // float Taylor tolerance (see gen_theta.py)
     a.tol64 = 0x1p-53;
     a.c = coef_dev(c->coef);
     b->args.push_back(a);

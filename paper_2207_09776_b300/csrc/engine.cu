@@ -111,7 +111,7 @@ msk_status launch_engine(msk_ctx* ctx, bool euler, int steps, int64_t paths, int
   a.dx = ctx->dx;
   a.T = ctx->T;
   a.s_cap = kMskScaleCap;
-  a.tol32 = 0x1p-24f;
+  a.tol32 = 0x1p-20f;   // float Taylor tolerance (see gen_theta.py)
   a.tol64 = 0x1p-53;
   a.c = coef_dev(ctx->coef);
   return euler ? dispatch<true>(ctx, precision, a, stream) : dispatch<false>(ctx, precision, a, stream);
