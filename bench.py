@@ -422,6 +422,12 @@ def run_ours(a):
         chosen = K_CANDIDATES[-1]
     K = chosen
     del wref
+    # reference-free alternative: the order-2 / order-3 distance (Remark stepSizeControl)
+    # on the same paths, same target; reported beside the protocol's choice
+    K_sc, d_sc = msk.msk_select_steps(ctx, ERR_TARGET, 4, 64, REF_PATHS, msk.MSK_F32)
+    step_control = {"tol": ERR_TARGET, "paths": REF_PATHS, "K_selected": K_sc,
+                    "m2_m3_distance": {f"K{4 * 2 ** i}": v for i, v in enumerate(d_sc)},
+                    "K_fixed_error_protocol": K}
 
     # ---- buffers of one step ------------------------------------------------------------
     F = torch.empty(P * K * msk.MSK_NF, dtype=torch.float64, device=dev)
@@ -539,6 +545,7 @@ def run_ours(a):
             comparators.setdefault("euler_fp32", {})[f"N{ne}"] = {
                 "paths_per_s": Pc / (msem / 1e3), "err": float(eem.cpu()[0])}
         comparators["magnus_fp32_sweep_err"] = {f"K{k}": v for k, v in sweep.items()}
+        comparators["step_control"] = step_control
         for Kc in K_CANDIDATES:   # order 2 on the same paths and reference
             u2, ms2 = timed(lambda: solver.magnus(2, Kc, paths=Pc, precision=msk.MSK_F32))
             _, e2 = solver.error(u2[:n].contiguous(), msk.MSK_F32, ref=refc, ref_precision=msk.MSK_F64)

@@ -390,6 +390,18 @@ msk_status msk_surrogate_infer(msk_surrogate* s, int64_t path0, int64_t paths, f
  * outputs are invalid), else MSK_OK. */
 msk_status msk_surrogate_sync_status(msk_surrogate* s, void* stream);
 
+/* Step-size control (Remark stepSizeControl): for K = k_min, 2 k_min, 4 k_min, ...
+ * <= k_max that divide n_fine (at most 16 of them), solve the context's paths
+ * 0 .. paths-1 (a subset of trajectories chosen through the seed's path
+ * offset) with orders 2 and 3 from the same Brownian functionals, and accept
+ * the first K whose largest per-path relative L2 distance between the two
+ * solutions (whole grid) is <= tol; a non-finite distance (blow-up) rejects K.
+ * *K_out = the accepted K, or the last candidate if none is accepted;
+ * dist_host (nullable, double[16]) the distance of every K tried; n_tried
+ * (nullable) their number.  Allocates its own scratch and synchronises `stream`. */
+msk_status msk_select_steps(msk_ctx* ctx, double tol, int k_min, int k_max, int64_t paths, int precision,
+                            int* K_out, double* dist_host, int* n_tried, void* stream);
+
 /* S7: Euler-Maruyama (Eq. EulerMaruyama) with `steps` equal steps, a(t),
  * sigma(t) at the left end of each step, dW the sum of the fine increments. */
 msk_status msk_solve_euler(msk_ctx* ctx, int steps, int64_t paths, int precision,

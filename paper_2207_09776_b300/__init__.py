@@ -111,6 +111,8 @@ SIGNATURES = {
     "msk_surrogate_train": (_INT, [_P, _P, _P, _I64, _INT, ctypes.c_float, _P, _P]),
     "msk_surrogate_infer": (_INT, [_P, _I64, _I64, _P, _P, _I64, _DBL, _DBL, ctypes.POINTER(_DBL), _P]),
     "msk_surrogate_sync_status": (_INT, [_P, _P]),
+    "msk_select_steps": (_INT, [_P, _DBL, _INT, _INT, _I64, _INT, ctypes.POINTER(_INT), ctypes.POINTER(_DBL),
+                                ctypes.POINTER(_INT), _P]),
     "msk_explicit_solution": (_INT, [_P, _I64, _P, _P]),
     "msk_error": (_INT, [_P, _P, _INT, _I64, _INT, _P, _INT, _INT, _P, _P, _P]),
     "msk_moments": (_INT, [_P, _P, _INT, _I64, _P, _P]),
@@ -272,6 +274,16 @@ def msk_work_counter(ctx, reset=False, stream=None) -> int:
     v = ctypes.c_uint64(0)
     _check(load_library().msk_work_counter(ctx, ctypes.byref(v), int(bool(reset)), _stream(stream)), ctx)
     return int(v.value)
+
+
+def msk_select_steps(ctx, tol, k_min, k_max, paths, precision, stream=None):
+    """Step-size control by the order-2 / order-3 distance; returns (K, [distance of each K tried])."""
+    K = _INT(0)
+    n = _INT(0)
+    d = (_DBL * 16)()
+    _check(load_library().msk_select_steps(ctx, tol, k_min, k_max, paths, precision, ctypes.byref(K), d,
+                                           ctypes.byref(n), _stream(stream)), ctx)
+    return K.value, list(d)[: n.value]
 
 
 def msk_solve_euler(ctx, steps, paths, precision, u_out, status=None, stream=None):

@@ -64,6 +64,7 @@ def test_argument_validation_needs_no_device(lib):
     lib.msk_destroy(None)
     assert lib.msk_last_error(None) == b"null context"
     assert lib.msk_brownian_functionals_ex(None, 1, 1, 0, None, None) == msk.MSK_ERR_ARG
+    assert lib.msk_select_steps(None, 1e-3, 1, 8, 1, 0, None, None, None, None) == msk.MSK_ERR_ARG
     # surrogate: NULL handles and missing arguments are rejected before any device work
     cfg = msk.msk_surrogate_config(16, 64, 512, 4, 4096, 65536, 3, 8, 0)
     assert lib.msk_surrogate_create(ctypes.byref(h), None, ctypes.byref(cfg)) == msk.MSK_ERR_ARG
