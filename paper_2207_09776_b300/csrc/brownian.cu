@@ -92,7 +92,13 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
   const double sg0 = a.c.s0, al0 = 0.5 * a.c.a0;
 
   double W0 = 0.0, O0 = 0.0;                                // W~ and omega~ at the round start
-  double S1 = 0.0, S2 = 0.0, S3 = 0.0, J1 = 0.0, J2 = 0.0, J3 = 0.0, J4 = 0.0;
+  // Per-lane sums over the lane's cells (w0, w1 = W~ at a cell's ends, k = cell
+  // index in the step, sdw = sigma dW of the cell); the functionals follow at
+  // the end through the telescoping identities
+  //   sum (w0 + w1) = 2 sum w0 + sum dw,   sum (w0 + 2 w1) = 3 sum w0 + 2 sum dw,
+  //   sum (k + 1/2) sdw = sum k sdw + sum sdw / 2,   sum (om0 + om1) = 2 sum om0 + sum sdw.
+  double Sw0 = 0.0, S2 = 0.0, Skw = 0.0, So0 = 0.0, Sks = 0.0, J3 = 0.0, J4 = 0.0;
+  double swT = 0.0, soT = 0.0;                              // sum dw, sum sigma dW of the lane's cells
   for (int64_t rb = 0; rb < L; rb += kRound) {
     // ---- pass 1: normals of this lane's chunk, chunk sums -------------------------
     const int64_t c0 = rb + (int64_t)lane * kChunk;
@@ -114,6 +120,8 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
     W0 += warp_sum(sw);
     O0 += warp_sum(so);
     if (!FULL) continue;
+    swT += sw;
+    soT += so;
     // ---- pass 2: functionals over the staged increments -------------------------
     // Sums are kept without their constant factors (delta/2, delta/3, delta^2/6,
     // delta), applied once at the end; k is carried as a double counter.
@@ -124,14 +132,14 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
       const double dw = st[q * 32 + lane];
       const double w1 = w0 + dw;
       const double ws = w0 + w1;
-      S1 += ws;                                              // delta/2 sum (w0 + w1)
+      Sw0 += w0;
       S2 = fma(w0, ws, fma(w1, w1, S2));                     // delta/3 sum (w0^2 + w0 w1 + w1^2)
-      S3 = fma(3.0 * kd, ws, S3 + (w0 + 2.0 * w1));          // delta^2/6 sum (3k (w0+w1) + w0 + 2 w1)
+      Skw = fma(kd, ws, Skw);                                // sum k (w0 + w1)
       const double sig = TRIG ? tsig[fi] : sg0;
       const double sdw = sig * dw;
       const double om1 = om0 + sdw;
-      J1 += om0 + om1;                                       // delta/2 sum (om0 + om1)
-      J2 = fma(kd + 0.5, sdw, J2);                           // delta sum (k + 1/2) sigma dW
+      So0 += om0;
+      Sks = fma(kd, sdw, Sks);                               // sum k sigma dW
       if (TRIG) {
         J3 = fma(talp[fi], om0, fma(talp[fi + 1], om1, J3)); // delta/2 sum (alpha0 om0 + alpha1 om1)
         J4 = fma(tA[fi] - Astart, sdw, J4);                  // sum alpha_bar(s_mid) sigma dW
@@ -143,6 +151,10 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
     __syncwarp();   // the stage buffer is rewritten by the next round
   }
   if (FULL) {
+    const double S1 = 2.0 * Sw0 + swT;                       // sum (w0 + w1)
+    const double S3 = 3.0 * (Skw + Sw0) + 2.0 * swT;          // sum (3k (w0 + w1) + w0 + 2 w1)
+    const double J1 = 2.0 * So0 + soT;                       // sum (om0 + om1)
+    const double J2 = Sks + 0.5 * soT;                       // sum (k + 1/2) sigma dW
     const double I1 = 0.5 * delta * warp_sum(S1);
     const double I2 = delta / 3.0 * warp_sum(S2);
     const double I3 = delta * delta / 6.0 * warp_sum(S3);
