@@ -86,15 +86,33 @@ def assemble(nx, ax, bx, nv, av, bv, *, h=None, fx=None, fv=None, gxx=None, gxv=
     return B.tocsr(), A.tocsr()
 
 
+def x_profile(w, x):
+    """psi(x) of the variable coefficients (Eq. coeffsLangevinVar).
+
+    The paper's variable-coefficient Langevin SPDE has g^vv(x, v) = a (1 + 1/(x^2+1))
+    and sigma^v(x, v) = sigma sqrt(1 + 1/(x^2+1)); with psi(x) = 1 + c/(1 + x^2)
+    (c = 1 there) these are a psi and sigma sqrt(psi).  Without a profile psi = 1.
+    """
+    from workloads import XPROF_NONE, XPROF_RATIONAL
+    x = np.asarray(x, dtype=np.float64)
+    kind = getattr(w, "x_profile", XPROF_NONE)
+    if kind == XPROF_NONE:
+        return np.ones_like(x)
+    if kind == XPROF_RATIONAL:
+        return 1.0 + w.x_profile_c / (1.0 + x * x)
+    raise ValueError("unknown x profile")
+
+
 class LangevinOperators:
     """Unit operators of the Langevin SPDE on one grid.
 
-    With f^x = kappa v, g^vv = a, sigma^v = sigma and all other coefficients
-    zero (Eq. coeffsLangevinConst, kappa = -1 there):
+    With f^x = kappa v, g^vv = a psi(x), sigma^v = sigma sqrt(psi(x)) and all
+    other coefficients zero (Eq. coeffsLangevinConst with psi = 1, Eq.
+    coeffsLangevinVar with the paper's psi; kappa = -1 there):
         B = Bx + (a/2) Bvv,   A = sigma A0,
         Bx  = diag(vec F^x)(I (x) D^x),  F^x_ij = kappa v_j
-        Bvv = D^vv (x) I
-        A0  = D^v (x) I
+        Bvv = diag(vec Psi)(D^vv (x) I)
+        A0  = diag(vec Psi^(1/2))(D^v (x) I)
     Each is assembled through the general formula of `assemble` with unit
     coefficients, so time-dependent a(t), sigma(t) only rescale Bvv and A0.
     """
@@ -105,9 +123,10 @@ class LangevinOperators:
         self.xs, self.dx = grid(d, w.ax, w.bx)
         self.vs, self.dv = grid(d, w.av, w.bv)
         args = (d, w.ax, w.bx, d, w.av, w.bv)
+        psi = lambda x, v: x_profile(w, x)
         self.Bx, _ = assemble(*args, fx=lambda x, v: k * v)
-        self.Bvv, _ = assemble(*args, gvv=lambda x, v: 2.0)   # 1/2 * 2 = unit weight
-        _, self.A0 = assemble(*args, sv=lambda x, v: 1.0)
+        self.Bvv, _ = assemble(*args, gvv=lambda x, v: 2.0 * psi(x, v))   # 1/2 * 2 psi
+        _, self.A0 = assemble(*args, sv=lambda x, v: np.sqrt(psi(x, v)))
 
     def B(self, a: float):
         return (self.Bx + (0.5 * a) * self.Bvv).tocsr()

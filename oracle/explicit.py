@@ -52,6 +52,8 @@ def diffusion_cov(w):
 
 def terminal_gaussian(w, path_local: int):
     """Mean (x, v) and covariance (xx, xv, vv) of u_T / c0 for one path."""
+    if getattr(w, "x_profile", 0) != 0:
+        raise ValueError("no closed form with x-dependent coefficients (Section 3.2)")
     k = float(w.drift_sign)
     M = drift_matrix(k, w.T)
     m0 = np.asarray(w.u0_mean, float)

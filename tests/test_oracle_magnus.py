@@ -230,3 +230,52 @@ def test_moments_of_a_gaussian_grid_function():
     U = disc.gaussian_initial(w).T[None]
     m = errors.moments(U, xs, vs, dx, dv)[0]
     np.testing.assert_allclose(m, [3.0, 0.5, -1.0, 1.5, -0.3, 0.8], atol=1e-8)
+
+
+# ---------------------------------------------------------------- variable coefficients
+def _var(d=6, sigma=10 ** -0.5, n_fine=120, c=1.0):
+    from workloads import PAPER_VAR
+    return PAPER_VAR[0].with_(d=d, s0=sigma, n_fine=n_fine, paths=4, x_profile_c=c, ax=-3.0, bx=3.0,
+                              av=-3.0, bv=3.0)
+
+
+def test_variable_coefficient_deterministic_case_is_exact():
+    """sigma = 0 with the x profile: Omega = h B at every order, so K steps give exp(T B) u0."""
+    w = _var(d=6, sigma=0.0)
+    ops = disc.LangevinOperators(w)
+    u0 = disc.vec(disc.gaussian_initial(w))
+    exact = sla.expm(w.T * ops.B(w.a0).toarray()) @ u0
+    for order, K in ((1, 1), (2, 3), (3, 5)):
+        np.testing.assert_allclose(magnus.solve_path(w, order, K, 0).ravel(), exact, rtol=1e-11,
+                                   atol=1e-13 * np.abs(exact).max())
+
+
+def test_variable_coefficient_euler_step_matches_pointwise_formula():
+    w = _var(d=5, n_fine=10).with_(ax=-2.0, bx=2.0, av=-2.0, bv=2.0)
+    xs, dx = disc.grid(w.d, w.ax, w.bx)
+    vs, dv = disc.grid(w.d, w.av, w.bv)
+    u = disc.gaussian_initial(w)                         # (x, v)
+    dW = brownian.coarse_increments(w, 0, 1)[0]
+    new = np.zeros_like(u)
+    g = lambda i, j: u[i, j] if (0 <= i < w.d and 0 <= j < w.d) else 0.0
+    for i in range(w.d):
+        psi = 1.0 + 1.0 / (xs[i] ** 2 + 1.0)             # Eq. coeffsLangevinVar
+        for j in range(w.d):
+            ux = (g(i + 1, j) - g(i - 1, j)) / (2 * dx)
+            uv = (g(i, j + 1) - g(i, j - 1)) / (2 * dv)
+            uvv = (g(i, j + 1) - 2 * g(i, j) + g(i, j - 1)) / dv ** 2
+            new[i, j] = (u[i, j] + (-vs[j] * ux + 0.5 * w.a0 * psi * uvv) * w.T
+                         + w.s0 * math.sqrt(psi) * uv * dW)
+    np.testing.assert_allclose(euler.solve_path(w, 1, 0), new.T, atol=1e-14)
+
+
+def test_variable_coefficient_magnus_and_euler_meet():
+    """Two different schemes for the same SPDE: the fine Euler solution approaches the
+    order-3 Magnus solution as its step shrinks (Table errorsVar uses fine Euler as reference)."""
+    w = _var(d=12, n_fine=4000).with_(ax=-4.0, bx=4.0, av=-4.0, bv=4.0)
+    ref = magnus.solve(w, 3, 50, [0, 1])
+    e = [errors.Err(euler.solve(w, n, [0, 1]), ref) for n in (250, 4000)]
+    assert e[1] < e[0] / 2 and e[1] < 2e-3
+    # and the profile matters: the constant-coefficient solution is far away
+    ref0 = magnus.solve(w.with_(x_profile=0), 3, 50, [0, 1])
+    assert errors.Err(ref0, ref) > 10 * e[1]

@@ -154,3 +154,57 @@ def test_gaussian_initial_is_a_density():
     X, V = np.meshgrid(xs, vs, indexing="ij")
     assert (u * X).sum() * dx * dv == pytest.approx(0.3, abs=1e-6)
     assert (u * X * V).sum() * dx * dv - 0.3 * -0.2 == pytest.approx(0.2, abs=1e-6)
+
+
+# ---------------------------------------------------------------- variable coefficients
+def _var_case(d=7, c=1.0, a=1.1, s=0.3, kappa=-1):
+    from workloads import PAPER_VAR
+    return PAPER_VAR[0].with_(d=d, x_profile_c=c, a0=a, s0=s, drift_sign=kappa)
+
+
+def test_paper_profile_values():
+    w = _var_case()
+    # psi(0) = 2, psi(+-1) = 3/2, psi -> 1 far out (Eq. coeffsLangevinVar)
+    np.testing.assert_allclose(disc.x_profile(w, [0.0, 1.0, -1.0, 1e8]), [2.0, 1.5, 1.5, 1.0], rtol=1e-15)
+    # g^vv - (sigma^v)^2 = (a - sigma^2) psi: equals 1 everywhere only where psi = 1
+    # for the paper's a = 1.1, sigma^2 = 0.1 the difference is a psi - sigma^2 psi = psi
+    ws = _var_case(a=1.1, s=10 ** -0.5)
+    x = np.linspace(-4, 4, 9)
+    psi = disc.x_profile(ws, x)
+    np.testing.assert_allclose(ws.a0 * psi - (ws.s0 * np.sqrt(psi)) ** 2, psi, rtol=1e-14)
+
+
+@pytest.mark.parametrize("kappa", [1, -1])
+def test_variable_coefficient_operators_match_pointwise_stencils(kappa):
+    """B, A of the x-profile case against the pointwise finite-difference loops."""
+    w = _var_case(d=6, c=0.7, a=1.3, s=0.4, kappa=kappa).with_(ax=-3.0, bx=2.0, av=-2.5, bv=3.5)
+    ops = disc.LangevinOperators(w)
+    psi = lambda x: 1.0 + 0.7 / (1.0 + x * x)
+    zero = lambda x, v: 0.0 * x
+    c = dict(h=zero, fx=lambda x, v: kappa * v + 0 * x, fv=zero, gxx=zero, gxv=zero,
+             gvv=lambda x, v: 1.3 * psi(x), s=zero, sx=zero, sv=lambda x, v: 0.4 * np.sqrt(psi(x)))
+    Bb, Ab = _bruteforce(6, -3.0, 2.0, 6, -2.5, 3.5, c)
+    np.testing.assert_allclose(ops.B(1.3).toarray(), Bb, rtol=1e-13, atol=1e-12)
+    np.testing.assert_allclose(ops.A(0.4).toarray(), Ab, rtol=1e-13, atol=1e-12)
+
+
+def test_variable_coefficient_operators_have_kronecker_form():
+    """Bvv = D^vv (x) Psi and A0 = D^v (x) Psi^(1/2): the profile acts on the x index only."""
+    w = _var_case(d=9)
+    ops = disc.LangevinOperators(w)
+    xs, dx = disc.grid(9, w.ax, w.bx)
+    vs, dv = disc.grid(9, w.av, w.bv)
+    Psi = sp.diags(disc.x_profile(w, xs))
+    np.testing.assert_allclose(ops.Bvv.toarray(), sp.kron(disc.d_second(9, dv), Psi).toarray(), rtol=1e-14)
+    np.testing.assert_allclose(ops.A0.toarray(), sp.kron(disc.d_first(9, dv), Psi.sqrt()).toarray(), rtol=1e-14)
+    # the profile does not commute with D^x, so [Bx, A0] picks up the x-derivative of sqrt(psi)
+    C = comm(ops.Bx, ops.A0).toarray()
+    w1 = w.with_(x_profile=0)
+    C1 = comm(disc.LangevinOperators(w1).Bx, disc.LangevinOperators(w1).A0).toarray()
+    assert np.abs(C - C1).max() > 1e-3
+
+
+def test_no_closed_form_with_a_profile():
+    from oracle import explicit
+    with pytest.raises(ValueError):
+        explicit.solution(_var_case(), 0)

@@ -22,6 +22,11 @@ from typing import Tuple
 COEF_CONST = 0
 COEF_TRIG = 1
 
+# x profile psi of the variable-coefficient operators (Eq. coeffsLangevinVar):
+# g^vv(x) = a psi(x), sigma^v(x) = sigma sqrt(psi(x)).
+XPROF_NONE = 0        # psi = 1: the constant-coefficient operators
+XPROF_RATIONAL = 1    # psi(x) = 1 + c / (1 + x^2); c = 1 is the paper's choice
+
 
 @dataclass(frozen=True)
 class Workload:
@@ -43,6 +48,8 @@ class Workload:
     paths        number of Brownian paths
     seed         64-bit Philox key
     path_offset  global index of the first path (paths are keyed by global index)
+    x_profile    XPROF_NONE or XPROF_RATIONAL (x-dependent g^vv and sigma^v)
+    x_profile_c  the constant c of the rational profile
     """
 
     name: str
@@ -65,6 +72,8 @@ class Workload:
     paths: int = 100
     seed: int = 20220719
     path_offset: int = 0
+    x_profile: int = XPROF_NONE
+    x_profile_c: float = 1.0
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
@@ -108,6 +117,18 @@ PAPER_CONST = Workload(
     name="paper_langevin_const", d=100, ax=-4.0, bx=4.0, av=-4.0, bv=4.0,
     drift_sign=-1, kind=COEF_CONST, a0=1.1, s0=10.0 ** -0.5,
     u0_scale=2.0 * 3.141592653589793, T=1.0, n_fine=10_000, paths=100, seed=2207)
+
+
+# The paper's variable-coefficient setting (Section 3.2, Table errorsVar): the
+# constant case above with g^vv = a (1 + 1/(x^2+1)), sigma^v = sigma sqrt(1 + 1/(x^2+1)),
+# d = 100, 200, 300; the reference is Euler-Maruyama with step 1e-5, so the fine
+# Brownian grid has 10^5 cells on [0, 1].
+PAPER_VAR = tuple(
+    Workload(name=f"paper_langevin_var_d{d}", d=d, ax=-4.0, bx=4.0, av=-4.0, bv=4.0,
+             drift_sign=-1, kind=COEF_CONST, a0=1.1, s0=10.0 ** -0.5,
+             u0_scale=2.0 * 3.141592653589793, T=1.0, n_fine=100_000, paths=100, seed=2208,
+             x_profile=XPROF_RATIONAL, x_profile_c=1.0)
+    for d in (100, 200, 300))
 
 
 def path_range(paths: int, rank: int, world: int) -> Tuple[int, int]:
