@@ -51,6 +51,7 @@ typedef enum {
 } msk_status;
 
 enum { MSK_COEF_CONST = 0, MSK_COEF_TRIG = 1 };
+enum { MSK_XPROF_NONE = 0, MSK_XPROF_RATIONAL = 1, MSK_XPROF_VALUES = 2 };
 enum { MSK_F64 = 0, MSK_F32 = 1 };
 enum { MSK_REF_EXPLICIT = 0, MSK_REF_BUFFER = 1 };
 
@@ -104,7 +105,12 @@ typedef struct {
  * difference operators and the thirteen basis-operator band tables on the
  * device (Section 2, "Computation of A and B"; commutators of
  * Eq. MagnusFormulas).  Defaults: drift +1, a = 1, sigma = 0.5, standard
- * Gaussian density, seed 0, n_fine 10000, T 1.  *out is NULL on failure. */
+ * Gaussian density, seed 0, n_fine 10000, T 1, no x profile.  *out is NULL
+ * on failure.  nx = nv = d with 8 <= d <= 512 (else MSK_ERR_ARG); the
+ * constant-coefficient engine is built for d = 32, 64, 128, 256, 512 (float)
+ * and 32 .. 256 (double), the variable-coefficient engine (msk_set_x_profile)
+ * for any d whose five-field slab fits a cluster of at most 16 CTAs; other
+ * combinations fail at solve time with MSK_ERR_UNSUPPORTED. */
 msk_status msk_create(msk_ctx** out, const msk_grid* grid, int device);
 
 /* Release the context and every library-owned device buffer.  NULL is a no-op.
@@ -118,6 +124,26 @@ const char* msk_last_error(const msk_ctx* ctx);
 
 /* Set the coefficient profile (see msk_coeffs).  Non-finite values -> MSK_ERR_NONFINITE. */
 msk_status msk_set_coefficients(msk_ctx* ctx, const msk_coeffs* coeffs);
+
+/* Variable coefficients in x (Section 3.2, Eq. coeffsLangevinVar):
+ *   g^vv(x, v) = a(t) psi(x),   sigma^v(x, v) = sigma(t) sqrt(psi(x)),
+ * so that Bvv = D^vv (x) Psi and A0 = D^v (x) Psi^(1/2) with Psi = diag(psi(x_i)).
+ *   kind MSK_XPROF_NONE      psi = 1 (the constant-coefficient operators; default)
+ *   kind MSK_XPROF_RATIONAL  psi(x) = 1 + c / (1 + x^2), evaluated on the x nodes on
+ *                            the device (c = 1 is the paper's choice); c >= 0
+ *   kind MSK_XPROF_VALUES    psi_host[i] = psi(x_i), i = 0 .. d-1 (host, copied), all > 0
+ * With a profile, msk_solve_magnus / msk_solve_magnus_noalloc /
+ * msk_magnus_from_weights / msk_solve_euler / msk_select_steps run the
+ * variable-coefficient engine, which applies Omega by composing the two base
+ * operators B and A0 (exact truncated products) instead of folded stencils.
+ * Magnus then needs constant coefficients (MSK_COEF_CONST; time-dependent
+ * ones -> MSK_ERR_UNSUPPORTED; Euler accepts both), and msk_magnus_from_weights
+ * reads only the weights of BX, A0, A0A0, BX_A0, BXA0_A0 and BXA0_BX, the others
+ * being implied (B = Bx + a/2 Bvv).  msk_apply_omega, msk_explicit_solution,
+ * msk_error with MSK_REF_EXPLICIT and batches -> MSK_ERR_UNSUPPORTED (no closed
+ * form exists).  Invalid kind, c < 0, non-positive or non-finite values ->
+ * MSK_ERR_ARG / MSK_ERR_NONFINITE before any device work. */
+msk_status msk_set_x_profile(msk_ctx* ctx, int kind, double c, const double* psi_host);
 
 /* Set a Gaussian initial datum; evaluated on the interior grid on the device. */
 msk_status msk_set_initial_gaussian(msk_ctx* ctx, const msk_gaussian* g);

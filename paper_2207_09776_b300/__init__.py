@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "libmsk.so")
 
 MSK_OK, MSK_ERR_ARG, MSK_ERR_CUDA, MSK_ERR_OOM, MSK_ERR_TIMEOUT, MSK_ERR_NONFINITE, MSK_ERR_UNSUPPORTED = range(7)
 MSK_COEF_CONST, MSK_COEF_TRIG = 0, 1
+MSK_XPROF_NONE, MSK_XPROF_RATIONAL, MSK_XPROF_VALUES = 0, 1, 2
 MSK_F64, MSK_F32 = 0, 1
 MSK_REF_EXPLICIT, MSK_REF_BUFFER = 0, 1
 MSK_PATH_NONFINITE, MSK_PATH_SCALE_CAP, MSK_PATH_BLOWUP = 1, 2, 4
@@ -71,6 +72,7 @@ SIGNATURES = {
     "msk_last_error": (ctypes.c_char_p, [_P]),
     "msk_set_coefficients": (_INT, [_P, ctypes.POINTER(msk_coeffs)]),
     "msk_set_initial_gaussian": (_INT, [_P, ctypes.POINTER(msk_gaussian)]),
+    "msk_set_x_profile": (_INT, [_P, _INT, _DBL, _P]),
     "msk_set_initial": (_INT, [_P, _P, _P]),
     "msk_set_seed": (_INT, [_P, _U64, _U64, _I64, _DBL]),
     "msk_philox_words": (_INT, [_U64, _U64, ctypes.c_uint32, _I64, _I64, _P, _P]),
@@ -195,6 +197,15 @@ def msk_last_error(ctx) -> str:
 
 def msk_set_coefficients(ctx, drift_sign, kind, a0, a1, s0, s1):
     _check(load_library().msk_set_coefficients(ctx, ctypes.byref(msk_coeffs(drift_sign, kind, a0, a1, s0, s1))), ctx)
+
+
+def msk_set_x_profile(ctx, kind, c=1.0, psi=None):
+    """psi: None, or a sequence of d host values for MSK_XPROF_VALUES."""
+    buf = None
+    if psi is not None:
+        vals = [float(x) for x in psi]
+        buf = (ctypes.c_double * len(vals))(*vals)
+    _check(load_library().msk_set_x_profile(ctx, kind, c, ctypes.cast(buf, _P) if buf is not None else None), ctx)
 
 
 def msk_set_initial_gaussian(ctx, mean, cov, scale=1.0):
@@ -489,6 +500,8 @@ class Solver:
         msk_set_coefficients(self.ctx, w.drift_sign, w.kind, w.a0, w.a1, w.s0, w.s1)
         msk_set_initial_gaussian(self.ctx, w.u0_mean, w.u0_cov, w.u0_scale)
         msk_set_seed(self.ctx, w.seed, w.path_offset, w.n_fine, w.T)
+        if getattr(w, "x_profile", MSK_XPROF_NONE) != MSK_XPROF_NONE:
+            msk_set_x_profile(self.ctx, w.x_profile, getattr(w, "x_profile_c", 1.0))
 
     def close(self):
         if self.ctx:

@@ -35,7 +35,7 @@ msk_status msk_ensure_scratch(msk_ctx* ctx, size_t bytes) {
   return MSK_OK;
 }
 
-bool msk_supported_d(int d) { return d == 32 || d == 64 || d == 128 || d == 256 || d == 512; }
+bool msk_supported_d(int d) { return d >= 8 && d <= 512; }
 
 static bool is_fin(double x) { return isfinite(x) != 0; }
 
@@ -53,6 +53,8 @@ extern "C" void msk_destroy(msk_ctx* ctx) {
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (ctx->work) cudaFree(ctx->work);
   if (ctx->tab) cudaFree(ctx->tab);
+  if (ctx->psi) cudaFree(ctx->psi);
+  if (ctx->var_tab) cudaFree(ctx->var_tab);
   delete ctx;
 }
 
@@ -106,6 +108,7 @@ extern "C" msk_status msk_set_coefficients(msk_ctx* ctx, const msk_coeffs* c) {
   msk_status st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
   if (st != MSK_OK) return st;
   const bool rebuild = c->drift_sign != ctx->coef.drift_sign;
+  if (rebuild || c->a0 != ctx->coef.a0) ctx->var_dirty = true;
   ctx->coef = *c;
   if (rebuild) return launch_band_tables(ctx, 0);
   return MSK_OK;

@@ -98,6 +98,7 @@ msk_status launch_engine(msk_ctx* ctx, bool euler, int steps, int64_t paths, int
                          const double* Wt, const double* dW, void* out, uint32_t* status,
                          cudaStream_t stream) {
   if (paths == 0) return MSK_OK;
+  if (ctx->xprof) return launch_engine_var(ctx, euler, steps, paths, precision, Wt, dW, out, status, stream);
   EngineArgs a;
   a.band = ctx->band;
   a.u0 = ctx->u0;

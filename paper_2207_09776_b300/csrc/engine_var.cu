@@ -1,0 +1,798 @@
+// Variable-coefficient engine (Section 3.2, Eq. coeffsLangevinVar).
+//
+// With g^vv = a psi(x) and sigma^v = sigma sqrt(psi(x)) the Langevin operators are
+//   B = Bx + alpha Bvv,  Bx = kappa diag(v) (x) D^x,  Bvv = D^vv (x) Psi,  alpha = a/2,
+//   A = sigma A0,        A0 = D^v (x) Psi^(1/2),      Psi = diag(psi(x_i)),
+// no longer constant along x, so the per-v-row widened stencils of the
+// constant-coefficient engine do not apply.  Constant a and sigma keep the
+// six-term logarithm of Eq. MagnusFormulas,
+//   Omega = wB B + wA A0 + wAA A0^2 + wBA [B,A0] + wBAA [[B,A0],A0] + wBAB [[B,A0],B]
+// (sigma and the Brownian functionals folded into the weights), and every
+// Taylor term applies it by composing the two base operators.  Each has radius
+// one and is applied with zero padding outside the grid, which reproduces the
+// products of the truncated matrices exactly, boundary rows included:
+//   pass 1:  a = A0 t,  b = B t
+//   pass 2:  p = wB t + wBA a + wBAA A0 a + wBAB (2 A0 b - B a)
+//            q = wA t + wAA a - wBA b + wBAA (A0 b - 2 B a) - wBAB B b
+//   pass 3:  (Omega - mu) t = B p + A0 q - mu t
+// (expanding [[B,A0],A0] = B A0 A0 - 2 A0 B A0 + A0 A0 B and
+// [[B,A0],B] = 2 B A0 B - A0 B B - B B A0 and grouping by the last factor).
+// Passes 1 and 2 are fused: a thread evaluates a and b itself at the five
+// points of its own point's neighbourhood that pass 2 needs (values at points
+// outside the grid are zero, as in the truncated products), so a Taylor term
+// costs two passes and two barriers:
+//   pass A:  t -> p, q        pass B:  p, q -> next term (and partial sum)
+// Euler-Maruyama (Eq. EulerMaruyama) is one pass per step:
+//   t + dt (Bx + alpha(t_n) Bvv) t + sigma(t_n) dW_n A0 t.
+//
+// Layout.  One path per cluster of C CTAs (1 <= C <= 16, the smallest C whose
+// slab of ceil(d/C) v-rows fits in shared memory while keeping the SMs busy).
+// Three fields t, p, q with two halo rows above and below and two zero columns
+// on each side, and the Taylor partial sum at the CTA's own points.  A thread
+// owns one grid column and a strip of consecutive rows and slides a window of
+// rows down the strip.  Halo rows facing another CTA are written by that CTA
+// (shared::cluster stores) as it stores its own edge rows, so a pass reads only
+// local shared memory.  The next term overwrites t in place in pass B (each
+// thread reads only its own point of t there).  The Taylor parameters
+// (s, m, mu) come from the weights kernel with the exact traces and shifted
+// infinity norms of the six operators (var_*_kernel below).
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "msk_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+extern const double kMskScaleCap;
+
+namespace {
+
+constexpr int kVarFields = 3;
+constexpr int kVarMaxTerms = 64;        // >= the largest Taylor degree of either theta table
+constexpr int kVarMaxThreads = 512;
+constexpr size_t kVarSmemCap = 232448;  // 227 KB per CTA
+constexpr int kVarNormBlocks = 32;      // blocks per operator in the norm kernels
+constexpr int kVarOps = 6;
+
+struct VarArgs {
+  const double* u0;
+  const double* Wt;   // Magnus: [paths][steps][MSK_NWT]
+  const double* dW;   // Euler:  [paths][steps]
+  const double* psi;  // [d]
+  void* out;
+  uint32_t* status;
+  unsigned long long* work;
+  int64_t paths;
+  int steps, d, C, RS, tpr, R;
+  double dx, dv, av, kappa, T, s_cap;
+  float tol32;
+  double tol64;
+  CoefDev c;
+};
+
+// Shared memory of one CTA in elements of T: three fields of (RS + 4) x W
+// (W = d + 4), the partial sum [RS][d], the per-row Bx coefficient of the rows
+// -2 .. RS+1, 1/(s k), and the norm slots.  (All offsets fit 32 bits: the
+// layout is capped at 227 KB.)
+struct VarLayout {
+  int FS, off_acc, off_cx, off_scale, off_slot, off_cslot, total;
+};
+__host__ __device__ inline VarLayout var_layout(int RS, int d, int NT) {
+  VarLayout L;
+  L.FS = (RS + 4) * (d + 4);
+  L.off_acc = kVarFields * L.FS;
+  L.off_cx = L.off_acc + RS * d;
+  L.off_scale = L.off_cx + RS + 4;
+  L.off_slot = L.off_scale + kVarMaxTerms + 1;
+  L.off_cslot = L.off_slot + 4 * (NT / 32);
+  L.total = L.off_cslot + 4;
+  return L;
+}
+
+__device__ __forceinline__ uint32_t cl_addr(const void* p, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cl_st(uint32_t addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void cl_st(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ float cl_ld(uint32_t addr, float) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ double cl_ld(uint32_t addr, double) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+template <typename T> __device__ __forceinline__ T vabsnan(T x) { return (x == x) ? fabs(x) : T(INFINITY); }
+
+__device__ __forceinline__ double var_sigma_t(const CoefDev& c, double t) {
+  return c.s0 * (1.0 + c.s1 * cospi(2.0 * t));
+}
+__device__ __forceinline__ double var_alpha_t(const CoefDev& c, double t) {
+  return 0.5 * (c.a0 + c.a1 * sinpi(2.0 * t));
+}
+
+template <typename T, bool EULER>
+__global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const VarArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x, NT = blockDim.x, NW = NT >> 5;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int C = a.C, RS = a.RS, d = a.d, W = d + 4;
+  const int rank = C > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const VarLayout L = var_layout(RS, d, NT);
+  const int FS = L.FS;
+  T* accs = sm + L.off_acc;
+  T* cxr = sm + L.off_cx + 2;   // cxr[p], p in [-2, RS + 1]
+  T* scale_tab = sm + L.off_scale;
+  T* slots = sm + L.off_slot;
+  T* cslot = sm + L.off_cslot;
+
+  auto sync_all = [&]() {
+    if (C > 1) cg::this_cluster().sync();
+    else __syncthreads();
+  };
+
+  const int r0 = rank * RS;          // first global v-row of this CTA
+  const int rs = min(RS, d - r0);    // rows held by this CTA
+  const int col = tid % a.tpr, grp = tid / a.tpr;
+  const bool act = col < d;
+  const int p0 = grp * a.R;
+  const int nrows = act ? max(0, min(a.R, rs - p0)) : 0;
+
+  // zero the fields once: grid-boundary halos and pad columns are never written again
+  for (int e = tid; e < kVarFields * FS; e += NT) sm[e] = T(0);
+  for (int p = tid - 2; p < RS + 2; p += NT) {
+    const int jg = r0 + p;
+    const double v = a.av + (double)(jg + 1) * a.dv;
+    cxr[p] = (jg >= 0 && jg < d) ? (T)(a.kappa * v * (0.5 / a.dx)) : T(0);   // Bx: kappa v_j / (2 dx)
+  }
+  // column constants of the own column and its two neighbours (zero outside the grid)
+  auto colc = [&](int c, T& cvb, T& cav, T& cvv) {
+    if (c >= 0 && c < d) {
+      const double ps = a.psi[c];
+      cvb = (T)(0.5 * a.c.a0 * ps / (a.dv * a.dv));   // alpha Bvv: alpha psi / dv^2 (x) (1, -2, 1)
+      cav = (T)(sqrt(ps) * (0.5 / a.dv));             // A0: sqrt(psi) / (2 dv) (x) (-1, 0, 1)
+      cvv = (T)(ps / (a.dv * a.dv));
+    } else {
+      cvb = cav = cvv = T(0);
+    }
+  };
+  T cvB, ca, cvv, cvBL, caL, cvvL, cvBR, caR, cvvR;
+  colc(act ? col : -1, cvB, ca, cvv);
+  colc(act ? col - 1 : -1, cvBL, caL, cvvL);
+  colc(act ? col + 1 : -1, cvBR, caR, cvvR);
+  const T mL = (act && col > 0) ? T(1) : T(0), mR = (act && col < d - 1) ? T(1) : T(0);
+  sync_all();   // every CTA zeroed before any halo store reaches it
+
+  const uint32_t peer_lo = (C > 1 && rank > 0) ? cl_addr(sm, rank - 1) : 0u;
+  const uint32_t peer_hi = (C > 1 && rank < C - 1) ? cl_addr(sm, rank + 1) : 0u;
+  // element offset of (local row p in [-2, RS + 1], own column) in field f
+  auto at = [&](int f, int p) -> int { return f * FS + (p + 2) * W + col + 2; };
+  // store an own point, and its copy in the facing halo (depth `hd`) of the neighbour CTA
+  auto store = [&](int f, int p, T v, int hd) {
+    sm[at(f, p)] = v;
+    if (C > 1) {
+      if (p < hd && rank > 0) cl_st(peer_lo + (uint32_t)(at(f, RS + p) * (int)sizeof(T)), v);
+      if (p >= rs - hd && rank < C - 1) cl_st(peer_hi + (uint32_t)(at(f, p - rs) * (int)sizeof(T)), v);
+    }
+  };
+
+  // Norms: per-warp maxima in shared memory; with clusters warp 0 folds them
+  // into one CTA slot and every warp reads the C slots after the barrier.
+  auto publish = [&](int par, T mn, T ma) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      mn = vmax(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+      ma = vmax(ma, __shfl_xor_sync(0xffffffffu, ma, off));
+    }
+    if (lane == 0) {
+      slots[(par * NW + warp) * 2 + 0] = mn;
+      slots[(par * NW + warp) * 2 + 1] = ma;
+    }
+    if (C > 1) {
+      __syncthreads();
+      if (warp == 0) {
+        T x = T(0), y = T(0);
+        for (int q = lane; q < NW; q += 32) {
+          x = vmax(x, slots[(par * NW + q) * 2 + 0]);
+          y = vmax(y, slots[(par * NW + q) * 2 + 1]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          x = vmax(x, __shfl_xor_sync(0xffffffffu, x, off));
+          y = vmax(y, __shfl_xor_sync(0xffffffffu, y, off));
+        }
+        if (lane == 0) {
+          cslot[par * 2 + 0] = x;
+          cslot[par * 2 + 1] = y;
+        }
+      }
+    }
+  };
+  auto gather = [&](int par, T& gn, T& ga) {
+    gn = T(0);
+    ga = T(0);
+    if (C > 1) {
+      if (lane < C) {
+        const uint32_t q = cl_addr(cslot + par * 2, lane);
+        gn = cl_ld(q, T(0));
+        ga = cl_ld(q + (uint32_t)sizeof(T), T(0));
+      }
+    } else {
+      for (int q = lane; q < NW; q += 32) {
+        gn = vmax(gn, slots[(par * NW + q) * 2 + 0]);
+        ga = vmax(ga, slots[(par * NW + q) * 2 + 1]);
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      gn = vmax(gn, __shfl_xor_sync(0xffffffffu, gn, off));
+      ga = vmax(ga, __shfl_xor_sync(0xffffffffu, ga, off));
+    }
+  };
+  // row mask: 1 for rows of the grid, 0 for the halo rows beyond its boundary
+  auto rowm = [&](int p) -> T { return (r0 + p >= 0 && r0 + p < d) ? T(1) : T(0); };
+
+  const T tol = sizeof(T) == 4 ? (T)a.tol32 : (T)a.tol64;
+  const int64_t cid = blockIdx.x / C, ncl = gridDim.x / C;
+  constexpr int FT = 0, FP = 1, FQ = 2;
+  int par = 0;
+
+  for (int64_t path = cid; path < a.paths; path += ncl) {
+    int ft = FT, fo = FP;   // Euler ping-pongs t between fields 0 and 1
+    T m0 = T(0);
+    for (int r = 0; r < nrows; ++r) {
+      const int p = p0 + r;
+      const T v = (T)a.u0[(size_t)(r0 + p) * d + col];
+      accs[p * d + col] = v;
+      store(ft, p, v, 2);
+      m0 = vmax(m0, vabsnan(v));
+    }
+    publish(par, m0, m0);
+    sync_all();
+    T unorm, u0max;
+    gather(par, unorm, u0max);
+    par ^= 1;
+    bool scale_cap = false;
+    unsigned long long nmv = 0;
+
+    for (int n = 0; n < a.steps; ++n) {
+      if constexpr (EULER) {
+        const double dt = a.T / a.steps, tn = n * dt;
+        const double dWn = a.dW[path * a.steps + n];
+        const T kx = (T)dt;
+        const T kv = (T)(var_alpha_t(a.c, tn) * dt) * cvv;
+        const T ka = (T)(var_sigma_t(a.c, tn) * dWn) * ca;
+        if (nrows > 0) {
+          const T* t = sm + ft * FS;
+          int o = at(ft, p0) - ft * FS;
+          T up = t[o - W], ce = t[o];
+          for (int r = 0; r < nrows; ++r, o += W) {
+            const T dn = t[o + W], l = t[o - 1], rr = t[o + 1];
+            const T tn_ = fma(kx * cxr[p0 + r], rr - l, fma(kv, fma(T(-2), ce, dn + up), fma(ka, dn - up, ce)));
+            store(fo, p0 + r, tn_, 2);
+            accs[(p0 + r) * d + col] = tn_;
+            up = ce;
+            ce = dn;
+          }
+        }
+        sync_all();
+        const int sw = ft;
+        ft = fo;
+        fo = sw;
+        ++nmv;
+      } else {
+        const double* rec = a.Wt + ((size_t)path * a.steps + n) * MSK_NWT;
+        const T wB = (T)rec[MSK_OP_BX], wA = (T)rec[MSK_OP_A0], wAA = (T)rec[MSK_OP_A0A0];
+        const T wBA = (T)rec[MSK_OP_BX_A0], wBAA = (T)rec[MSK_OP_BXA0_A0], wBAB = (T)rec[MSK_OP_BXA0_BX];
+        const double mu = rec[MSK_WT_MU];
+        const int s_steps = max(1, (int)rec[MSK_WT_S]);
+        const int m_terms = min((int)rec[MSK_WT_M], kVarMaxTerms);
+        if (rec[MSK_WT_S] >= a.s_cap) scale_cap = true;
+        const T te = (T)exp(mu / s_steps);
+        for (int k = tid; k <= kVarMaxTerms; k += NT)
+          scale_tab[k] = (T)(k == 0 ? 1.0 : 1.0 / ((double)s_steps * k));
+        __syncthreads();
+
+        for (int sub = 0; sub < s_steps; ++sub) {
+          T c1 = unorm;   // norm of the previous Taylor term (term 0 = the state)
+          for (int k = 1; k <= m_terms; ++k) {
+            const T sc = scale_tab[k];
+            const T scmu = (T)(mu / ((double)s_steps * k));
+            // ---- pass A: p, q at the own points from t (a = A0 t and b = B t
+            // evaluated at the own point and its four neighbours, zero off the grid)
+            if (nrows > 0) {
+              const T* t = sm + FT * FS;
+              int o = at(FT, p0) - FT * FS;   // row p0, own column
+              // window: rows p-1 .. p+1 of the own and both side columns
+              T c0 = t[o - W], c1_ = t[o], c2 = t[o + W];
+              T l0 = t[o - W - 1], l1 = t[o - 1], l2 = t[o + W - 1];
+              T q0 = t[o - W + 1], q1 = t[o + 1], q2 = t[o + W + 1];
+              // a, b of rows p0-1 and p0 in the own column
+              T am, a0, bm, b0;
+              {
+                const T cm2 = t[o - 2 * W];
+                const T mrow = rowm(p0 - 1);
+                am = mrow * ca * (c1_ - cm2);
+                bm = mrow * fma(cxr[p0 - 1], q0 - l0, cvB * fma(T(-2), c0, c1_ + cm2));
+                a0 = ca * (c2 - c0);
+                b0 = fma(cxr[p0], q1 - l1, cvB * fma(T(-2), c1_, c2 + c0));
+              }
+              for (int r = 0; r < nrows; ++r, o += W) {
+                const int p = p0 + r;
+                const T c3 = t[o + 2 * W];
+                const T xl = t[o - 2], xr = t[o + 2];
+                const T cx = cxr[p];
+                // a, b one row down in the own column (zero beyond the grid)
+                const T mdn = rowm(p + 1);
+                const T ap = mdn * ca * (c3 - c1_);
+                const T bp = mdn * fma(cxr[p + 1], q2 - l2, cvB * fma(T(-2), c2, c3 + c1_));
+                // a, b at the two side columns of the own row (zero beyond the grid)
+                const T aL = mL * caL * (l2 - l0), aR = mR * caR * (q2 - q0);
+                const T bL = mL * fma(cx, c1_ - xl, cvBL * fma(T(-2), l1, l2 + l0));
+                const T bR = mR * fma(cx, xr - c1_, cvBR * fma(T(-2), q1, q2 + q0));
+                const T aa = ca * (ap - am), ab = ca * (bp - bm);
+                const T ba = fma(cx, aR - aL, cvB * fma(T(-2), a0, ap + am));
+                const T bb = fma(cx, bR - bL, cvB * fma(T(-2), b0, bp + bm));
+                const T P = fma(wB, c1_, fma(wBA, a0, fma(wBAA, aa, wBAB * fma(T(2), ab, -ba))));
+                const T Q = fma(wA, c1_, fma(wAA, a0, fma(-wBA, b0, fma(wBAA, fma(T(-2), ba, ab), -wBAB * bb))));
+                store(FP, p, P, 1);
+                store(FQ, p, Q, 1);
+                // slide the window one row down
+                am = a0; a0 = ap; bm = b0; b0 = bp;
+                c0 = c1_; c1_ = c2; c2 = c3;
+                l0 = l1; l1 = l2; l2 = t[o + 2 * W - 1];
+                q0 = q1; q1 = q2; q2 = t[o + 2 * W + 1];
+              }
+            }
+            sync_all();
+            // ---- pass B: next term (B p + A0 q - mu t) / (s k), in place of t
+            T mn = T(0), ma = T(0);
+            if (nrows > 0) {
+              const T* Pf = sm + FP * FS;
+              const T* Qf = sm + FQ * FS;
+              T* t = sm + FT * FS;
+              int o = at(FT, p0) - FT * FS;
+              T pu = Pf[o - W], pc = Pf[o], qu = Qf[o - W], qc = Qf[o];
+              for (int r = 0; r < nrows; ++r, o += W) {
+                const int p = p0 + r;
+                const T pd = Pf[o + W], qd = Qf[o + W], pl = Pf[o - 1], pr = Pf[o + 1];
+                const T Bp = fma(cxr[p], pr - pl, cvB * fma(T(-2), pc, pd + pu));
+                const T tn_ = fma(sc, fma(ca, qd - qu, Bp), -scmu * t[o]);
+                store(FT, p, tn_, 2);
+                T& ac = accs[p * d + col];
+                const T s_ = ac + tn_;
+                ac = s_;
+                mn = vmax(mn, fabs(tn_));
+                ma = vmax(ma, fabs(s_));
+                pu = pc;
+                pc = pd;
+                qu = qc;
+                qc = qd;
+              }
+            }
+            publish(par, mn, ma);
+            sync_all();
+            T gn, ga;
+            gather(par, gn, ga);
+            par ^= 1;
+            ++nmv;
+            unorm = ga;
+            if (c1 + gn <= tol * ga) break;
+            c1 = gn;
+          }
+          // u <- e^{mu/s} (partial sum), which is also the next sub-step's t
+          for (int r = 0; r < nrows; ++r) {
+            T& ac = accs[(p0 + r) * d + col];
+            const T v = ac * te;
+            ac = v;
+            store(FT, p0 + r, v, 2);
+          }
+          unorm = unorm * te;
+          sync_all();
+        }
+      }
+    }
+
+    // ---- solution, work counter and path status
+    T mfin = T(0);
+    for (int r = 0; r < nrows; ++r) {
+      const T v = accs[(p0 + r) * d + col];
+      reinterpret_cast<T*>(a.out)[(size_t)path * d * d + (size_t)(r0 + p0 + r) * d + col] = v;
+      mfin = vmax(mfin, vabsnan(v));
+    }
+    if (a.work && rank == 0 && tid == 0) atomicAdd(a.work, nmv);
+    publish(par, mfin, mfin);
+    sync_all();
+    T gfin, gfin2;
+    gather(par, gfin, gfin2);
+    par ^= 1;
+    if (a.status && rank == 0 && tid == 0) {
+      uint32_t st = 0;
+      if (!(gfin < T(INFINITY))) st |= MSK_PATH_NONFINITE;
+      if (scale_cap) st |= MSK_PATH_SCALE_CAP;
+      if (!((double)gfin <= 10.0 * (double)u0max)) st |= MSK_PATH_BLOWUP;
+      a.status[path] = st;
+    }
+    sync_all();   // nobody may still read this path's fields or slots
+  }
+}
+
+// ------------------------------------------------------------------ operator norms
+// Row (i, j) of each of the six operators, accumulated on a 7 x 7 patch around
+// the point by multiplying the unit row vector from the right by the base
+// operators of each word (B = 0, A0 = 1); entries that would leave the grid are
+// dropped, as in the truncated matrices.
+struct VarOpsDev {
+  int d;
+  double kx;      // kappa / (2 dx)
+  double av, dv;  // v grid
+  double alpha;   // a0 / 2
+  const double* psi;
+};
+
+__device__ void add_base_row(const VarOpsDev& o, int op, int i, int j, double c, int pi, int pj,
+                             double (&out)[7][7]) {
+  auto put = [&](int ii, int jj, double v) {
+    if (ii >= 0 && ii < o.d && jj >= 0 && jj < o.d) out[jj - pj + 3][ii - pi + 3] += c * v;
+  };
+  const double psi = o.psi[i];
+  if (op == 0) {
+    const double gx = o.kx * (o.av + (double)(j + 1) * o.dv);
+    const double gv = o.alpha * psi / (o.dv * o.dv);
+    put(i + 1, j, gx);
+    put(i - 1, j, -gx);
+    put(i, j + 1, gv);
+    put(i, j - 1, gv);
+    put(i, j, -2.0 * gv);
+  } else {
+    const double ga = sqrt(psi) * (0.5 / o.dv);
+    put(i, j + 1, ga);
+    put(i, j - 1, -ga);
+  }
+}
+
+// words of the six operators: coefficient, length, letters
+struct VarWord {
+  double c;
+  int len;
+  int w[3];
+};
+__constant__ VarWord c_var_words[12] = {
+    {1.0, 1, {0, 0, 0}},                                              // B
+    {1.0, 1, {1, 0, 0}},                                              // A0
+    {1.0, 2, {1, 1, 0}},                                              // A0 A0
+    {1.0, 2, {0, 1, 0}},  {-1.0, 2, {1, 0, 0}},                      // [B, A0]
+    {1.0, 3, {0, 1, 1}},  {-2.0, 3, {1, 0, 1}}, {1.0, 3, {1, 1, 0}}, // [[B, A0], A0]
+    {2.0, 3, {0, 1, 0}},  {-1.0, 3, {1, 0, 0}}, {-1.0, 3, {0, 0, 1}} // [[B, A0], B]
+};
+__constant__ int c_var_first[kVarOps + 1] = {0, 1, 2, 3, 5, 8, 11};
+
+__device__ void op_row(const VarOpsDev& o, int op, int pi, int pj, double (&row)[7][7]) {
+  for (int y = 0; y < 7; ++y)
+    for (int x = 0; x < 7; ++x) row[y][x] = 0.0;
+  for (int q = c_var_first[op]; q < c_var_first[op + 1]; ++q) {
+    const VarWord wd = c_var_words[q];
+    double cur[7][7], nxt[7][7];
+    for (int y = 0; y < 7; ++y)
+      for (int x = 0; x < 7; ++x) cur[y][x] = 0.0;
+    cur[3][3] = 1.0;
+    for (int l = 0; l < wd.len; ++l) {
+      for (int y = 0; y < 7; ++y)
+        for (int x = 0; x < 7; ++x) nxt[y][x] = 0.0;
+      for (int y = 0; y < 7; ++y)
+        for (int x = 0; x < 7; ++x)
+          if (cur[y][x] != 0.0) add_base_row(o, wd.w[l], pi + x - 3, pj + y - 3, cur[y][x], pi, pj, nxt);
+      for (int y = 0; y < 7; ++y)
+        for (int x = 0; x < 7; ++x) cur[y][x] = nxt[y][x];
+    }
+    for (int y = 0; y < 7; ++y)
+      for (int x = 0; x < 7; ++x) row[y][x] += wd.c * cur[y][x];
+  }
+}
+
+// partial traces: block (op, b) sums the diagonal over points b*256+tid, stride NB*256
+__global__ void var_trace_kernel(VarOpsDev o, double* part) {
+  const int op = blockIdx.x, b = blockIdx.y, NB = gridDim.y;
+  const int n = o.d * o.d;
+  double s = 0.0;
+  for (int P = b * blockDim.x + threadIdx.x; P < n; P += NB * blockDim.x) {
+    double row[7][7];
+    op_row(o, op, P % o.d, P / o.d, row);
+    s += row[3][3];
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[op * NB + b] = red[0];
+}
+
+// partial maxima of the absolute row sums of Op - (trace / n) I
+__global__ void var_norm_kernel(VarOpsDev o, const double* tr_part, double* part) {
+  const int op = blockIdx.x, b = blockIdx.y, NB = gridDim.y;
+  const int n = o.d * o.d;
+  double tr = 0.0;
+  for (int q = 0; q < NB; ++q) tr += tr_part[op * NB + q];
+  const double shift = tr / n;
+  double mx = 0.0;
+  for (int P = b * blockDim.x + threadIdx.x; P < n; P += NB * blockDim.x) {
+    double row[7][7];
+    op_row(o, op, P % o.d, P / o.d, row);
+    row[3][3] -= shift;
+    double s = 0.0;
+    for (int y = 0; y < 7; ++y)
+      for (int x = 0; x < 7; ++x) s += fabs(row[y][x]);
+    mx = fmax(mx, s);
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + k]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[op * NB + b] = red[0];
+}
+
+// tab[0..5] traces, tab[6..11] shifted norms
+__global__ void var_final_kernel(const double* tr_part, const double* nu_part, int NB, double* tab) {
+  const int op = threadIdx.x;
+  if (op >= kVarOps) return;
+  double tr = 0.0, nu = 0.0;
+  for (int q = 0; q < NB; ++q) {
+    tr += tr_part[op * NB + q];
+    nu = fmax(nu, nu_part[op * NB + q]);
+  }
+  tab[op] = tr;
+  tab[kVarOps + op] = nu;
+}
+
+__global__ void psi_rational_kernel(int d, double ax, double dx, double c, double* psi) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d) return;
+  const double x = ax + (double)(i + 1) * dx;
+  psi[i] = 1.0 + c / (1.0 + x * x);
+}
+
+// ------------------------------------------------------------------ launch planning
+struct VarPlan {
+  int C = 0, RS = 0, tpr = 0, R = 0, NT = 0, clusters = 0;
+  size_t smem = 0;
+};
+
+std::mutex g_plan_mu;
+std::map<std::tuple<int, int, int, bool>, VarPlan> g_plans;
+
+template <typename T, bool EULER>
+msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
+  const int d = ctx->d;
+  const auto key = std::make_tuple(ctx->device, d, (int)sizeof(T), EULER);
+  {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) {
+      *out = it->second;
+      return MSK_OK;
+    }
+  }
+  auto kern = var_engine_kernel<T, EULER>;
+  msk_status st = msk_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)kVarSmemCap), "smem attribute");
+  if (st != MSK_OK) return st;
+  st = msk_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
+                "cluster attribute");
+  if (st != MSK_OK) return st;
+  const int tpr = 32 * ((d + 31) / 32);
+  if (tpr > kVarMaxThreads) return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "grid too wide for the variable-coefficient engine");
+  std::vector<VarPlan> cands;
+  int best_used = 0;
+  for (int C = 1; C <= 16; ++C) {
+    const int RS = (d + C - 1) / C;
+    if ((C - 1) * RS >= d || RS < 2) continue;
+    const int ng = std::max(1, std::min(kVarMaxThreads / tpr, RS / 2));   // at least two rows per strip
+    const int R = (RS + ng - 1) / ng;
+    const int NT = tpr * ng;
+    const size_t smem = (size_t)var_layout(RS, d, NT).total * sizeof(T);
+    if (smem > kVarSmemCap) continue;
+    int clusters = 0;
+    if (C == 1) {
+      int per_sm = 0;
+      st = msk_cuda(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem), "occupancy");
+      if (st != MSK_OK) return st;
+      clusters = per_sm * ctx->num_sms;
+    } else {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cfg.gridDim = dim3(C, 1, 1);
+      cfg.blockDim = dim3(NT, 1, 1);
+      cfg.dynamicSmemBytes = smem;
+      int nc = 0;
+      if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        nc = 0;
+      }
+      clusters = nc;
+    }
+    if (clusters < 1) continue;
+    VarPlan p;
+    p.C = C;
+    p.RS = RS;
+    p.tpr = tpr;
+    p.R = R;
+    p.NT = NT;
+    p.clusters = clusters;
+    p.smem = smem;
+    cands.push_back(p);
+    best_used = std::max(best_used, clusters * C);
+  }
+  // the smallest cluster that keeps at least 97 % of the best SM count busy
+  for (const VarPlan& p : cands) {
+    if (p.clusters * p.C * 100 >= best_used * 97) {
+      std::lock_guard<std::mutex> lock(g_plan_mu);
+      g_plans[key] = p;
+      *out = p;
+      return MSK_OK;
+    }
+  }
+  return msk_fail(ctx, MSK_ERR_UNSUPPORTED,
+                  "grid size / precision does not fit the variable-coefficient engine (cluster of <= 16 CTAs)");
+}
+
+template <typename T, bool EULER>
+msk_status launch_var_typed(msk_ctx* ctx, VarArgs a, int64_t paths, cudaStream_t stream) {
+  VarPlan pl;
+  msk_status st = plan_var<T, EULER>(ctx, &pl);
+  if (st != MSK_OK) return st;
+  a.C = pl.C;
+  a.RS = pl.RS;
+  a.tpr = pl.tpr;
+  a.R = pl.R;
+  const int64_t clusters = std::min<int64_t>(pl.clusters, paths);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(pl.NT, 1, 1);
+  cfg.dynamicSmemBytes = pl.smem;
+  cfg.stream = stream;
+  cfg.gridDim = dim3((unsigned)(clusters * pl.C), 1, 1);
+  if (pl.C > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = pl.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return msk_cuda(ctx, cudaLaunchKernelEx(&cfg, var_engine_kernel<T, EULER>, a), "variable-coefficient engine");
+}
+
+}  // namespace
+
+msk_status launch_psi_rational(msk_ctx* ctx, double c, cudaStream_t stream) {
+  psi_rational_kernel<<<(ctx->d + 127) / 128, 128, 0, stream>>>(ctx->d, ctx->ax, ctx->dx, c, ctx->psi);
+  return msk_cuda(ctx, cudaGetLastError(), "psi kernel");
+}
+
+msk_status ensure_var_tables(msk_ctx* ctx, cudaStream_t stream) {
+  if (!ctx->xprof || !ctx->var_dirty) return MSK_OK;
+  constexpr int NB = kVarNormBlocks;
+  if (!ctx->var_tab) {
+    msk_status st = msk_cuda(ctx, cudaMalloc(&ctx->var_tab, (2 * kVarOps + 2 * kVarOps * NB) * sizeof(double)),
+                             "operator table allocation");
+    if (st != MSK_OK) return st;
+  }
+  VarOpsDev o;
+  o.d = ctx->d;
+  o.kx = (double)ctx->coef.drift_sign * (0.5 / ctx->dx);
+  o.av = ctx->av;
+  o.dv = ctx->dv;
+  o.alpha = 0.5 * ctx->coef.a0;
+  o.psi = ctx->psi;
+  double* tr_part = ctx->var_tab + 2 * kVarOps;
+  double* nu_part = tr_part + kVarOps * NB;
+  var_trace_kernel<<<dim3(kVarOps, NB), 256, 0, stream>>>(o, tr_part);
+  var_norm_kernel<<<dim3(kVarOps, NB), 256, 0, stream>>>(o, tr_part, nu_part);
+  var_final_kernel<<<1, 32, 0, stream>>>(tr_part, nu_part, NB, ctx->var_tab);
+  msk_status st = msk_cuda(ctx, cudaGetLastError(), "operator norm kernels");
+  if (st == MSK_OK) ctx->var_dirty = false;
+  return st;
+}
+
+msk_status launch_engine_var(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
+                             const double* Wt, const double* dW, void* out, uint32_t* status,
+                             cudaStream_t stream) {
+  if (paths == 0) return MSK_OK;
+  if (!euler && ctx->coef.kind != MSK_COEF_CONST)
+    return msk_fail(ctx, MSK_ERR_UNSUPPORTED,
+                    "Magnus with an x profile needs constant coefficients (time-dependent ones are built for "
+                    "the constant-coefficient operators only)");
+  VarArgs a{};
+  a.u0 = ctx->u0;
+  a.Wt = Wt;
+  a.dW = dW;
+  a.psi = ctx->psi;
+  a.out = out;
+  a.status = status;
+  a.work = ctx->work;
+  a.paths = paths;
+  a.steps = steps;
+  a.d = ctx->d;
+  a.dx = ctx->dx;
+  a.dv = ctx->dv;
+  a.av = ctx->av;
+  a.kappa = (double)ctx->coef.drift_sign;
+  a.T = ctx->T;
+  a.s_cap = kMskScaleCap;
+  a.tol32 = 0x1p-20f;   // float Taylor tolerance (see gen_theta.py)
+  a.tol64 = 0x1p-53;
+  a.c = coef_dev(ctx->coef);
+  if (precision == MSK_F32)
+    return euler ? launch_var_typed<float, true>(ctx, a, paths, stream)
+                 : launch_var_typed<float, false>(ctx, a, paths, stream);
+  return euler ? launch_var_typed<double, true>(ctx, a, paths, stream)
+               : launch_var_typed<double, false>(ctx, a, paths, stream);
+}
+
+extern "C" msk_status msk_set_x_profile(msk_ctx* ctx, int kind, double c, const double* psi_host) {
+  if (!ctx) return MSK_ERR_ARG;
+  if (kind != MSK_XPROF_NONE && kind != MSK_XPROF_RATIONAL && kind != MSK_XPROF_VALUES)
+    return msk_fail(ctx, MSK_ERR_ARG, "unknown x profile kind");
+  if (kind == MSK_XPROF_RATIONAL) {
+    if (!isfinite(c)) return msk_fail(ctx, MSK_ERR_NONFINITE, "non-finite profile constant");
+    if (!(c >= 0)) return msk_fail(ctx, MSK_ERR_ARG, "profile constant must be >= 0");
+  }
+  if (kind == MSK_XPROF_VALUES) {
+    if (!psi_host) return msk_fail(ctx, MSK_ERR_ARG, "null profile values");
+    for (int i = 0; i < ctx->d; ++i) {
+      if (!isfinite(psi_host[i])) return msk_fail(ctx, MSK_ERR_NONFINITE, "non-finite profile value");
+      if (!(psi_host[i] > 0)) return msk_fail(ctx, MSK_ERR_ARG, "profile values must be positive");
+    }
+  }
+  msk_status st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
+  if (st != MSK_OK) return st;
+  if (kind == MSK_XPROF_NONE) {
+    ctx->xprof = 0;
+    ctx->var_dirty = true;
+    return MSK_OK;
+  }
+  if (!ctx->psi) {
+    st = msk_cuda(ctx, cudaMalloc(&ctx->psi, (size_t)ctx->d * sizeof(double)), "profile allocation");
+    if (st != MSK_OK) return st;
+  }
+  if (kind == MSK_XPROF_RATIONAL) st = launch_psi_rational(ctx, c, 0);
+  else st = msk_cuda(ctx, cudaMemcpy(ctx->psi, psi_host, (size_t)ctx->d * sizeof(double), cudaMemcpyHostToDevice),
+                     "copy profile");
+  if (st == MSK_OK) st = msk_cuda(ctx, cudaStreamSynchronize(0), "profile sync");
+  if (st != MSK_OK) return st;
+  ctx->xprof = kind;
+  ctx->var_dirty = true;
+  return MSK_OK;
+}

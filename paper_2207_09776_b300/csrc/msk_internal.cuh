@@ -36,6 +36,11 @@ struct msk_ctx {
   void* scratch = nullptr;    // library-owned scratch (functionals + weights)
   size_t scratch_bytes = 0;
   int num_sms = 0;
+  // x profile of the variable coefficients (msk_set_x_profile)
+  int xprof = 0;              // MSK_XPROF_*; 0: constant-coefficient operators
+  double* psi = nullptr;      // [d] psi(x_i), device
+  double* var_tab = nullptr;  // 6 traces, 6 shifted norms of the variable-coefficient operators; partials
+  bool var_dirty = true;      // var_tab must be rebuilt (profile, a0 or drift changed)
   std::string err;
 };
 
@@ -76,6 +81,13 @@ msk_status launch_omega(msk_ctx* ctx, int order, int steps, int64_t paths, int p
 msk_status launch_engine(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
                          const double* Wt, const double* dW, void* out, uint32_t* status,
                          cudaStream_t stream);
+// Variable-coefficient path (engine_var.cu): the engine, and the traces and
+// norms of its six operators for the (s, m) selection (rebuilt when dirty).
+msk_status launch_engine_var(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
+                             const double* Wt, const double* dW, void* out, uint32_t* status,
+                             cudaStream_t stream);
+msk_status ensure_var_tables(msk_ctx* ctx, cudaStream_t stream);
+msk_status launch_psi_rational(msk_ctx* ctx, double c, cudaStream_t stream);
 
 // Device-side coefficient profiles.
 struct CoefDev {

@@ -31,6 +31,7 @@ __constant__ double c_theta32[MSK_THETA_MMAX_F32];
 struct OmegaArgs {
   const double* band;
   const double* trace;
+  const double* var;   // x profile: traces [0, 6) and shifted norms [6, 12) of the six operators; else null
   int D, order, steps, precision;
   int64_t paths;
   double T, dx;
@@ -126,18 +127,32 @@ __global__ void omega_kernel(OmegaArgs a, const double* __restrict__ F, double* 
   const int n = (int)(idx % a.steps);
   double w[MSK_NOPS];
   magnus_weights(a, n, F + idx * MSK_NF, w);
-  double tr = 0.0;
-  for (int k = 0; k < MSK_NOPS; ++k) tr += w[k] * a.trace[k];
-  const double mu = tr / ((double)a.D * a.D);
-  // infinity-norm bound of Omega - mu I over the row classes: the four boundary
-  // rows and the two extreme interior rows (only V1's centre varies inside, linearly)
   const int D = a.D;
-  const int rows[6] = {0, 1, 2, D - 3, D - 2, D - 1};
-  double nrm = 0.0;
-  for (int r = 0; r < 6; ++r) {
-    double c[MSK_NCOEF];
-    fold_row(a.band, D, rows[r], w, -mu, 0.5 / a.dx, 0.25 / (a.dx * a.dx), c);
-    nrm = fmax(nrm, row_abs_sum(c));
+  double mu, nrm = 0.0;
+  if (a.var) {
+    // x profile (constant coefficients): Omega over the six operators B, A0, A0^2,
+    // [B,A0], [[B,A0],A0], [[B,A0],B] with B = Bx + alpha Bvv; the bound is the sum
+    // of |weight| x the exact norm of each operator minus its own trace shift
+    const double w6[6] = {w[MSK_OP_BX],    w[MSK_OP_A0],      w[MSK_OP_A0A0],
+                          w[MSK_OP_BX_A0], w[MSK_OP_BXA0_A0], w[MSK_OP_BXA0_BX]};
+    double tr = 0.0;
+    for (int k = 0; k < 6; ++k) {
+      tr += w6[k] * a.var[k];
+      nrm += fabs(w6[k]) * a.var[6 + k];
+    }
+    mu = tr / ((double)D * D);
+  } else {
+    double tr = 0.0;
+    for (int k = 0; k < MSK_NOPS; ++k) tr += w[k] * a.trace[k];
+    mu = tr / ((double)D * D);
+    // infinity-norm bound of Omega - mu I over the row classes: the four boundary
+    // rows and the two extreme interior rows (only V1's centre varies inside, linearly)
+    const int rows[6] = {0, 1, 2, D - 3, D - 2, D - 1};
+    for (int r = 0; r < 6; ++r) {
+      double c[MSK_NCOEF];
+      fold_row(a.band, D, rows[r], w, -mu, 0.5 / a.dx, 0.25 / (a.dx * a.dx), c);
+      nrm = fmax(nrm, row_abs_sum(c));
+    }
   }
   const double* th = a.precision == MSK_F32 ? c_theta32 : c_theta64;
   const int mmax = a.precision == MSK_F32 ? MSK_THETA_MMAX_F32 : MSK_THETA_MMAX_F64;
@@ -190,8 +205,12 @@ msk_status launch_omega(msk_ctx* ctx, int order, int steps, int64_t paths, int p
   if (st0 != MSK_OK) return st0;
   const int64_t n = paths * steps;
   if (n == 0) return MSK_OK;
-  OmegaArgs a{ctx->band, ctx->aux, ctx->d, order, steps, precision, paths, ctx->T, ctx->dx,
-              coef_dev(ctx->coef), kMskScaleCap};
+  if (ctx->xprof) {
+    st0 = ensure_var_tables(ctx, stream);
+    if (st0 != MSK_OK) return st0;
+  }
+  OmegaArgs a{ctx->band, ctx->aux, ctx->xprof ? ctx->var_tab : nullptr, ctx->d, order, steps, precision, paths,
+              ctx->T, ctx->dx, coef_dev(ctx->coef), kMskScaleCap};
   omega_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(a, F, Wt);
   return msk_cuda(ctx, cudaGetLastError(), "omega kernel");
 }

@@ -47,8 +47,8 @@ def test_binding_covers_every_declared_symbol():
 
 def test_argument_validation_needs_no_device(lib):
     h = ctypes.c_void_p()
-    bad = [msk.msk_grid(33, 33, -1, 1, -1, 1), msk.msk_grid(32, 64, -1, 1, -1, 1),
-           msk.msk_grid(32, 32, 1, -1, -1, 1)]
+    bad = [msk.msk_grid(7, 7, -1, 1, -1, 1), msk.msk_grid(513, 513, -1, 1, -1, 1),
+           msk.msk_grid(32, 64, -1, 1, -1, 1), msk.msk_grid(32, 32, 1, -1, -1, 1)]
     for g in bad:
         assert lib.msk_create(ctypes.byref(h), ctypes.byref(g), 0) == msk.MSK_ERR_ARG
         assert h.value is None
@@ -57,6 +57,7 @@ def test_argument_validation_needs_no_device(lib):
     assert lib.msk_create(None, ctypes.byref(g), 0) == msk.MSK_ERR_ARG
     # calls on a NULL context fail with MSK_ERR_ARG, destroy(NULL) is a no-op
     assert lib.msk_solve_magnus(None, 2, 1, 1, 0, None, None, None) == msk.MSK_ERR_ARG
+    assert lib.msk_set_x_profile(None, msk.MSK_XPROF_RATIONAL, 1.0, None) == msk.MSK_ERR_ARG
     assert lib.msk_solve_euler(None, 1, 1, 0, None, None, None) == msk.MSK_ERR_ARG
     assert lib.msk_set_seed(None, 1, 0, 100, 1.0) == msk.MSK_ERR_ARG
     assert lib.msk_philox_words(1, 1, 0, -1, 1, None, None) == msk.MSK_ERR_ARG
