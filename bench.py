@@ -55,7 +55,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-comparators", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=0, help="paths in the CPU-oracle sample (0 = auto)")
-    p.add_argument("--workload", default="trig128", choices=("trig128", "batch", "surrogate", "large512"),
+    p.add_argument("--workload", default="trig128", choices=("trig128", "batch", "surrogate", "large512",
+                                                              "paper_var"),
                    help="trig128: the time-dependent 128^2 workload (default); batch: grids 64/128/256 "
                         "in ratio 4:2:1 of 16384 paths in one persistent launch; surrogate: the learned "
                         "surrogate of the 128^2 workload served 65536 paths per step with a 1%% Magnus audit; "
@@ -65,7 +66,7 @@ def parse():
                    help="serve PATHS paths twice with an untrained surrogate of the 128^2 workload (random "
                         "weights, random orthonormal POD basis; features, network, decode; no audit) -- a "
                         "small case for ncu captures of the surrogate kernels -- and exit")
-    p.add_argument("--profile-grid", type=int, default=128, choices=(128, 512),
+    p.add_argument("--profile-grid", type=int, default=128, choices=(128, 512, 100, 200, 300),
                    help="grid of --profile-case: 128 (the bench workload, m3, K = 8) or 512 "
                         "(sigma = 0.5, m2, K = 64)")
     p.add_argument("--profile-case", type=int, default=0, metavar="PATHS",
@@ -986,6 +987,184 @@ def run_large512(a):
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ variable coefficients (Table errorsVar)
+
+VAR_STEPS = {100: 20, 200: 40, 300: 100}       # the paper's Magnus step sizes 0.05, 0.025, 0.01
+VAR_PATHS = {100: 4096, 200: 1024, 300: 512}   # paths per timed solve (outputs > 126 MB L2)
+VAR_REF_PATHS = 16
+VAR_EM_REF = 100_000                           # Euler-Maruyama with step 1e-5 (the paper's reference)
+VAR_EM_CMP = 10_000                            # Euler-Maruyama with step 1e-4 (the paper's comparator)
+# floating-point operations per grid point and Taylor term of the variable-coefficient
+# engine: pass A (a, b at the point and its four neighbours, A0 a, A0 b, B a, B b, p, q)
+# 71, pass B (B p + A0 q - mu t, scaled, accumulated) 14; a fused multiply-add counts 2
+VAR_FLOPS_PER_POINT = 85
+PAPER_VAR_TABLE = {   # Table errorsVar: seconds per simulation on the paper's V100 (MATLAB)
+    100: {"M2": 0.13, "M3": 0.24, "EM_1e-4": 4.24, "EM_1e-5": 42.24},
+    200: {"M2": 1.66, "M3": 1.83, "EM_1e-4": 21.02, "EM_1e-5": 209.02},
+    300: {"M2": 4.28, "M3": 5.0, "EM_1e-4": 58.41, "EM_1e-5": 582.88}}
+
+
+def _oracle_var_paths(args):
+    w, order, K, paths = args
+    from oracle import magnus
+    from oracle.discretization import LangevinOperators
+    ops = LangevinOperators(w)
+    for p in paths:
+        magnus.solve_path(w, order, K, p, ops)
+    return len(paths)
+
+
+def run_paper_var(a):
+    """The paper's variable-coefficient experiment (Section 3.2, Table errorsVar): d = 100,
+    200, 300 on [-4, 4]^2, g^vv = 1.1 (1 + 1/(x^2+1)), sigma^v = 10^-1/2 sqrt(1 + 1/(x^2+1)),
+    -v d_x drift, phi = exp(-(x^2+v^2)/2), T = 1, 10^5 fine Brownian cells.  Per grid: the
+    double Euler-Maruyama solution with step 1e-5 on 16 paths is the reference; Magnus orders 2
+    and 3 at the paper's steps (float and double) and Euler-Maruyama with step 1e-4 report Err
+    against it; the timed step is one float order-3 solve of each grid's batch."""
+    import torch
+
+    import paper_2207_09776_b300 as msk
+    from paper_2207_09776_b300 import build as mbuild
+    from workloads import PAPER_VAR
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    mbuild.build()
+    msk.load_library()
+    stream = torch.cuda.current_stream()
+    peaks, peak_src = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    reps = max(1, a.steps // 3)
+    clocks = ClockSampler(local)
+    per_grid, total_ms, total_paths, total_flops, launches = {}, 0.0, 0, 0.0, 0
+    e2e_ms, d2h = 0.0, 0
+    started = False
+    for w0 in PAPER_VAR:
+        d, K = w0.d, VAR_STEPS[w0.d]
+        P = VAR_PATHS[d]
+        w = w0.with_(paths=P, path_offset=rank * P)
+        s = msk.Solver(w, device=local)
+        R = VAR_REF_PATHS
+        # ---- accuracy (untimed): errors on R paths against Euler-Maruyama with step 1e-5
+        t0 = time.perf_counter()
+        ref = s.euler(VAR_EM_REF, paths=R, precision=msk.MSK_F64)
+        torch.cuda.synchronize()
+        ref_s = time.perf_counter() - t0
+        acc = {}
+
+        def err(u, prec):
+            e, m = s.error(u, prec, ref=ref, ref_precision=msk.MSK_F64)
+            e1, _ = s.error(u, prec, ref=ref, ref_precision=msk.MSK_F64, kappa=1)
+            return {"err": float(m.cpu()[0]), "err_kappa1": float(e1.mean().cpu())}
+        for order in (2, 3):
+            for prec, nm in ((msk.MSK_F32, "f32"), (msk.MSK_F64, "f64")):
+                u, st = s.magnus(order, K, paths=R, precision=prec, status=True)
+                acc[f"M{order}_{nm}"] = dict(err(u, prec), flagged_paths=int((st != 0).sum()))
+        for n_em, nm in ((VAR_EM_CMP, "EM_1e-4_f64"), (VAR_EM_CMP // 10, "EM_1e-3_f64")):
+            u = s.euler(n_em, paths=R, precision=msk.MSK_F64)
+            e = err(u, msk.MSK_F64)
+            acc[nm] = {k: (v if math.isfinite(v) else None) for k, v in e.items()}
+        # ---- timed: float order-3 solves of P paths (L2 flushed between solves)
+        out = s.state(P, msk.MSK_F32)
+        st = torch.zeros(P, dtype=torch.int32, device="cuda")
+        for _ in range(max(a.warmup, 1)):
+            msk.msk_solve_magnus(s.ctx, ORDER, K, P, msk.MSK_F32, out, st, stream)
+        torch.cuda.synchronize()
+        msk.msk_work_counter(s.ctx, reset=True, stream=stream)
+        if not started:
+            clocks.start()
+            started = True
+        ms = 0.0
+        for _ in range(reps):
+            flush.fill_(1)
+            e0, e1 = _events(torch, stream)
+            e0.record(stream)
+            msk.msk_solve_magnus(s.ctx, ORDER, K, P, msk.MSK_F32, out, st, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        ms /= reps
+        mv = msk.msk_work_counter(s.ctx, reset=True, stream=stream) / reps
+        # order 2 and the Euler comparators on the same batch (one solve each)
+        extra = {}
+        for nm, fn in (("M2_f32", lambda: msk.msk_solve_magnus(s.ctx, 2, K, P, msk.MSK_F32, out, st, stream)),
+                       ("EM_1e-4_f32", lambda: msk.msk_solve_euler(s.ctx, VAR_EM_CMP, P, msk.MSK_F32, out, st,
+                                                                   stream))):
+            flush.fill_(1)
+            e0, e1 = _events(torch, stream)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            extra[nm] = {"paths_per_s": P / (e0.elapsed_time(e1) / 1e3)}
+        # end to end: the same float solve with the solution read back to pinned host memory
+        host = torch.empty(P * d * d, dtype=torch.float32, pin_memory=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        msk.msk_solve_magnus(s.ctx, ORDER, K, P, msk.MSK_F32, out, st, stream)
+        host.copy_(out.view(-1), non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
+        d2h += host.numel() * 4
+        flops = mv * d * d * VAR_FLOPS_PER_POINT
+        per_grid[f"d{d}"] = {
+            "paths": P, "K": K, "h": w.T / K, "paths_per_s": P / (ms / 1e3), "ms": ms,
+            "s_per_path": ms / 1e3 / P, "matvecs_per_path": mv / P,
+            "tflops": flops / (ms / 1e3) / 1e12, "flagged_paths": int((st != 0).sum()),
+            "errors_vs_EM_1e-5_on_16_paths": acc, "reference_solve_s": ref_s, "comparators": extra,
+            "paper_V100_s_per_simulation": PAPER_VAR_TABLE[d]}
+        total_ms += ms
+        total_paths += P
+        total_flops += flops
+        launches += 3 * reps
+        s.close()
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    achieved = total_flops / (total_ms / 1e3) / 1e12
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cores = host_cores()
+        w = PAPER_VAR[0].with_(paths=cores)
+        chunks = [[c] for c in range(cores)]
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores) as pool:
+            pool.map(_oracle_var_paths, [(w.with_(n_fine=200), ORDER, 2, [0])] * cores)   # imports
+            t0 = time.perf_counter()
+            done = sum(pool.map(_oracle_var_paths, [(w, ORDER, VAR_STEPS[100], c) for c in chunks]))
+            secs = time.perf_counter() - t0
+        cpu = {"value": done / secs, "unit": "paths/s", "cores": cores, "kind": "oracle",
+               "sample": f"{done} paths of the d = 100 grid (FP64 oracle, order 3, K = 20), {secs:.1f} s"}
+    line = {"metric": METRIC, "value": world * total_paths / (total_ms / 1e3), "unit": "paths/s", "n_gpus": world,
+            "steps": reps, "warmup": max(a.warmup, 1), "ms_per_step": total_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "paper_langevin_var_d100_d200_d300", "grids": [100, 200, 300],
+                       "paths_per_gpu": total_paths, "order": ORDER, "n_fine": PAPER_VAR[0].n_fine,
+                       "step": "one float order-3 solve of each grid's batch at the paper's step size",
+                       "reference": "double Euler-Maruyama, step 1e-5, 16 paths per grid",
+                       "l2": "L2 flushed (256 MB write) before every timed solve",
+                       "parallelism": f"replicas x{world} (path ranges)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "traffic": None,
+                         "kernel": "var_engine_kernel<float> (composed B and A0, clusters of 1/3/7 CTAs)",
+                         "flops_per_point_per_term": VAR_FLOPS_PER_POINT,
+                         "peak_note": f"FP32 FMA peak 148 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz ({peak_src} clock)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * total_paths / (e2e_ms / 1e3), "unit": "paths/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": d2h},
+            "per_grid": per_grid, "clocks": clk, "gpu_launches": launches}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_surrogate_profile_case(a):
     """Two serves of PATHS paths by a surrogate with random parameters (kernel timing only)."""
     import torch
@@ -1025,6 +1204,10 @@ def run_profile_case(a):
     if a.profile_grid == 512:
         from workloads import LARGE_512
         w, K, order = LARGE_512[1].with_(paths=P), 64, 2
+    elif a.profile_grid in VAR_STEPS:
+        from workloads import PAPER_VAR
+        w = PAPER_VAR[(100, 200, 300).index(a.profile_grid)].with_(paths=P)
+        K, order = VAR_STEPS[a.profile_grid], ORDER
     else:
         w, K, order = LANGEVIN_TRIG_128.with_(paths=P), K_CANDIDATES[0], ORDER
     s = msk.Solver(w)
@@ -1056,6 +1239,8 @@ def main():
         run_surrogate(a)
     elif a.workload == "large512":
         run_large512(a)
+    elif a.workload == "paper_var":
+        run_paper_var(a)
     else:
         run_ours(a)
 
