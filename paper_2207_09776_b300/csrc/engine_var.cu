@@ -30,7 +30,9 @@
 // Three fields t, p, q with two halo rows above and below and two zero columns
 // on each side, and the Taylor partial sum at the CTA's own points.  A thread
 // owns one grid column and a strip of consecutive rows and slides a window of
-// rows down the strip.  Halo rows facing another CTA are written by that CTA
+// rows down the strip (threads take the CTA's points in group-major order, so
+// no lane idles when d is not a multiple of 32 and a warp may span two row
+// groups).  Halo rows facing another CTA are written by that CTA
 // (shared::cluster stores) as it stores its own edge rows, so a pass reads only
 // local shared memory.  The next term overwrites t in place in pass B (each
 // thread reads only its own point of t there).  The Taylor parameters
@@ -69,7 +71,7 @@ struct VarArgs {
   uint32_t* status;
   unsigned long long* work;
   int64_t paths;
-  int steps, d, C, RS, tpr, R;
+  int steps, d, C, RS, ng, R;
   double dx, dv, av, kappa, T, s_cap;
   float tol32;
   double tol64;
@@ -153,8 +155,11 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
 
   const int r0 = rank * RS;          // first global v-row of this CTA
   const int rs = min(RS, d - r0);    // rows held by this CTA
-  const int col = tid % a.tpr, grp = tid / a.tpr;
-  const bool act = col < d;
+  // thread -> (row group, column): the CTA's points as the group-major sequence
+  // of (group, column) pairs, one per thread, so no lane idles when d is not a
+  // multiple of 32 (a warp may span two groups; nothing is exchanged by lanes)
+  const bool act = tid < a.ng * d;
+  const int col = act ? tid % d : 0, grp = act ? tid / d : 0;
   const int p0 = grp * a.R;
   const int nrows = act ? max(0, min(a.R, rs - p0)) : 0;
 
@@ -579,7 +584,7 @@ __global__ void psi_rational_kernel(int d, double ax, double dx, double c, doubl
 
 // ------------------------------------------------------------------ launch planning
 struct VarPlan {
-  int C = 0, RS = 0, tpr = 0, R = 0, NT = 0, clusters = 0;
+  int C = 0, RS = 0, ng = 0, R = 0, NT = 0, clusters = 0;
   size_t smem = 0;
 };
 
@@ -605,16 +610,16 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
   st = msk_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
                 "cluster attribute");
   if (st != MSK_OK) return st;
-  const int tpr = 32 * ((d + 31) / 32);
-  if (tpr > kVarMaxThreads) return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "grid too wide for the variable-coefficient engine");
+  if (d > kVarMaxThreads) return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "grid too wide for the variable-coefficient engine");
   std::vector<VarPlan> cands;
   int best_used = 0;
   for (int C = 1; C <= 16; ++C) {
     const int RS = (d + C - 1) / C;
     if ((C - 1) * RS >= d || RS < 2) continue;
-    const int ng = std::max(1, std::min(kVarMaxThreads / tpr, RS / 2));   // at least two rows per strip
+    // row groups: as many as 512 threads hold, at least two rows per strip
+    const int ng = std::max(1, std::min(kVarMaxThreads / d, RS / 2));
     const int R = (RS + ng - 1) / ng;
-    const int NT = tpr * ng;
+    const int NT = 32 * ((ng * d + 31) / 32);
     const size_t smem = (size_t)var_layout(RS, d, NT).total * sizeof(T);
     if (smem > kVarSmemCap) continue;
     int clusters = 0;
@@ -646,7 +651,7 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
     VarPlan p;
     p.C = C;
     p.RS = RS;
-    p.tpr = tpr;
+    p.ng = ng;
     p.R = R;
     p.NT = NT;
     p.clusters = clusters;
@@ -674,7 +679,7 @@ msk_status launch_var_typed(msk_ctx* ctx, VarArgs a, int64_t paths, cudaStream_t
   if (st != MSK_OK) return st;
   a.C = pl.C;
   a.RS = pl.RS;
-  a.tpr = pl.tpr;
+  a.ng = pl.ng;
   a.R = pl.R;
   const int64_t clusters = std::min<int64_t>(pl.clusters, paths);
   cudaLaunchConfig_t cfg = {};
