@@ -39,46 +39,55 @@ def _cells(w, K: int):
     return w.n_fine // K
 
 
-def step_functionals(w, path_local: int, K: int) -> dict:
-    """Per-step functionals of one path for an iterated scheme with K steps.
-
-    Returns arrays of length K:
+def interval_functionals(w, path_local: int, c0: int, c1: int, dw_all=None) -> dict:
+    """Functionals of the fine cells c0 .. c1-1, i.e. of [t0, t0 + h] with t0 = c0 delta and
+    h = (c1 - c0) delta, with the Brownian motion restarted at t0 (W~(s) = W(t0 + s) - W(t0)):
       dW  = W~(h)                       I1 = int_0^h W~ ds
       I2  = int_0^h W~^2 ds             I3 = int_0^h s W~ ds
       om  = omega~(h) = int_0^h sigma dW
       Jom = int_0^h omega~ ds
       G1  = int omega~ ds - int s sigma dW
       G2  = int alpha omega~ ds - int alpha_bar sigma dW
-    where sigma, alpha are evaluated at absolute time t_n + s.
-    """
+    where sigma, alpha are evaluated at absolute time t0 + s.  A Magnus step is one
+    such interval; an output time inside a step is another (Section 3, "Implementation":
+    the expansion of a sub-interval evaluated at any time inside it)."""
+    if not 0 <= c0 < c1 <= w.n_fine:
+        raise ValueError("need 0 <= c0 < c1 <= n_fine")
     coef = Coefficients.of(w)
-    L = _cells(w, K)
     delta = w.T / w.n_fine
-    h = w.T / K
-    dw_all = fine_increments(w, path_local).reshape(K, L)
-    out = {k: np.empty(K) for k in ("dW", "I1", "I2", "I3", "om", "Jom", "G1", "G2")}
+    if dw_all is None:
+        dw_all = fine_increments(w, path_local)
+    dw = dw_all[c0:c1]
+    L = c1 - c0
+    tn = c0 * delta
     s_nodes = delta * np.arange(L + 1)
     s_mid = delta * (np.arange(L) + 0.5)
-    for n in range(K):
-        tn = n * h
-        dw = dw_all[n]
-        wn = np.concatenate(([0.0], np.cumsum(dw)))            # W~ at the fine nodes
-        w0, w1 = wn[:-1], wn[1:]
-        out["dW"][n] = wn[-1]
-        out["I1"][n] = np.sum(delta * (w0 + w1) / 2.0)
-        out["I2"][n] = np.sum(delta * (w0 * w0 + w0 * w1 + w1 * w1) / 3.0)
-        out["I3"][n] = np.sum(delta * (s_nodes[:-1] * (2 * w0 + w1) + s_nodes[1:] * (w0 + 2 * w1)) / 6.0)
-        sig_mid = coef.sigma(tn + s_mid)
-        om = np.concatenate(([0.0], np.cumsum(sig_mid * dw)))   # omega~ at the nodes
-        alp = coef.alpha(tn + s_nodes)
-        abar_mid = coef.alpha_bar(tn, s_mid)
-        jom = np.sum(delta * (om[:-1] + om[1:]) / 2.0)
-        out["om"][n] = om[-1]
-        out["Jom"][n] = jom
-        out["G1"][n] = jom - np.sum(s_mid * sig_mid * dw)
-        out["G2"][n] = (np.sum(delta * (alp[:-1] * om[:-1] + alp[1:] * om[1:]) / 2.0)
-                        - np.sum(abar_mid * sig_mid * dw))
+    wn = np.concatenate(([0.0], np.cumsum(dw)))            # W~ at the fine nodes
+    w0, w1 = wn[:-1], wn[1:]
+    out = {"dW": wn[-1],
+           "I1": np.sum(delta * (w0 + w1) / 2.0),
+           "I2": np.sum(delta * (w0 * w0 + w0 * w1 + w1 * w1) / 3.0),
+           "I3": np.sum(delta * (s_nodes[:-1] * (2 * w0 + w1) + s_nodes[1:] * (w0 + 2 * w1)) / 6.0)}
+    sig_mid = coef.sigma(tn + s_mid)
+    om = np.concatenate(([0.0], np.cumsum(sig_mid * dw)))   # omega~ at the nodes
+    alp = coef.alpha(tn + s_nodes)
+    abar_mid = coef.alpha_bar(tn, s_mid)
+    jom = np.sum(delta * (om[:-1] + om[1:]) / 2.0)
+    out["om"] = om[-1]
+    out["Jom"] = jom
+    out["G1"] = jom - np.sum(s_mid * sig_mid * dw)
+    out["G2"] = (np.sum(delta * (alp[:-1] * om[:-1] + alp[1:] * om[1:]) / 2.0)
+                 - np.sum(abar_mid * sig_mid * dw))
     return out
+
+
+def step_functionals(w, path_local: int, K: int) -> dict:
+    """Per-step functionals of one path for an iterated scheme with K steps: the
+    interval functionals of the cells n L .. (n+1) L - 1, n = 0..K-1 (arrays of length K)."""
+    L = _cells(w, K)
+    dw_all = fine_increments(w, path_local)
+    per = [interval_functionals(w, path_local, n * L, (n + 1) * L, dw_all) for n in range(K)]
+    return {k: np.array([f[k] for f in per]) for k in ("dW", "I1", "I2", "I3", "om", "Jom", "G1", "G2")}
 
 
 def terminal_functionals(w, path_local: int) -> dict:

@@ -32,7 +32,7 @@ import scipy.sparse as sp
 from scipy.sparse.linalg import expm_multiply
 
 from workloads import COEF_CONST
-from .brownian import step_functionals
+from .brownian import fine_increments, interval_functionals, step_functionals
 from .coefficients import Coefficients
 from .discretization import LangevinOperators, gaussian_initial, vec
 
@@ -99,6 +99,45 @@ def solve_path(w, order: int, K: int, path_local: int, ops=None, u0=None):
     return U.reshape(w.d, w.d)          # vec index j*nx + i -> [v][x]
 
 
+def solve_times(w, order: int, K: int, path_local: int, cells, ops=None):
+    """Solutions at several output times (Section 3, "Implementation": within each
+    sub-interval the Magnus expansion is evaluated at every requested time).  Output
+    time t = T c / n_fine (c in `cells`, 1 <= c <= n_fine) lies in the sub-interval
+    n = (c - 1) // L of the K-step scheme (L = n_fine / K cells); the solution there is
+    exp(Y(t_n, t)) U(t_n), Y over the cells n L .. c - 1 and U(t_n) the iterated solution
+    after n full steps.  Returns shape (len(cells), n_v, n_x)."""
+    if order not in (1, 2, 3):
+        raise ValueError("order must be 1, 2 or 3")
+    ops = ops or LangevinOperators(w)
+    coef = Coefficients.of(w)
+    L = w.n_fine // K
+    if L * K != w.n_fine:
+        raise ValueError("n_fine must be a multiple of K")
+    delta = w.T / w.n_fine
+    dw_all = fine_increments(w, path_local)
+    U = vec(gaussian_initial(w, ops.xs, ops.vs))
+    if w.kind == COEF_CONST:
+        B, A = ops.B(coef.a0), ops.A(coef.s0)
+
+    def log_of(c0, c1):
+        f = interval_functionals(w, path_local, c0, c1, dw_all)
+        h = (c1 - c0) * delta
+        if w.kind == COEF_CONST:
+            return omega_const(B, A, h, f["dW"], f["I1"], f["I2"], f["I3"], order)
+        return omega_timedep(ops, coef, c0 * delta, h, f, order)
+
+    out, n_done = [], 0
+    for c in cells:
+        if not 1 <= c <= w.n_fine:
+            raise ValueError("output cells must lie in 1 .. n_fine")
+        n = (c - 1) // L
+        while n_done < n:                                   # advance U to t_n
+            U = expm_action(log_of(n_done * L, (n_done + 1) * L), U)
+            n_done += 1
+        out.append(expm_action(log_of(n * L, c), U).reshape(w.d, w.d))
+    return np.stack(out)
+
+
 def solve(w, order: int, K: int, paths=None):
     """U_T for a list of local path indices (default: all w.paths); shape (P, n_v, n_x)."""
     ops = LangevinOperators(w)
@@ -118,5 +157,5 @@ def omega_matrix(w, order: int, K: int, path_local: int, step: int):
     return omega_timedep(ops, coef, step * h, h, f, order)
 
 
-__all__ = ["comm", "omega_const", "omega_timedep", "expm_action", "solve_path", "solve",
+__all__ = ["comm", "omega_const", "omega_timedep", "expm_action", "solve_path", "solve", "solve_times",
            "omega_matrix", "sp"]
