@@ -222,6 +222,25 @@ msk_status msk_magnus_from_weights(msk_ctx* ctx, int steps, int64_t paths, int p
                                    const double* Wt_dev, void* u_out_dev,
                                    uint32_t* path_status_dev, void* stream);
 
+/* Solutions at several output times inside the Magnus sub-intervals (Section 3,
+ * "Implementation": the expansion of a sub-interval is evaluated at every requested
+ * time, all times and trajectories in parallel).  times_cells (host, n_times
+ * entries, strictly increasing, each in 1 .. n_fine) are output times in fine cells,
+ * t_q = T times_cells[q] / n_fine.  With `steps` sub-intervals of L = n_fine/steps
+ * cells, t_q lies in sub-interval n = (times_cells[q] - 1) / L and
+ *   u(t_q) = exp(Y(t_n, t_q)) u(t_n),
+ * Y(t_n, t_q) the order-`order` logarithm of Eq. MagnusFormulas over [t_n, t_q] (its
+ * functionals from the same Brownian path) and u(t_n) the iterated solution after n
+ * steps; an output at a sub-interval end equals the iterated solution there.
+ * u_out_dev: [paths][n_times][v][x] of double (MSK_F64) or float (MSK_F32),
+ * caller-owned; path_status_dev (nullable): uint32[paths * n_times], the MSK_PATH_*
+ * bits of the partial step OR those of the path's whole iterated solve.  Scratch is
+ * library-owned (as msk_solve_magnus, plus 14 doubles per (path, output)).  Also with
+ * an x profile (msk_set_x_profile).  Bad times -> MSK_ERR_ARG before device work. */
+msk_status msk_solve_magnus_times(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
+                                  const int64_t* times_cells, int n_times, void* u_out_dev,
+                                  uint32_t* path_status_dev, void* stream);
+
 /* msk_solve_magnus for callers that cannot allocate device memory.  The paper
  * has no counterpart: this is a property of the library, not of the method.
  * Callers whose device memory belongs to another allocator (a framework's

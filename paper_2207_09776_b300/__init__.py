@@ -85,6 +85,7 @@ SIGNATURES = {
     "msk_solve_euler": (_INT, [_P, _INT, _I64, _INT, _P, _P, _P]),
     "msk_magnus_from_weights": (_INT, [_P, _INT, _I64, _INT, _P, _P, _P, _P]),
     "msk_solve_magnus_noalloc": (_INT, [_P, _INT, _INT, _I64, _INT, _P, _P, _P]),
+    "msk_solve_magnus_times": (_INT, [_P, _INT, _INT, _I64, _INT, ctypes.POINTER(_I64), _INT, _P, _P, _P]),
     "msk_work_counter": (_INT, [_P, ctypes.POINTER(ctypes.c_uint64), _INT, _P]),
     "msk_batch_create": (_INT, [ctypes.POINTER(_P), ctypes.POINTER(msk_batch_item), _INT, ctypes.c_char_p]),
     "msk_batch_run": (_INT, [_P, _P]),
@@ -271,6 +272,17 @@ def msk_solve_magnus_noalloc(ctx, order, steps, paths, precision, u_out, status=
     _need(u_out, 1, _dtype(precision), "u_out")
     _check(load_library().msk_solve_magnus_noalloc(ctx, order, steps, paths, precision, _ptr(u_out), _ptr(status),
                                                    _stream(stream)), ctx)
+
+
+def msk_solve_magnus_times(ctx, order, steps, paths, precision, times_cells, u_out, status=None, stream=None):
+    """times_cells: output times in fine cells (strictly increasing, 1 .. n_fine);
+    u_out: [paths][len(times_cells)][d][d] tensor; status: optional int32[paths * n_times]."""
+    import torch
+    cells = [int(c) for c in times_cells]
+    arr = (_I64 * max(len(cells), 1))(*cells)
+    _need(u_out, paths * len(cells), _dtype(precision), "u_out")
+    _check(load_library().msk_solve_magnus_times(ctx, order, steps, paths, precision, arr, len(cells), _ptr(u_out),
+                                                 _ptr(status), _stream(stream)), ctx)
 
 
 def msk_magnus_from_weights(ctx, steps, paths, precision, Wt, u_out, status=None, stream=None):
@@ -527,6 +539,17 @@ class Solver:
         u = self.state(paths, precision) if out is None else out
         st = torch.zeros(max(paths, 1), dtype=torch.int32, device=self.device) if status else None
         msk_solve_magnus(self.ctx, order, steps, paths, precision, u, st)
+        return (u, st) if status else u
+
+    def magnus_times(self, order, steps, times_cells, paths=None, precision=MSK_F64, status=False):
+        """Solutions at the output times (fine-cell units); shape (paths, n_times, d, d)."""
+        import torch
+        paths = self.w.paths if paths is None else paths
+        q = len(times_cells)
+        u = self._empty(max(paths, 1) * q * self.w.d * self.w.d, _dtype(precision))[: paths * q * self.w.d ** 2]
+        u = u.view(paths, q, self.w.d, self.w.d)
+        st = torch.zeros(max(paths * q, 1), dtype=torch.int32, device=self.device) if status else None
+        msk_solve_magnus_times(self.ctx, order, steps, paths, precision, times_cells, u, st)
         return (u, st) if status else u
 
     def euler(self, steps, paths=None, precision=MSK_F64, status=False):

@@ -14,7 +14,8 @@
 //     G1 = int omega~ ds - sum s_mid sigma(t_mid) dW_k
 //     G2 = delta/2 sum (alpha0 omega0 + alpha1 omega1) - sum alpha_bar(s_mid) sigma(t_mid) dW_k.
 //
-// Parallel layout: one warp per (path, step).  The step's fine cells are
+// Parallel layout: one warp per (path, step), or per (path, interval of fine
+// cells) for the solutions at output times inside a step.  The step's fine cells are
 // processed in rounds of 32 x 64 cells; in a round each lane draws the normals
 // of 64 consecutive cells (Philox4x32-10 + Box-Muller, double precision) into
 // shared memory and sums its chunk's dW and sigma dW; an exclusive warp scan
@@ -39,6 +40,9 @@ struct BrownArgs {
   double T;
   CoefDev c;
   const double* tab;   // TRIG: [3][n_fine + 1]: sigma(mid), alpha(node), A(mid); null for CONST
+  // Interval mode (steps = 1, paths = number of intervals): interval i covers the
+  // fine cells jobs[3i+1] .. jobs[3i+1] + jobs[3i+2] - 1 of local path jobs[3i].
+  const int64_t* jobs;
 };
 
 // antiderivative of alpha: A(t) = int_0^t alpha = (a0 t + a1 (1 - cos 2 pi t) / (2 pi)) / 2
@@ -77,13 +81,17 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t idx = (int64_t)blockIdx.x * kWarps + wib;   // (path, step) pair of this warp
   if (idx >= a.paths * a.steps) return;                     // whole warp leaves together
-  const int64_t p = idx / a.steps;
-  const int n = (int)(idx % a.steps);
-  const int64_t L = a.n_fine / a.steps;
+  int64_t p = idx / a.steps;
+  int64_t L = a.n_fine / a.steps;                           // cells of the step
+  int64_t f0 = (idx % a.steps) * L;                         // first fine cell of the step
+  if (a.jobs) {
+    p = a.jobs[3 * idx];
+    f0 = a.jobs[3 * idx + 1];
+    L = a.jobs[3 * idx + 2];
+  }
   const double delta = a.T / (double)a.n_fine;
   const double sq = sqrt(delta);
   const uint64_t gpath = a.path_offset + (uint64_t)p * a.path_stride;
-  const int64_t f0 = (int64_t)n * L;                        // first fine cell of the step
   const double* tsig = a.tab;
   const double* talp = a.tab + (a.n_fine + 1);
   const double* tA = a.tab + 2 * (a.n_fine + 1);
@@ -235,9 +243,25 @@ msk_status launch_brownian(msk_ctx* ctx, int steps, int64_t paths, double* out, 
     if (st != MSK_OK) return st;
   }
   BrownArgs a{ctx->seed, ctx->path_offset, 1, ctx->n_fine, paths, steps, ctx->T, coef_dev(ctx->coef),
-              trig ? ctx->tab : nullptr};
+              trig ? ctx->tab : nullptr, nullptr};
   dispatch_brownian(a, !increments_only, trig, nf32, out, stream);
   return msk_cuda(ctx, cudaGetLastError(), "brownian kernel");
+}
+
+// Functionals of arbitrary fine-cell intervals: jobs_dev[3 i .. 3 i + 2] = (local
+// path, first cell, number of cells) of interval i (device, njobs entries).
+msk_status launch_brownian_jobs(msk_ctx* ctx, const int64_t* jobs_dev, int64_t njobs, double* out,
+                                cudaStream_t stream, bool nf32) {
+  if (njobs == 0) return MSK_OK;
+  const bool trig = ctx->coef.kind == MSK_COEF_TRIG;
+  if (trig) {
+    msk_status st = ensure_cell_table(ctx, stream);
+    if (st != MSK_OK) return st;
+  }
+  BrownArgs a{ctx->seed, ctx->path_offset, 1, ctx->n_fine, njobs, 1, ctx->T, coef_dev(ctx->coef),
+              trig ? ctx->tab : nullptr, jobs_dev};
+  dispatch_brownian(a, true, trig, nf32, out, stream);
+  return msk_cuda(ctx, cudaGetLastError(), "brownian kernel (intervals)");
 }
 
 // Functionals of the global paths first, first + stride, ... (paths of them).
@@ -251,7 +275,7 @@ msk_status launch_brownian_strided(msk_ctx* ctx, int steps, int64_t paths, doubl
     if (st != MSK_OK) return st;
   }
   BrownArgs a{ctx->seed, first, stride, ctx->n_fine, paths, steps, ctx->T, coef_dev(ctx->coef),
-              trig ? ctx->tab : nullptr};
+              trig ? ctx->tab : nullptr, nullptr};
   dispatch_brownian(a, true, trig, nf32, out, stream);
   return msk_cuda(ctx, cudaGetLastError(), "brownian kernel");
 }
@@ -270,7 +294,7 @@ msk_status launch_brownian_with_table(msk_ctx* ctx, int steps, int64_t paths, do
   if (n == 0) return MSK_OK;
   const bool trig = ctx->coef.kind == MSK_COEF_TRIG;
   BrownArgs a{ctx->seed, ctx->path_offset, 1, ctx->n_fine, paths, steps, ctx->T, coef_dev(ctx->coef),
-              trig ? tab : nullptr};
+              trig ? tab : nullptr, nullptr};
   dispatch_brownian(a, true, trig, nf32, out, stream);
   return msk_cuda(ctx, cudaGetLastError(), "brownian kernel");
 }

@@ -97,9 +97,20 @@ msk_status dispatch(msk_ctx* ctx, int precision, const EngineArgs& a, cudaStream
 msk_status launch_engine(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
                          const double* Wt, const double* dW, void* out, uint32_t* status,
                          cudaStream_t stream) {
+  return launch_engine_ex(ctx, euler, steps, paths, precision, Wt, dW, out, status, stream, EngineSnap{});
+}
+
+msk_status launch_engine_ex(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
+                            const double* Wt, const double* dW, void* out, uint32_t* status,
+                            cudaStream_t stream, const EngineSnap& x) {
   if (paths == 0) return MSK_OK;
-  if (ctx->xprof) return launch_engine_var(ctx, euler, steps, paths, precision, Wt, dW, out, status, stream);
-  EngineArgs a;
+  if (ctx->xprof) return launch_engine_var(ctx, euler, steps, paths, precision, Wt, dW, out, status, stream, x);
+  EngineArgs a{};
+  a.snap = x.snap;
+  a.snap_first = x.snap_first;
+  a.snap_cnt = x.snap_cnt;
+  a.n_out = x.n_out;
+  a.u0_self = x.u0_self;
   a.band = ctx->band;
   a.u0 = ctx->u0;
   a.Wt = Wt;

@@ -54,7 +54,15 @@ struct EngineArgs {
   const double* u0;
   const double* Wt;   // Magnus: [paths][steps][MSK_NWT]
   const double* dW;   // Euler:  [paths][steps]
-  void* out;
+  void* out;          // [paths][d][d] of T; null: the final state is not stored
+  // Snapshots for output times inside the steps: at the start of step n the
+  // state is stored into snap[path][q] (T, d x d) for q = snap_first[n] ..
+  // snap_first[n] + snap_cnt[n] - 1; snap null: none.
+  void* snap;
+  const int* snap_first;
+  const int* snap_cnt;
+  int n_out;
+  int u0_self;        // 1: each path starts from its own out[path] (T) instead of u0
   uint32_t* status;
   unsigned long long* work;
   int64_t paths;
@@ -358,9 +366,15 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
     // ---- initial datum: own rows, plus the halo rows facing other CTAs ----------
     T m0 = T(0);
 #pragma unroll
+    // own points of the initial datum (u0, or the path's own output slot)
+    const T* self0 = a.u0_self ? reinterpret_cast<const T*>(a.out) + (size_t)path * D * D : nullptr;
+    auto load0 = [&](int jg) -> V4<T> {
+      if (self0) return ld4(self0 + (size_t)jg * D + i0);
+      const double* src = a.u0 + (size_t)jg * D + i0;
+      return V4<T>{(T)src[0], (T)src[1], (T)src[2], (T)src[3]};
+    };
     for (int r = 0; r < R; ++r) {
-      const double* src = a.u0 + (size_t)(r0 + j0 + r) * D + i0;
-      const V4<T> v = {(T)src[0], (T)src[1], (T)src[2], (T)src[3]};
+      const V4<T> v = load0(r0 + j0 + r);
       acc_put(r, v);
       st4(sm + at(j0 + r, i0), v);
       m0 = tmax(m0, tmax(tmax(absnan(v.x), absnan(v.y)), tmax(absnan(v.z), absnan(v.w))));
@@ -369,10 +383,7 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
       for (int h = 0; h < 2; ++h) {
         const int p = j0 == 0 ? h - 2 : RS + h;
         const int jg = r0 + p;
-        if (jg >= 0 && jg < D) {
-          const double* src = a.u0 + (size_t)jg * D + i0;
-          st4(sm + at(p, i0), V4<T>{(T)src[0], (T)src[1], (T)src[2], (T)src[3]});
-        }
+        if (jg >= 0 && jg < D) st4(sm + at(p, i0), load0(jg));
       }
     }
     publish(par, m0, m0);
@@ -384,6 +395,15 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
     unsigned long long nmv = 0;
 
     for (int n = 0; n < a.steps; ++n) {
+      // ---- snapshots of the state at the step start (output times inside the step)
+      if (a.snap) {
+        const int q0 = a.snap_first[n], nq = a.snap_cnt[n];
+        for (int q = q0; q < q0 + nq; ++q) {
+          T* dst = reinterpret_cast<T*>(a.snap) + ((size_t)path * a.n_out + q) * D * D;
+#pragma unroll
+          for (int r = 0; r < R; ++r) st4(dst + (size_t)(r0 + j0 + r) * D + i0, acc_get(r));
+        }
+      }
       // ---- this step's operator: coefficient tables and Taylor parameters ---------
       double w[MSK_NOPS];
       double shift;
@@ -524,7 +544,7 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const V4<T> v = acc_get(r);
-      st4(reinterpret_cast<T*>(a.out) + (size_t)path * D * D + (size_t)(r0 + j0 + r) * D + i0, v);
+      if (a.out) st4(reinterpret_cast<T*>(a.out) + (size_t)path * D * D + (size_t)(r0 + j0 + r) * D + i0, v);
       mfin = tmax(mfin, tmax(tmax(absnan(v.x), absnan(v.y)), tmax(absnan(v.z), absnan(v.w))));
     }
     if (a.work && rank == 0 && tid == 0) atomicAdd(a.work, nmv);

@@ -67,9 +67,13 @@ struct VarArgs {
   const double* Wt;   // Magnus: [paths][steps][MSK_NWT]
   const double* dW;   // Euler:  [paths][steps]
   const double* psi;  // [d]
-  void* out;
+  void* out;          // [paths][d][d] of T; null: the final state is not stored
   uint32_t* status;
   unsigned long long* work;
+  void* snap;         // snapshots at step starts for output times inside the steps (see EngineSnap)
+  const int* snap_first;
+  const int* snap_cnt;
+  int n_out, u0_self;
   int64_t paths;
   int steps, d, C, RS, ng, R;
   double dx, dv, av, kappa, T, s_cap;
@@ -265,9 +269,11 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
   for (int64_t path = cid; path < a.paths; path += ncl) {
     int ft = FT, fo = FP;   // Euler ping-pongs t between fields 0 and 1
     T m0 = T(0);
+    const T* self0 = a.u0_self ? reinterpret_cast<const T*>(a.out) + (size_t)path * d * d : nullptr;
     for (int r = 0; r < nrows; ++r) {
       const int p = p0 + r;
-      const T v = (T)a.u0[(size_t)(r0 + p) * d + col];
+      const size_t g = (size_t)(r0 + p) * d + col;
+      const T v = self0 ? self0[g] : (T)a.u0[g];
       accs[p * d + col] = v;
       store(ft, p, v, 2);
       m0 = vmax(m0, vabsnan(v));
@@ -281,6 +287,14 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
     unsigned long long nmv = 0;
 
     for (int n = 0; n < a.steps; ++n) {
+      // snapshots of the state at the step start (output times inside the step)
+      if (a.snap) {
+        const int q0 = a.snap_first[n], nq = a.snap_cnt[n];
+        for (int q = q0; q < q0 + nq; ++q) {
+          T* dst = reinterpret_cast<T*>(a.snap) + ((size_t)path * a.n_out + q) * d * d;
+          for (int r = 0; r < nrows; ++r) dst[(size_t)(r0 + p0 + r) * d + col] = accs[(p0 + r) * d + col];
+        }
+      }
       if constexpr (EULER) {
         const double dt = a.T / a.steps, tn = n * dt;
         const double dWn = a.dW[path * a.steps + n];
@@ -422,7 +436,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
     T mfin = T(0);
     for (int r = 0; r < nrows; ++r) {
       const T v = accs[(p0 + r) * d + col];
-      reinterpret_cast<T*>(a.out)[(size_t)path * d * d + (size_t)(r0 + p0 + r) * d + col] = v;
+      if (a.out) reinterpret_cast<T*>(a.out)[(size_t)path * d * d + (size_t)(r0 + p0 + r) * d + col] = v;
       mfin = vmax(mfin, vabsnan(v));
     }
     if (a.work && rank == 0 && tid == 0) atomicAdd(a.work, nmv);
@@ -733,7 +747,7 @@ msk_status ensure_var_tables(msk_ctx* ctx, cudaStream_t stream) {
 
 msk_status launch_engine_var(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
                              const double* Wt, const double* dW, void* out, uint32_t* status,
-                             cudaStream_t stream) {
+                             cudaStream_t stream, const EngineSnap& x) {
   if (paths == 0) return MSK_OK;
   if (!euler && ctx->coef.kind != MSK_COEF_CONST)
     return msk_fail(ctx, MSK_ERR_UNSUPPORTED,
@@ -747,6 +761,11 @@ msk_status launch_engine_var(msk_ctx* ctx, bool euler, int steps, int64_t paths,
   a.out = out;
   a.status = status;
   a.work = ctx->work;
+  a.snap = x.snap;
+  a.snap_first = x.snap_first;
+  a.snap_cnt = x.snap_cnt;
+  a.n_out = x.n_out;
+  a.u0_self = x.u0_self;
   a.paths = paths;
   a.steps = steps;
   a.d = ctx->d;

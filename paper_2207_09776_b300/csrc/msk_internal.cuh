@@ -81,11 +81,30 @@ msk_status launch_omega(msk_ctx* ctx, int order, int steps, int64_t paths, int p
 msk_status launch_engine(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
                          const double* Wt, const double* dW, void* out, uint32_t* status,
                          cudaStream_t stream);
+// Optional engine behaviour for the solutions at output times inside the steps:
+// snapshots of the state at step starts into snap[path][q] (q = snap_first[n] ..
+// + snap_cnt[n] - 1 at step n, n_out slots per path), and/or starting every path
+// from its own output slot (u0_self).  out may be null (final state not stored).
+struct EngineSnap {
+  void* snap = nullptr;
+  const int* snap_first = nullptr;
+  const int* snap_cnt = nullptr;
+  int n_out = 0;
+  int u0_self = 0;
+};
+msk_status launch_engine_ex(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
+                            const double* Wt, const double* dW, void* out, uint32_t* status,
+                            cudaStream_t stream, const EngineSnap& x);
+// Interval mode of the Brownian and weight kernels (times.cu).
+msk_status launch_brownian_jobs(msk_ctx* ctx, const int64_t* jobs_dev, int64_t njobs, double* out,
+                                cudaStream_t stream, bool nf32);
+msk_status launch_omega_jobs(msk_ctx* ctx, int order, int64_t njobs, int precision, const double* F,
+                             const double* job_th_dev, double* Wt, cudaStream_t stream);
 // Variable-coefficient path (engine_var.cu): the engine, and the traces and
 // norms of its six operators for the (s, m) selection (rebuilt when dirty).
 msk_status launch_engine_var(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
                              const double* Wt, const double* dW, void* out, uint32_t* status,
-                             cudaStream_t stream);
+                             cudaStream_t stream, const EngineSnap& x);
 msk_status ensure_var_tables(msk_ctx* ctx, cudaStream_t stream);
 msk_status launch_psi_rational(msk_ctx* ctx, double c, cudaStream_t stream);
 

@@ -32,6 +32,7 @@ struct OmegaArgs {
   const double* band;
   const double* trace;
   const double* var;   // x profile: traces [0, 6) and shifted norms [6, 12) of the six operators; else null
+  const double* job_th;   // interval mode: (t0, h) per record; else null (step n: t0 = n h, h = T / steps)
   int D, order, steps, precision;
   int64_t paths;
   double T, dx;
@@ -63,10 +64,8 @@ __device__ double g3_int(const CoefDev& c, double t0, double h) {
   return 2.0 * s_alpha - h * alpha_bar(c, t0, h);
 }
 
-__device__ void magnus_weights(const OmegaArgs& a, int n, const double* f, double w[MSK_NOPS]) {
+__device__ void magnus_weights(const OmegaArgs& a, double tn, double h, const double* f, double w[MSK_NOPS]) {
   for (int k = 0; k < MSK_NOPS; ++k) w[k] = 0.0;
-  const double h = a.T / a.steps;
-  const double tn = n * h;
   const double dW = f[MSK_F_DW], I1 = f[MSK_F_I1], I2 = f[MSK_F_I2], I3 = f[MSK_F_I3];
   const double cA = 0.5 * I2 - 0.5 * dW * I1 + h * dW * dW / 12.0;
   const double cB = I3 - 0.5 * h * I1 - h * h * dW / 12.0;
@@ -124,9 +123,16 @@ __device__ double row_abs_sum(const double c[MSK_NCOEF]) {
 __global__ void omega_kernel(OmegaArgs a, const double* __restrict__ F, double* __restrict__ Wt) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= a.paths * a.steps) return;
-  const int n = (int)(idx % a.steps);
+  double tn, h;
+  if (a.job_th) {
+    tn = a.job_th[2 * idx];
+    h = a.job_th[2 * idx + 1];
+  } else {
+    h = a.T / a.steps;
+    tn = (double)(idx % a.steps) * h;
+  }
   double w[MSK_NOPS];
-  magnus_weights(a, n, F + idx * MSK_NF, w);
+  magnus_weights(a, tn, h, F + idx * MSK_NF, w);
   const int D = a.D;
   double mu, nrm = 0.0;
   if (a.var) {
@@ -209,10 +215,27 @@ msk_status launch_omega(msk_ctx* ctx, int order, int steps, int64_t paths, int p
     st0 = ensure_var_tables(ctx, stream);
     if (st0 != MSK_OK) return st0;
   }
-  OmegaArgs a{ctx->band, ctx->aux, ctx->xprof ? ctx->var_tab : nullptr, ctx->d, order, steps, precision, paths,
-              ctx->T, ctx->dx, coef_dev(ctx->coef), kMskScaleCap};
+  OmegaArgs a{ctx->band, ctx->aux, ctx->xprof ? ctx->var_tab : nullptr, nullptr, ctx->d, order, steps, precision,
+              paths, ctx->T, ctx->dx, coef_dev(ctx->coef), kMskScaleCap};
   omega_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(a, F, Wt);
   return msk_cuda(ctx, cudaGetLastError(), "omega kernel");
+}
+
+// Weight records of arbitrary intervals: job_th_dev[2 i], [2 i + 1] = (t0, h) of
+// interval i, F its functionals (njobs records, one step each).
+msk_status launch_omega_jobs(msk_ctx* ctx, int order, int64_t njobs, int precision, const double* F,
+                             const double* job_th_dev, double* Wt, cudaStream_t stream) {
+  msk_status st0 = msk_prepare_omega(ctx);
+  if (st0 != MSK_OK) return st0;
+  if (njobs == 0) return MSK_OK;
+  if (ctx->xprof) {
+    st0 = ensure_var_tables(ctx, stream);
+    if (st0 != MSK_OK) return st0;
+  }
+  OmegaArgs a{ctx->band, ctx->aux, ctx->xprof ? ctx->var_tab : nullptr, job_th_dev, ctx->d, order, 1, precision,
+              njobs, ctx->T, ctx->dx, coef_dev(ctx->coef), kMskScaleCap};
+  omega_kernel<<<(unsigned)((njobs + 127) / 128), 128, 0, stream>>>(a, F, Wt);
+  return msk_cuda(ctx, cudaGetLastError(), "omega kernel (intervals)");
 }
 
 extern "C" msk_status msk_omega_weights(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
