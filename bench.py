@@ -552,6 +552,18 @@ def run_ours(a):
             _, e2 = solver.error(u2[:n].contiguous(), msk.MSK_F32, ref=refc, ref_precision=msk.MSK_F64)
             comparators.setdefault("magnus_fp32_m2", {})[f"K{Kc}"] = {
                 "paths_per_s": Pc / (ms2 / 1e3), "err": float(e2.cpu()[0])}
+        # solutions at the midpoint and the end of every sub-interval (2K output times,
+        # the parallel-in-time evaluation of Section 3 "Implementation") against the plain solve
+        L = w.n_fine // K
+        cells = sorted([(2 * i + 1) * L // 2 for i in range(K)] + [(i + 1) * L for i in range(K)])
+        ut = torch.empty(Pc * len(cells) * w.d * w.d, dtype=torch.float32, device=dev)
+        _, ms_t = timed(lambda: msk.msk_solve_magnus_times(ctx, ORDER, K, Pc, msk.MSK_F32, cells, ut, None,
+                                                           stream))
+        _, ms_p = timed(lambda: solver.magnus(ORDER, K, paths=Pc, precision=msk.MSK_F32))
+        comparators["output_times"] = {
+            "paths": Pc, "n_times": len(cells), "paths_per_s": Pc / (ms_t / 1e3),
+            "solutions_per_s": Pc * len(cells) / (ms_t / 1e3), "ms": ms_t, "plain_solve_ms": ms_p,
+            "time_vs_plain_solve": ms_t / ms_p}
 
     # ---- learned surrogate of the same workload (setup untimed; own timed serve steps) ----------
     if not a.no_surrogate and world == 1:

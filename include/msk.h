@@ -227,11 +227,11 @@ msk_status msk_magnus_from_weights(msk_ctx* ctx, int steps, int64_t paths, int p
  * time, all times and trajectories in parallel).  times_cells (host, n_times
  * entries, strictly increasing, each in 1 .. n_fine) are output times in fine cells,
  * t_q = T times_cells[q] / n_fine.  With `steps` sub-intervals of L = n_fine/steps
- * cells, t_q lies in sub-interval n = (times_cells[q] - 1) / L and
+ * cells and n = times_cells[q] / L (t_n <= t_q < t_{n+1}),
  *   u(t_q) = exp(Y(t_n, t_q)) u(t_n),
  * Y(t_n, t_q) the order-`order` logarithm of Eq. MagnusFormulas over [t_n, t_q] (its
  * functionals from the same Brownian path) and u(t_n) the iterated solution after n
- * steps; an output at a sub-interval end equals the iterated solution there.
+ * steps; an output at a sub-interval end is the iterated solution there.
  * u_out_dev: [paths][n_times][v][x] of double (MSK_F64) or float (MSK_F32),
  * caller-owned; path_status_dev (nullable): uint32[paths * n_times], the MSK_PATH_*
  * bits of the partial step OR those of the path's whole iterated solve.  Scratch is

@@ -55,9 +55,10 @@ struct EngineArgs {
   const double* Wt;   // Magnus: [paths][steps][MSK_NWT]
   const double* dW;   // Euler:  [paths][steps]
   void* out;          // [paths][d][d] of T; null: the final state is not stored
-  // Snapshots for output times inside the steps: at the start of step n the
-  // state is stored into snap[path][q] (T, d x d) for q = snap_first[n] ..
-  // snap_first[n] + snap_cnt[n] - 1; snap null: none.
+  // Snapshots for output times: at the start of step n (n = steps: after the
+  // last step) the state is stored into snap[path][q] (T, d x d) for
+  // q = snap_first[n] .. snap_first[n] + snap_cnt[n] - 1 (tables of steps + 1
+  // entries); snap null: none.
   void* snap;
   const int* snap_first;
   const int* snap_cnt;
@@ -394,16 +395,19 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
     bool scale_cap = false;
     unsigned long long nmv = 0;
 
-    for (int n = 0; n < a.steps; ++n) {
-      // ---- snapshots of the state at the step start (output times inside the step)
-      if (a.snap) {
-        const int q0 = a.snap_first[n], nq = a.snap_cnt[n];
-        for (int q = q0; q < q0 + nq; ++q) {
-          T* dst = reinterpret_cast<T*>(a.snap) + ((size_t)path * a.n_out + q) * D * D;
+    // snapshots of the state at the start of step n (n = steps: the final state)
+    auto snapshot = [&](int n) {
+      if (!a.snap) return;
+      const int q0 = a.snap_first[n], nq = a.snap_cnt[n];
+      for (int q = q0; q < q0 + nq; ++q) {
+        T* dst = reinterpret_cast<T*>(a.snap) + ((size_t)path * a.n_out + q) * D * D;
 #pragma unroll
-          for (int r = 0; r < R; ++r) st4(dst + (size_t)(r0 + j0 + r) * D + i0, acc_get(r));
-        }
+        for (int r = 0; r < R; ++r) st4(dst + (size_t)(r0 + j0 + r) * D + i0, acc_get(r));
       }
+    };
+
+    for (int n = 0; n < a.steps; ++n) {
+      snapshot(n);
       // ---- this step's operator: coefficient tables and Taylor parameters ---------
       double w[MSK_NOPS];
       double shift;
@@ -539,6 +543,7 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
       }
     }
 
+    snapshot(a.steps);
     // ---- solution, work counter and path status ----------------------------------
     T mfin = T(0);
 #pragma unroll

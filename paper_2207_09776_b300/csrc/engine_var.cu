@@ -286,15 +286,17 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
     bool scale_cap = false;
     unsigned long long nmv = 0;
 
-    for (int n = 0; n < a.steps; ++n) {
-      // snapshots of the state at the step start (output times inside the step)
-      if (a.snap) {
-        const int q0 = a.snap_first[n], nq = a.snap_cnt[n];
-        for (int q = q0; q < q0 + nq; ++q) {
-          T* dst = reinterpret_cast<T*>(a.snap) + ((size_t)path * a.n_out + q) * d * d;
-          for (int r = 0; r < nrows; ++r) dst[(size_t)(r0 + p0 + r) * d + col] = accs[(p0 + r) * d + col];
-        }
+    // snapshots of the state at the start of step n (n = steps: the final state)
+    auto snapshot = [&](int n) {
+      if (!a.snap) return;
+      const int q0 = a.snap_first[n], nq = a.snap_cnt[n];
+      for (int q = q0; q < q0 + nq; ++q) {
+        T* dst = reinterpret_cast<T*>(a.snap) + ((size_t)path * a.n_out + q) * d * d;
+        for (int r = 0; r < nrows; ++r) dst[(size_t)(r0 + p0 + r) * d + col] = accs[(p0 + r) * d + col];
       }
+    };
+    for (int n = 0; n < a.steps; ++n) {
+      snapshot(n);
       if constexpr (EULER) {
         const double dt = a.T / a.steps, tn = n * dt;
         const double dWn = a.dW[path * a.steps + n];
@@ -432,6 +434,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
       }
     }
 
+    snapshot(a.steps);
     // ---- solution, work counter and path status
     T mfin = T(0);
     for (int r = 0; r < nrows; ++r) {

@@ -83,8 +83,9 @@ msk_status launch_engine(msk_ctx* ctx, bool euler, int steps, int64_t paths, int
                          cudaStream_t stream);
 // Optional engine behaviour for the solutions at output times inside the steps:
 // snapshots of the state at step starts into snap[path][q] (q = snap_first[n] ..
-// + snap_cnt[n] - 1 at step n, n_out slots per path), and/or starting every path
-// from its own output slot (u0_self).  out may be null (final state not stored).
+// + snap_cnt[n] - 1 at the start of step n, n = 0 .. steps, n = steps meaning after
+// the last step; n_out slots per path), and/or starting every path from its own
+// output slot (u0_self).  out may be null (final state not stored).
 struct EngineSnap {
   void* snap = nullptr;
   const int* snap_first = nullptr;

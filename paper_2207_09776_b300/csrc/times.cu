@@ -2,16 +2,18 @@
 // sub-interval of the iterated scheme the Magnus expansion can be evaluated at
 // every requested time, all times and trajectories in parallel).
 //
-// An output time t = T c / n_fine lies in the sub-interval n = (c - 1) / L
-// (L = n_fine / steps cells); its solution is exp(Y(t_n, t)) U(t_n), with
-// Y(t_n, t) the order-`order` logarithm over the cells n L .. c - 1 and U(t_n)
-// the iterated solution after n full steps.  Two engine launches:
+// An output time t = T c / n_fine with t_n <= t < t_{n+1}, n = c / L (L =
+// n_fine / steps cells), has the solution exp(Y(t_n, t)) U(t_n), with Y(t_n, t)
+// the order-`order` logarithm over the cells n L .. c - 1 and U(t_n) the
+// iterated solution after n full steps (a time on a sub-interval end is U(t_n)
+// itself: an empty interval).  Two engine launches:
 //   1. the iterated solve of every path, storing the state at the start of each
-//      step that contains output times into those outputs' slots (no final
-//      output);
+//      step that holds output times (and after the last step, for t = T) into
+//      those outputs' slots (no final output);
 //   2. one partial step per (path, output time): functionals and weights of its
 //      interval, and the exponential action started from the slot's snapshot,
-//      written over it.  All paths x outputs run concurrently.
+//      written over it (empty intervals: zero weights, no Taylor term, the
+//      snapshot stays).  All paths x outputs run concurrently.
 #include <algorithm>
 #include <vector>
 
@@ -53,10 +55,10 @@ extern "C" msk_status msk_solve_magnus_times(msk_ctx* ctx, int order, int steps,
   const int64_t jobs = paths * n_times;
   const double delta = ctx->T / (double)ctx->n_fine;
   // host tables: step -> its outputs; (path, output) -> interval and (t0, h)
-  std::vector<int> first(steps, 0), cnt(steps, 0);
+  std::vector<int> first(steps + 1, 0), cnt(steps + 1, 0);
   std::vector<int64_t> step_of(n_times);
   for (int q = 0; q < n_times; ++q) {
-    const int64_t n = (times_cells[q] - 1) / L;
+    const int64_t n = times_cells[q] / L;   // 0 .. steps
     step_of[q] = n;
     if (cnt[n] == 0) first[n] = q;
     ++cnt[n];
@@ -77,7 +79,7 @@ extern "C" msk_status msk_solve_magnus_times(msk_ctx* ctx, int order, int steps,
   const size_t nF = (size_t)paths * steps * MSK_NF, nW = (size_t)paths * steps * MSK_NWT;
   const size_t nFj = (size_t)jobs * MSK_NF, nWj = (size_t)jobs * MSK_NWT;
   const size_t doubles = nF + nW + nFj + nWj + 2 * (size_t)jobs + 3 * (size_t)jobs   // jt as int64
-                         + (size_t)steps + ((size_t)paths + 1) / 2 + 4;              // first/cnt, status
+                         + (size_t)steps + 1 + ((size_t)paths + 1) / 2 + 4;          // first/cnt, status
   st = msk_ensure_scratch(ctx, doubles * sizeof(double));
   if (st != MSK_OK) return st;
   double* F = reinterpret_cast<double*>(ctx->scratch);
@@ -87,18 +89,18 @@ extern "C" msk_status msk_solve_magnus_times(msk_ctx* ctx, int order, int steps,
   double* thd = Wtj + nWj;
   int64_t* jtd = reinterpret_cast<int64_t*>(thd + 2 * jobs);
   int* firstd = reinterpret_cast<int*>(jtd + 3 * jobs);
-  int* cntd = firstd + steps;
-  uint32_t* main_st = reinterpret_cast<uint32_t*>(cntd + steps);
+  int* cntd = firstd + steps + 1;
+  uint32_t* main_st = reinterpret_cast<uint32_t*>(cntd + steps + 1);
   st = msk_cuda(ctx, cudaMemcpyAsync(thd, th.data(), th.size() * sizeof(double), cudaMemcpyHostToDevice, s),
                 "copy interval times");
   if (st == MSK_OK)
     st = msk_cuda(ctx, cudaMemcpyAsync(jtd, jt.data(), jt.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s),
                   "copy intervals");
   if (st == MSK_OK)
-    st = msk_cuda(ctx, cudaMemcpyAsync(firstd, first.data(), steps * sizeof(int), cudaMemcpyHostToDevice, s),
+    st = msk_cuda(ctx, cudaMemcpyAsync(firstd, first.data(), (steps + 1) * sizeof(int), cudaMemcpyHostToDevice, s),
                   "copy step table");
   if (st == MSK_OK)
-    st = msk_cuda(ctx, cudaMemcpyAsync(cntd, cnt.data(), steps * sizeof(int), cudaMemcpyHostToDevice, s),
+    st = msk_cuda(ctx, cudaMemcpyAsync(cntd, cnt.data(), (steps + 1) * sizeof(int), cudaMemcpyHostToDevice, s),
                   "copy step table");
   if (st != MSK_OK) return st;
   // the pageable copies above are staged before they return; the host tables may go out of scope
