@@ -145,6 +145,22 @@ msk_status msk_set_coefficients(msk_ctx* ctx, const msk_coeffs* coeffs);
  * MSK_ERR_ARG / MSK_ERR_NONFINITE before any device work. */
 msk_status msk_set_x_profile(msk_ctx* ctx, int kind, double c, const double* psi_host);
 
+/* General coefficients (Eq. generalSPDE, Section 2 "Computation of A and B"):
+ * coef_host (host, copied) holds 9 grids [9][v][x] of the time-independent
+ * coefficient functions at the interior nodes, in the order
+ *   h, f^x, f^v, g^xx, g^xv, g^vv, sigma, sigma^x, sigma^v,
+ * of du = (h u + f^x u_x + f^v u_v + g^xx/2 u_xx + g^xv u_xv + g^vv/2 u_vv) dt
+ *        + (sigma u + sigma^x u_x + sigma^v u_v) dW.
+ * B becomes the nine-point and A the five-point central-difference stencil with
+ * these per-point coefficients (zero Dirichlet boundary), and msk_solve_magnus /
+ * _noalloc / _times, msk_magnus_from_weights, msk_solve_euler and msk_select_steps
+ * run the general-coefficient engine (Omega by composing B and A; the coefficient
+ * set of msk_set_coefficients and any x profile are ignored while this is set).
+ * NULL returns to the Langevin operators.  msk_apply_omega, msk_explicit_solution,
+ * msk_error with MSK_REF_EXPLICIT and batches -> MSK_ERR_UNSUPPORTED.  Non-finite
+ * values -> MSK_ERR_NONFINITE before any device work.  Synchronises the device. */
+msk_status msk_set_general_coefficients(msk_ctx* ctx, const double* coef_host);
+
 /* Set a Gaussian initial datum; evaluated on the interior grid on the device. */
 msk_status msk_set_initial_gaussian(msk_ctx* ctx, const msk_gaussian* g);
 

@@ -73,6 +73,7 @@ SIGNATURES = {
     "msk_set_coefficients": (_INT, [_P, ctypes.POINTER(msk_coeffs)]),
     "msk_set_initial_gaussian": (_INT, [_P, ctypes.POINTER(msk_gaussian)]),
     "msk_set_x_profile": (_INT, [_P, _INT, _DBL, _P]),
+    "msk_set_general_coefficients": (_INT, [_P, _P]),
     "msk_set_initial": (_INT, [_P, _P, _P]),
     "msk_set_seed": (_INT, [_P, _U64, _U64, _I64, _DBL]),
     "msk_philox_words": (_INT, [_U64, _U64, ctypes.c_uint32, _I64, _I64, _P, _P]),
@@ -207,6 +208,17 @@ def msk_set_x_profile(ctx, kind, c=1.0, psi=None):
         vals = [float(x) for x in psi]
         buf = (ctypes.c_double * len(vals))(*vals)
     _check(load_library().msk_set_x_profile(ctx, kind, c, ctypes.cast(buf, _P) if buf is not None else None), ctx)
+
+
+def msk_set_general_coefficients(ctx, coef=None):
+    """coef: None, or 9 x d x d host values (numpy array or nested sequence) of h, f^x, f^v,
+    g^xx, g^xv, g^vv, sigma, sigma^x, sigma^v on the [v][x] grid."""
+    if coef is None:
+        _check(load_library().msk_set_general_coefficients(ctx, None), ctx)
+        return
+    import numpy as np
+    arr = np.ascontiguousarray(np.asarray(coef, dtype=np.float64).reshape(-1))
+    _check(load_library().msk_set_general_coefficients(ctx, arr.ctypes.data_as(_P)), ctx)
 
 
 def msk_set_initial_gaussian(ctx, mean, cov, scale=1.0):

@@ -299,7 +299,7 @@ extern "C" msk_status msk_batch_create(msk_batch** out, const msk_batch_item* it
     if (!it.ctx || it.ctx->device != dev) return MSK_ERR_ARG;
     const int d = it.ctx->d;
     if (d != 64 && d != 128 && d != 256) return MSK_ERR_UNSUPPORTED;
-    if (it.ctx->xprof) return MSK_ERR_UNSUPPORTED;   // batches run the constant-coefficient engine
+    if (it.ctx->xprof || it.ctx->gen) return MSK_ERR_UNSUPPORTED;   // batches run the constant-coefficient engine
     if (it.order < 1 || it.order > 3 || it.steps < 1 || it.ctx->n_fine % it.steps != 0 || it.paths < 0)
       return MSK_ERR_ARG;
     if (it.paths > 0 && !it.u_out_dev) return MSK_ERR_ARG;

@@ -55,6 +55,8 @@ extern "C" void msk_destroy(msk_ctx* ctx) {
   if (ctx->tab) cudaFree(ctx->tab);
   if (ctx->psi) cudaFree(ctx->psi);
   if (ctx->var_tab) cudaFree(ctx->var_tab);
+  if (ctx->gen64) cudaFree(ctx->gen64);
+  if (ctx->gen32) cudaFree(ctx->gen32);
   delete ctx;
 }
 

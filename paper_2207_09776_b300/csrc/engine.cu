@@ -104,7 +104,8 @@ msk_status launch_engine_ex(msk_ctx* ctx, bool euler, int steps, int64_t paths, 
                             const double* Wt, const double* dW, void* out, uint32_t* status,
                             cudaStream_t stream, const EngineSnap& x) {
   if (paths == 0) return MSK_OK;
-  if (ctx->xprof) return launch_engine_var(ctx, euler, steps, paths, precision, Wt, dW, out, status, stream, x);
+  if (ctx->xprof || ctx->gen)
+    return launch_engine_var(ctx, euler, steps, paths, precision, Wt, dW, out, status, stream, x);
   EngineArgs a{};
   a.snap = x.snap;
   a.snap_first = x.snap_first;

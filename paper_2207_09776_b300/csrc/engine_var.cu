@@ -74,6 +74,8 @@ struct VarArgs {
   const int* snap_first;
   const int* snap_cnt;
   int n_out, u0_self;
+  const void* gB;     // general coefficients: B stencil [9][d][d] and A stencil [5][d][d] (T)
+  const void* gA;
   int64_t paths;
   int steps, d, C, RS, ng, R;
   double dx, dv, av, kappa, T, s_cap;
@@ -459,6 +461,328 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
   }
 }
 
+// ------------------------------------------------------------------ general coefficients
+// Eq. generalSPDE with time-independent coefficient functions of (x, v): B is the
+// nine-point stencil of h, f^x, f^v, g^xx, g^xv, g^vv and A the five-point stencil
+// of sigma, sigma^x, sigma^v, both with per-point coefficients (a stencil field of
+// 9 + 5 values per grid point, read through the read-only cache).  The same
+// six-operator logarithm is applied by composition in three passes
+//   1: a = A t, b = B t      2: p, q from A a, A b, B a, B b      3: B p + A q - mu t
+// over five shared-memory fields with one halo row and one zero column (the
+// stencils have radius one, diagonals included) plus the partial sum.
+constexpr int kGenFields = 5;
+
+struct GenLayout {
+  int FS, off_acc, off_scale, off_slot, off_cslot, total;
+};
+__host__ __device__ inline GenLayout gen_layout(int RS, int d, int NT) {
+  GenLayout L;
+  L.FS = (RS + 2) * (d + 2);
+  L.off_acc = kGenFields * L.FS;
+  L.off_scale = L.off_acc + RS * d;
+  L.off_slot = L.off_scale + kVarMaxTerms + 1;
+  L.off_cslot = L.off_slot + 4 * (NT / 32);
+  L.total = L.off_cslot + 4;
+  return L;
+}
+
+template <typename T, bool EULER>
+__global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const VarArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x, NT = blockDim.x, NW = NT >> 5;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int C = a.C, RS = a.RS, d = a.d, W = d + 2;
+  const int rank = C > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const GenLayout L = gen_layout(RS, d, NT);
+  const int FS = L.FS;
+  T* accs = sm + L.off_acc;
+  T* scale_tab = sm + L.off_scale;
+  T* slots = sm + L.off_slot;
+  T* cslot = sm + L.off_cslot;
+  const T* __restrict__ gB = reinterpret_cast<const T*>(a.gB);
+  const T* __restrict__ gA = reinterpret_cast<const T*>(a.gA);
+  const int dd = d * d;
+
+  auto sync_all = [&]() {
+    if (C > 1) cg::this_cluster().sync();
+    else __syncthreads();
+  };
+
+  const int r0 = rank * RS;
+  const int rs = min(RS, d - r0);
+  const bool act = tid < a.ng * d;   // group-major (row group, column) per thread
+  const int col = act ? tid % d : 0, grp = act ? tid / d : 0;
+  const int p0 = grp * a.R;
+  const int nrows = act ? max(0, min(a.R, rs - p0)) : 0;
+
+  for (int e = tid; e < kGenFields * FS; e += NT) sm[e] = T(0);
+  sync_all();
+
+  const uint32_t peer_lo = (C > 1 && rank > 0) ? cl_addr(sm, rank - 1) : 0u;
+  const uint32_t peer_hi = (C > 1 && rank < C - 1) ? cl_addr(sm, rank + 1) : 0u;
+  auto off = [&](int p) -> int { return (p + 1) * W + col + 1; };   // within a field
+  auto store = [&](int f, int p, T v) {
+    sm[f * FS + off(p)] = v;
+    if (C > 1) {
+      if (p == 0 && rank > 0) cl_st(peer_lo + (uint32_t)((f * FS + off(RS)) * (int)sizeof(T)), v);
+      if (p == rs - 1 && rank < C - 1) cl_st(peer_hi + (uint32_t)((f * FS + off(-1)) * (int)sizeof(T)), v);
+    }
+  };
+  // stencils at the own point of local row p (global index g) applied to field F
+  auto applyB = [&](const T* F, int o, int g) -> T {
+    T v = __ldg(gB + g) * F[o];
+    v = fma(__ldg(gB + dd + g), F[o + 1], v);
+    v = fma(__ldg(gB + 2 * dd + g), F[o - 1], v);
+    v = fma(__ldg(gB + 3 * dd + g), F[o + W], v);
+    v = fma(__ldg(gB + 4 * dd + g), F[o - W], v);
+    v = fma(__ldg(gB + 5 * dd + g), F[o + W + 1], v);
+    v = fma(__ldg(gB + 6 * dd + g), F[o + W - 1], v);
+    v = fma(__ldg(gB + 7 * dd + g), F[o - W + 1], v);
+    return fma(__ldg(gB + 8 * dd + g), F[o - W - 1], v);
+  };
+  auto applyA = [&](const T* F, int o, int g) -> T {
+    T v = __ldg(gA + g) * F[o];
+    v = fma(__ldg(gA + dd + g), F[o + 1], v);
+    v = fma(__ldg(gA + 2 * dd + g), F[o - 1], v);
+    v = fma(__ldg(gA + 3 * dd + g), F[o + W], v);
+    return fma(__ldg(gA + 4 * dd + g), F[o - W], v);
+  };
+
+  auto publish = [&](int par, T mn, T ma) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = vmax(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      ma = vmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+    }
+    if (lane == 0) {
+      slots[(par * NW + warp) * 2 + 0] = mn;
+      slots[(par * NW + warp) * 2 + 1] = ma;
+    }
+    if (C > 1) {
+      __syncthreads();
+      if (warp == 0) {
+        T x = T(0), y = T(0);
+        for (int q = lane; q < NW; q += 32) {
+          x = vmax(x, slots[(par * NW + q) * 2 + 0]);
+          y = vmax(y, slots[(par * NW + q) * 2 + 1]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          x = vmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+          y = vmax(y, __shfl_xor_sync(0xffffffffu, y, o));
+        }
+        if (lane == 0) {
+          cslot[par * 2 + 0] = x;
+          cslot[par * 2 + 1] = y;
+        }
+      }
+    }
+  };
+  auto gather = [&](int par, T& gn, T& ga) {
+    gn = T(0);
+    ga = T(0);
+    if (C > 1) {
+      if (lane < C) {
+        const uint32_t q = cl_addr(cslot + par * 2, lane);
+        gn = cl_ld(q, T(0));
+        ga = cl_ld(q + (uint32_t)sizeof(T), T(0));
+      }
+    } else {
+      for (int q = lane; q < NW; q += 32) {
+        gn = vmax(gn, slots[(par * NW + q) * 2 + 0]);
+        ga = vmax(ga, slots[(par * NW + q) * 2 + 1]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      gn = vmax(gn, __shfl_xor_sync(0xffffffffu, gn, o));
+      ga = vmax(ga, __shfl_xor_sync(0xffffffffu, ga, o));
+    }
+  };
+
+  const T tol = sizeof(T) == 4 ? (T)a.tol32 : (T)a.tol64;
+  const int64_t cid = blockIdx.x / C, ncl = gridDim.x / C;
+  constexpr int FB = 2, FP = 3, FQ = 4;
+  int par = 0;
+
+  for (int64_t path = cid; path < a.paths; path += ncl) {
+    int ft = 0, fa = 1;
+    T m0 = T(0);
+    const T* self0 = a.u0_self ? reinterpret_cast<const T*>(a.out) + (size_t)path * dd : nullptr;
+    for (int r = 0; r < nrows; ++r) {
+      const int p = p0 + r;
+      const size_t g = (size_t)(r0 + p) * d + col;
+      const T v = self0 ? self0[g] : (T)a.u0[g];
+      accs[p * d + col] = v;
+      store(ft, p, v);
+      m0 = vmax(m0, vabsnan(v));
+    }
+    publish(par, m0, m0);
+    sync_all();
+    T unorm, u0max;
+    gather(par, unorm, u0max);
+    par ^= 1;
+    bool scale_cap = false;
+    unsigned long long nmv = 0;
+    auto snapshot = [&](int n) {
+      if (!a.snap) return;
+      const int q0 = a.snap_first[n], nq = a.snap_cnt[n];
+      for (int q = q0; q < q0 + nq; ++q) {
+        T* dst = reinterpret_cast<T*>(a.snap) + ((size_t)path * a.n_out + q) * dd;
+        for (int r = 0; r < nrows; ++r) dst[(size_t)(r0 + p0 + r) * d + col] = accs[(p0 + r) * d + col];
+      }
+    };
+
+    for (int n = 0; n < a.steps; ++n) {
+      snapshot(n);
+      if constexpr (EULER) {
+        // t + dt B t + dW A t (time-independent coefficients)
+        const T kt = (T)(a.T / a.steps), kw = (T)a.dW[path * a.steps + n];
+        const T* t = sm + ft * FS;
+        for (int r = 0; r < nrows; ++r) {
+          const int p = p0 + r, o = off(p), g = (r0 + p) * d + col;
+          const T tn_ = fma(kt, applyB(t, o, g), fma(kw, applyA(t, o, g), t[o]));
+          store(fa, p, tn_);
+          accs[p * d + col] = tn_;
+        }
+        sync_all();
+        const int sw = ft;
+        ft = fa;
+        fa = sw;
+        ++nmv;
+      } else {
+        const double* rec = a.Wt + ((size_t)path * a.steps + n) * MSK_NWT;
+        const T wB = (T)rec[MSK_OP_BX], wA = (T)rec[MSK_OP_A0], wAA = (T)rec[MSK_OP_A0A0];
+        const T wBA = (T)rec[MSK_OP_BX_A0], wBAA = (T)rec[MSK_OP_BXA0_A0], wBAB = (T)rec[MSK_OP_BXA0_BX];
+        const double mu = rec[MSK_WT_MU];
+        const int s_steps = max(1, (int)rec[MSK_WT_S]);
+        const int m_terms = min((int)rec[MSK_WT_M], kVarMaxTerms);
+        if (rec[MSK_WT_S] >= a.s_cap) scale_cap = true;
+        const T te = (T)exp(mu / s_steps);
+        for (int k = tid; k <= kVarMaxTerms; k += NT)
+          scale_tab[k] = (T)(k == 0 ? 1.0 : 1.0 / ((double)s_steps * k));
+        __syncthreads();
+        for (int sub = 0; sub < s_steps; ++sub) {
+          T c1n = unorm;
+          for (int k = 1; k <= m_terms; ++k) {
+            const T sc = scale_tab[k];
+            const T scmu = (T)(mu / ((double)s_steps * k));
+            {   // pass 1: a = A t, b = B t
+              const T* t = sm + ft * FS;
+              for (int r = 0; r < nrows; ++r) {
+                const int p = p0 + r, o = off(p), g = (r0 + p) * d + col;
+                store(fa, p, applyA(t, o, g));
+                store(FB, p, applyB(t, o, g));
+              }
+            }
+            sync_all();
+            {   // pass 2: p, q
+              const T* t = sm + ft * FS;
+              const T* Af = sm + fa * FS;
+              const T* Bf = sm + FB * FS;
+              for (int r = 0; r < nrows; ++r) {
+                const int p = p0 + r, o = off(p), g = (r0 + p) * d + col;
+                const T aa = applyA(Af, o, g), ab = applyA(Bf, o, g);
+                const T ba = applyB(Af, o, g), bb = applyB(Bf, o, g);
+                const T tc = t[o], ac = Af[o], bc = Bf[o];
+                const T P = fma(wB, tc, fma(wBA, ac, fma(wBAA, aa, wBAB * fma(T(2), ab, -ba))));
+                const T Q = fma(wA, tc, fma(wAA, ac, fma(-wBA, bc, fma(wBAA, fma(T(-2), ba, ab), -wBAB * bb))));
+                store(FP, p, P);
+                store(FQ, p, Q);
+              }
+            }
+            sync_all();
+            T mn = T(0), ma = T(0);
+            {   // pass 3: next term into field fa (a is no longer needed)
+              const T* t = sm + ft * FS;
+              const T* Pf = sm + FP * FS;
+              const T* Qf = sm + FQ * FS;
+              for (int r = 0; r < nrows; ++r) {
+                const int p = p0 + r, o = off(p), g = (r0 + p) * d + col;
+                const T tn_ = fma(sc, applyB(Pf, o, g) + applyA(Qf, o, g), -scmu * t[o]);
+                store(fa, p, tn_);
+                T& ac = accs[p * d + col];
+                const T s_ = ac + tn_;
+                ac = s_;
+                mn = vmax(mn, fabs(tn_));
+                ma = vmax(ma, fabs(s_));
+              }
+            }
+            publish(par, mn, ma);
+            sync_all();
+            T gn, ga;
+            gather(par, gn, ga);
+            par ^= 1;
+            const int sw = ft;
+            ft = fa;
+            fa = sw;
+            ++nmv;
+            unorm = ga;
+            if (c1n + gn <= tol * ga) break;
+            c1n = gn;
+          }
+          for (int r = 0; r < nrows; ++r) {
+            T& ac = accs[(p0 + r) * d + col];
+            const T v = ac * te;
+            ac = v;
+            store(fa, p0 + r, v);
+          }
+          unorm = unorm * te;
+          sync_all();
+          const int sw = ft;
+          ft = fa;
+          fa = sw;
+        }
+      }
+    }
+
+    snapshot(a.steps);
+    T mfin = T(0);
+    for (int r = 0; r < nrows; ++r) {
+      const T v = accs[(p0 + r) * d + col];
+      if (a.out) reinterpret_cast<T*>(a.out)[(size_t)path * dd + (size_t)(r0 + p0 + r) * d + col] = v;
+      mfin = vmax(mfin, vabsnan(v));
+    }
+    if (a.work && rank == 0 && tid == 0) atomicAdd(a.work, nmv);
+    publish(par, mfin, mfin);
+    sync_all();
+    T gfin, gfin2;
+    gather(par, gfin, gfin2);
+    par ^= 1;
+    if (a.status && rank == 0 && tid == 0) {
+      uint32_t st = 0;
+      if (!(gfin < T(INFINITY))) st |= MSK_PATH_NONFINITE;
+      if (scale_cap) st |= MSK_PATH_SCALE_CAP;
+      if (!((double)gfin <= 10.0 * (double)u0max)) st |= MSK_PATH_BLOWUP;
+      a.status[path] = st;
+    }
+    sync_all();
+  }
+}
+
+// Stencil fields of the general coefficients c[9][d][d] (h, f^x, f^v, g^xx, g^xv,
+// g^vv, sigma, sigma^x, sigma^v at the nodes; Section 2, "Computation of A and B"):
+//   B: centre h - g^xx/dx^2 - g^vv/dv^2, x+-1: +-f^x/(2dx) + g^xx/(2dx^2),
+//      v+-1: +-f^v/(2dv) + g^vv/(2dv^2), (x+-1, v+-1): +-g^xv/(4 dx dv) (sign of the product)
+//   A: centre sigma, x+-1: +-sigma^x/(2dx), v+-1: +-sigma^v/(2dv)
+// in the order C, E (x+1), W, N (v+1), S, NE, NW, SE, SW (B) and C, E, W, N, S (A).
+__global__ void gen_stencil_kernel(int d, double dx, double dv, const double* c, double* g64, float* g32) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int dd = d * d;
+  if (e >= dd) return;
+  const double h = c[e], fx = c[dd + e], fv = c[2 * dd + e], gxx = c[3 * dd + e], gxv = c[4 * dd + e];
+  const double gvv = c[5 * dd + e], s = c[6 * dd + e], sx = c[7 * dd + e], sv = c[8 * dd + e];
+  const double ix = 0.5 / dx, iv = 0.5 / dv, ixx = 0.5 * gxx / (dx * dx), ivv = 0.5 * gvv / (dv * dv);
+  const double xv = 0.25 * gxv / (dx * dv);
+  const double v[14] = {h - 2.0 * ixx - 2.0 * ivv, fx * ix + ixx, -fx * ix + ixx, fv * iv + ivv, -fv * iv + ivv,
+                        xv, -xv, -xv, xv, s, sx * ix, -sx * ix, sv * iv, -sv * iv};
+  for (int k = 0; k < 14; ++k) {
+    g64[(size_t)k * dd + e] = v[k];
+    g32[(size_t)k * dd + e] = (float)v[k];
+  }
+}
+
 // ------------------------------------------------------------------ operator norms
 // Row (i, j) of each of the six operators, accumulated on a 7 x 7 patch around
 // the point by multiplying the unit row vector from the right by the base
@@ -470,6 +794,7 @@ struct VarOpsDev {
   double av, dv;  // v grid
   double alpha;   // a0 / 2
   const double* psi;
+  const double* gen;   // general coefficients: the 14 stencil fields (B then A); else null
 };
 
 __device__ void add_base_row(const VarOpsDev& o, int op, int i, int j, double c, int pi, int pj,
@@ -477,6 +802,22 @@ __device__ void add_base_row(const VarOpsDev& o, int op, int i, int j, double c,
   auto put = [&](int ii, int jj, double v) {
     if (ii >= 0 && ii < o.d && jj >= 0 && jj < o.d) out[jj - pj + 3][ii - pi + 3] += c * v;
   };
+  if (o.gen) {
+    const size_t dd = (size_t)o.d * o.d, g = (size_t)j * o.d + i;
+    const double* f = o.gen + (op == 0 ? 0 : 9 * dd);
+    put(i, j, f[g]);
+    put(i + 1, j, f[dd + g]);
+    put(i - 1, j, f[2 * dd + g]);
+    put(i, j + 1, f[3 * dd + g]);
+    put(i, j - 1, f[4 * dd + g]);
+    if (op == 0) {
+      put(i + 1, j + 1, f[5 * dd + g]);
+      put(i - 1, j + 1, f[6 * dd + g]);
+      put(i + 1, j - 1, f[7 * dd + g]);
+      put(i - 1, j - 1, f[8 * dd + g]);
+    }
+    return;
+  }
   const double psi = o.psi[i];
   if (op == 0) {
     const double gx = o.kx * (o.av + (double)(j + 1) * o.dv);
@@ -606,12 +947,12 @@ struct VarPlan {
 };
 
 std::mutex g_plan_mu;
-std::map<std::tuple<int, int, int, bool>, VarPlan> g_plans;
+std::map<std::tuple<int, int, int, bool, bool>, VarPlan> g_plans;
 
-template <typename T, bool EULER>
+template <typename T, bool EULER, bool GEN>
 msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
   const int d = ctx->d;
-  const auto key = std::make_tuple(ctx->device, d, (int)sizeof(T), EULER);
+  const auto key = std::make_tuple(ctx->device, d, (int)sizeof(T), EULER, GEN);
   {
     std::lock_guard<std::mutex> lock(g_plan_mu);
     auto it = g_plans.find(key);
@@ -620,7 +961,7 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
       return MSK_OK;
     }
   }
-  auto kern = var_engine_kernel<T, EULER>;
+  auto kern = GEN ? gen_engine_kernel<T, EULER> : var_engine_kernel<T, EULER>;
   msk_status st = msk_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                      (int)kVarSmemCap), "smem attribute");
   if (st != MSK_OK) return st;
@@ -637,7 +978,7 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
     const int ng = std::max(1, std::min(kVarMaxThreads / d, RS / 2));
     const int R = (RS + ng - 1) / ng;
     const int NT = 32 * ((ng * d + 31) / 32);
-    const size_t smem = (size_t)var_layout(RS, d, NT).total * sizeof(T);
+    const size_t smem = (size_t)(GEN ? gen_layout(RS, d, NT).total : var_layout(RS, d, NT).total) * sizeof(T);
     if (smem > kVarSmemCap) continue;
     int clusters = 0;
     if (C == 1) {
@@ -689,10 +1030,10 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
                   "grid size / precision does not fit the variable-coefficient engine (cluster of <= 16 CTAs)");
 }
 
-template <typename T, bool EULER>
+template <typename T, bool EULER, bool GEN>
 msk_status launch_var_typed(msk_ctx* ctx, VarArgs a, int64_t paths, cudaStream_t stream) {
   VarPlan pl;
-  msk_status st = plan_var<T, EULER>(ctx, &pl);
+  msk_status st = plan_var<T, EULER, GEN>(ctx, &pl);
   if (st != MSK_OK) return st;
   a.C = pl.C;
   a.RS = pl.RS;
@@ -713,7 +1054,8 @@ msk_status launch_var_typed(msk_ctx* ctx, VarArgs a, int64_t paths, cudaStream_t
     cfg.attrs = attr;
     cfg.numAttrs = 1;
   }
-  return msk_cuda(ctx, cudaLaunchKernelEx(&cfg, var_engine_kernel<T, EULER>, a), "variable-coefficient engine");
+  return msk_cuda(ctx, cudaLaunchKernelEx(&cfg, GEN ? gen_engine_kernel<T, EULER> : var_engine_kernel<T, EULER>, a),
+                  "variable-coefficient engine");
 }
 
 }  // namespace
@@ -724,7 +1066,7 @@ msk_status launch_psi_rational(msk_ctx* ctx, double c, cudaStream_t stream) {
 }
 
 msk_status ensure_var_tables(msk_ctx* ctx, cudaStream_t stream) {
-  if (!ctx->xprof || !ctx->var_dirty) return MSK_OK;
+  if ((!ctx->xprof && !ctx->gen) || !ctx->var_dirty) return MSK_OK;
   constexpr int NB = kVarNormBlocks;
   if (!ctx->var_tab) {
     msk_status st = msk_cuda(ctx, cudaMalloc(&ctx->var_tab, (2 * kVarOps + 2 * kVarOps * NB) * sizeof(double)),
@@ -738,6 +1080,7 @@ msk_status ensure_var_tables(msk_ctx* ctx, cudaStream_t stream) {
   o.dv = ctx->dv;
   o.alpha = 0.5 * ctx->coef.a0;
   o.psi = ctx->psi;
+  o.gen = ctx->gen ? ctx->gen64 : nullptr;
   double* tr_part = ctx->var_tab + 2 * kVarOps;
   double* nu_part = tr_part + kVarOps * NB;
   var_trace_kernel<<<dim3(kVarOps, NB), 256, 0, stream>>>(o, tr_part);
@@ -752,7 +1095,7 @@ msk_status launch_engine_var(msk_ctx* ctx, bool euler, int steps, int64_t paths,
                              const double* Wt, const double* dW, void* out, uint32_t* status,
                              cudaStream_t stream, const EngineSnap& x) {
   if (paths == 0) return MSK_OK;
-  if (!euler && ctx->coef.kind != MSK_COEF_CONST)
+  if (!euler && !ctx->gen && ctx->coef.kind != MSK_COEF_CONST)
     return msk_fail(ctx, MSK_ERR_UNSUPPORTED,
                     "Magnus with an x profile needs constant coefficients (time-dependent ones are built for "
                     "the constant-coefficient operators only)");
@@ -781,11 +1124,21 @@ msk_status launch_engine_var(msk_ctx* ctx, bool euler, int steps, int64_t paths,
   a.tol32 = 0x1p-20f;   // float Taylor tolerance (see gen_theta.py)
   a.tol64 = 0x1p-53;
   a.c = coef_dev(ctx->coef);
+  if (ctx->gen) {
+    const size_t dd = (size_t)ctx->d * ctx->d;
+    a.gB = precision == MSK_F32 ? (const void*)ctx->gen32 : (const void*)ctx->gen64;
+    a.gA = precision == MSK_F32 ? (const void*)(ctx->gen32 + 9 * dd) : (const void*)(ctx->gen64 + 9 * dd);
+    if (precision == MSK_F32)
+      return euler ? launch_var_typed<float, true, true>(ctx, a, paths, stream)
+                   : launch_var_typed<float, false, true>(ctx, a, paths, stream);
+    return euler ? launch_var_typed<double, true, true>(ctx, a, paths, stream)
+                 : launch_var_typed<double, false, true>(ctx, a, paths, stream);
+  }
   if (precision == MSK_F32)
-    return euler ? launch_var_typed<float, true>(ctx, a, paths, stream)
-                 : launch_var_typed<float, false>(ctx, a, paths, stream);
-  return euler ? launch_var_typed<double, true>(ctx, a, paths, stream)
-               : launch_var_typed<double, false>(ctx, a, paths, stream);
+    return euler ? launch_var_typed<float, true, false>(ctx, a, paths, stream)
+                 : launch_var_typed<float, false, false>(ctx, a, paths, stream);
+  return euler ? launch_var_typed<double, true, false>(ctx, a, paths, stream)
+               : launch_var_typed<double, false, false>(ctx, a, paths, stream);
 }
 
 extern "C" msk_status msk_set_x_profile(msk_ctx* ctx, int kind, double c, const double* psi_host) {
@@ -820,6 +1173,41 @@ extern "C" msk_status msk_set_x_profile(msk_ctx* ctx, int kind, double c, const 
   if (st == MSK_OK) st = msk_cuda(ctx, cudaStreamSynchronize(0), "profile sync");
   if (st != MSK_OK) return st;
   ctx->xprof = kind;
+  ctx->gen = 0;
+  ctx->var_dirty = true;
+  return MSK_OK;
+}
+
+extern "C" msk_status msk_set_general_coefficients(msk_ctx* ctx, const double* coef_host) {
+  if (!ctx) return MSK_ERR_ARG;
+  msk_status st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
+  if (st != MSK_OK) return st;
+  if (!coef_host) {
+    ctx->gen = 0;
+    ctx->var_dirty = true;
+    return MSK_OK;
+  }
+  const size_t dd = (size_t)ctx->d * ctx->d;
+  for (size_t e = 0; e < 9 * dd; ++e)
+    if (!isfinite(coef_host[e])) return msk_fail(ctx, MSK_ERR_NONFINITE, "non-finite coefficient value");
+  if (!ctx->gen64) {
+    st = msk_cuda(ctx, cudaMalloc(&ctx->gen64, 14 * dd * sizeof(double)), "stencil field allocation");
+    if (st == MSK_OK) st = msk_cuda(ctx, cudaMalloc(&ctx->gen32, 14 * dd * sizeof(float)), "stencil field allocation");
+    if (st != MSK_OK) return st;
+  }
+  double* tmp = nullptr;
+  st = msk_cuda(ctx, cudaMalloc(&tmp, 9 * dd * sizeof(double)), "coefficient upload");
+  if (st != MSK_OK) return st;
+  st = msk_cuda(ctx, cudaMemcpy(tmp, coef_host, 9 * dd * sizeof(double), cudaMemcpyHostToDevice), "copy coefficients");
+  if (st == MSK_OK) {
+    gen_stencil_kernel<<<(unsigned)((dd + 255) / 256), 256>>>(ctx->d, ctx->dx, ctx->dv, tmp, ctx->gen64, ctx->gen32);
+    st = msk_cuda(ctx, cudaGetLastError(), "stencil fields");
+  }
+  if (st == MSK_OK) st = msk_cuda(ctx, cudaDeviceSynchronize(), "stencil fields");
+  cudaFree(tmp);
+  if (st != MSK_OK) return st;
+  ctx->gen = 1;
+  ctx->xprof = 0;
   ctx->var_dirty = true;
   return MSK_OK;
 }

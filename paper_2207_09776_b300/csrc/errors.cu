@@ -206,7 +206,7 @@ extern "C" msk_status msk_explicit_solution(msk_ctx* ctx, int64_t paths, double*
   if (paths < 0) return msk_fail(ctx, MSK_ERR_ARG, "paths < 0");
   if (paths == 0) return MSK_OK;
   if (!u_out_dev) return msk_fail(ctx, MSK_ERR_ARG, "null buffer");
-  if (ctx->xprof) return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "no closed form with an x profile");
+  if (ctx->xprof || ctx->gen) return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "no closed form with variable coefficients");
   cudaStream_t s = (cudaStream_t)stream;
   msk_status st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
   if (st != MSK_OK) return st;
@@ -232,8 +232,8 @@ extern "C" msk_status msk_error(msk_ctx* ctx, const void* u_dev, int u_precision
   if (paths == 0) return MSK_OK;
   if (!u_dev || !err_per_path_dev || (ref_kind == MSK_REF_BUFFER && !ref_dev))
     return msk_fail(ctx, MSK_ERR_ARG, "null buffer");
-  if (ref_kind == MSK_REF_EXPLICIT && ctx->xprof)
-    return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "no closed form with an x profile");
+  if (ref_kind == MSK_REF_EXPLICIT && (ctx->xprof || ctx->gen))
+    return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "no closed form with variable coefficients");
   cudaStream_t s = (cudaStream_t)stream;
   msk_status st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
   if (st != MSK_OK) return st;

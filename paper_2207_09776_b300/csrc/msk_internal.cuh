@@ -40,7 +40,11 @@ struct msk_ctx {
   int xprof = 0;              // MSK_XPROF_*; 0: constant-coefficient operators
   double* psi = nullptr;      // [d] psi(x_i), device
   double* var_tab = nullptr;  // 6 traces, 6 shifted norms of the variable-coefficient operators; partials
-  bool var_dirty = true;      // var_tab must be rebuilt (profile, a0 or drift changed)
+  bool var_dirty = true;      // var_tab must be rebuilt (profile, a0, drift or general coefficients changed)
+  // general coefficients of Eq. generalSPDE (msk_set_general_coefficients)
+  int gen = 0;
+  double* gen64 = nullptr;    // [14][d][d] stencil fields: B (9), A (5)
+  float* gen32 = nullptr;
   std::string err;
 };
 

@@ -187,6 +187,19 @@ __global__ void omega_kernel(OmegaArgs a, const double* __restrict__ F, double* 
 
 bool g_theta_loaded[64] = {false};
 
+// Coefficient profile of the weights: with general coefficients A already holds
+// sigma and the coefficients are time-independent, so the weights are those of
+// constant coefficients with sigma = 1.
+CoefDev omega_coef(const msk_ctx* ctx) {
+  CoefDev c = coef_dev(ctx->coef);
+  if (ctx->gen) {
+    c.kind = MSK_COEF_CONST;
+    c.a0 = c.a1 = c.s1 = 0.0;
+    c.s0 = 1.0;
+  }
+  return c;
+}
+
 }  // namespace
 
 // Taylor scaling cap: beyond it the path is flagged MSK_PATH_SCALE_CAP.
@@ -211,12 +224,12 @@ msk_status launch_omega(msk_ctx* ctx, int order, int steps, int64_t paths, int p
   if (st0 != MSK_OK) return st0;
   const int64_t n = paths * steps;
   if (n == 0) return MSK_OK;
-  if (ctx->xprof) {
+  if (ctx->xprof || ctx->gen) {
     st0 = ensure_var_tables(ctx, stream);
     if (st0 != MSK_OK) return st0;
   }
-  OmegaArgs a{ctx->band, ctx->aux, ctx->xprof ? ctx->var_tab : nullptr, nullptr, ctx->d, order, steps, precision,
-              paths, ctx->T, ctx->dx, coef_dev(ctx->coef), kMskScaleCap};
+  OmegaArgs a{ctx->band, ctx->aux, (ctx->xprof || ctx->gen) ? ctx->var_tab : nullptr, nullptr, ctx->d, order, steps,
+              precision, paths, ctx->T, ctx->dx, omega_coef(ctx), kMskScaleCap};
   omega_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(a, F, Wt);
   return msk_cuda(ctx, cudaGetLastError(), "omega kernel");
 }
@@ -228,12 +241,12 @@ msk_status launch_omega_jobs(msk_ctx* ctx, int order, int64_t njobs, int precisi
   msk_status st0 = msk_prepare_omega(ctx);
   if (st0 != MSK_OK) return st0;
   if (njobs == 0) return MSK_OK;
-  if (ctx->xprof) {
+  if (ctx->xprof || ctx->gen) {
     st0 = ensure_var_tables(ctx, stream);
     if (st0 != MSK_OK) return st0;
   }
-  OmegaArgs a{ctx->band, ctx->aux, ctx->xprof ? ctx->var_tab : nullptr, job_th_dev, ctx->d, order, 1, precision,
-              njobs, ctx->T, ctx->dx, coef_dev(ctx->coef), kMskScaleCap};
+  OmegaArgs a{ctx->band, ctx->aux, (ctx->xprof || ctx->gen) ? ctx->var_tab : nullptr, job_th_dev, ctx->d, order, 1,
+              precision, njobs, ctx->T, ctx->dx, omega_coef(ctx), kMskScaleCap};
   omega_kernel<<<(unsigned)((njobs + 127) / 128), 128, 0, stream>>>(a, F, Wt);
   return msk_cuda(ctx, cudaGetLastError(), "omega kernel (intervals)");
 }

@@ -233,7 +233,8 @@ extern "C" msk_status msk_apply_omega(msk_ctx* ctx, const double* weights_dev, i
   if (paths < 0) return msk_fail(ctx, MSK_ERR_ARG, "paths < 0");
   if (paths == 0) return MSK_OK;
   if (!weights_dev || !u_dev || !out_dev) return msk_fail(ctx, MSK_ERR_ARG, "null buffer");
-  if (ctx->xprof) return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "the widened-stencil tables hold no x profile");
+  if (ctx->xprof || ctx->gen)
+    return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "the widened-stencil tables hold only the Langevin coefficients");
   msk_status st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
   if (st != MSK_OK) return st;
   const int64_t n = paths * (int64_t)ctx->d * ctx->d;
