@@ -1114,6 +1114,30 @@ def run_paper_var(a):
             e1.record(stream)
             torch.cuda.synchronize()
             extra[nm] = {"paths_per_s": P / (e0.elapsed_time(e1) / 1e3)}
+        if d == 100:
+            # the same problem through the general-coefficient path (nine-point B, five-point
+            # A with per-point coefficients): the cost of generality, and agreement
+            import numpy as np
+            xs = w.ax + (w.bx - w.ax) / (d + 1) * np.arange(1, d + 1)
+            X, V = np.meshgrid(xs, xs, indexing="xy")
+            psi = 1.0 + w.x_profile_c / (1.0 + X * X)
+            z = np.zeros_like(X)
+            coef = np.stack([z, w.drift_sign * V, z, z, z, w.a0 * psi, z, z, w.s0 * np.sqrt(psi)])
+            msk.msk_solve_magnus(s.ctx, ORDER, K, P, msk.MSK_F32, out, st, stream)   # variable engine
+            ref_var = out.clone()
+            msk.msk_set_general_coefficients(s.ctx, coef)
+            msk.msk_solve_magnus(s.ctx, ORDER, K, P, msk.MSK_F32, out, st, stream)   # warm
+            flush.fill_(1)
+            e0, e1 = _events(torch, stream)
+            e0.record(stream)
+            msk.msk_solve_magnus(s.ctx, ORDER, K, P, msk.MSK_F32, out, st, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            diff = float(((out - ref_var).norm() / ref_var.norm()).cpu())
+            extra["general_coefficients_engine"] = {"paths_per_s": P / (e0.elapsed_time(e1) / 1e3),
+                                                    "rel_l2_vs_variable_engine": diff}
+            msk.msk_set_general_coefficients(s.ctx, None)
+            msk.msk_set_x_profile(s.ctx, w.x_profile, w.x_profile_c)
         # end to end: the same float solve with the solution read back to pinned host memory
         host = torch.empty(P * d * d, dtype=torch.float32, pin_memory=True)
         torch.cuda.synchronize()
