@@ -39,7 +39,9 @@ struct BrownArgs {
   int steps;
   double T;
   CoefDev c;
-  const double* tab;   // TRIG: [3][n_fine + 1]: sigma(mid), alpha(node), A(mid); null for CONST
+  // TRIG: [3][n_fine + 1] doubles sigma(mid), alpha(node), A(mid), then [2][n_fine + 1]
+  // floats sigma(mid), alpha(node); null for CONST
+  const double* tab;
   // Interval mode (steps = 1, paths = number of intervals): interval i covers the
   // fine cells jobs[3i+1] .. jobs[3i+1] + jobs[3i+2] - 1 of local path jobs[3i].
   const int64_t* jobs;
@@ -55,9 +57,13 @@ __global__ void cell_table_kernel(CoefDev c, int64_t n_fine, double T, double* t
   if (k > n_fine) return;
   const double delta = T / (double)n_fine;
   const double tk = delta * (double)k, tm = delta * ((double)k + 0.5);
-  tab[k] = c.s0 * (1.0 + c.s1 * cospi(2.0 * tm));                              // sigma at cell midpoint
-  tab[(n_fine + 1) + k] = 0.5 * (c.a0 + c.a1 * sinpi(2.0 * tk));                  // alpha at node
-  tab[2 * (n_fine + 1) + k] = alpha_anti(c, tm);                                  // A at cell midpoint
+  const double sig = c.s0 * (1.0 + c.s1 * cospi(2.0 * tm)), alp = 0.5 * (c.a0 + c.a1 * sinpi(2.0 * tk));
+  tab[k] = sig;                                                                    // sigma at cell midpoint
+  tab[(n_fine + 1) + k] = alp;                                                     // alpha at node
+  tab[2 * (n_fine + 1) + k] = alpha_anti(c, tm);                                   // A at cell midpoint
+  float* tf = reinterpret_cast<float*>(tab + 3 * (n_fine + 1));                   // float copies
+  tf[k] = (float)sig;
+  tf[(n_fine + 1) + k] = (float)alp;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -107,21 +113,39 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
   //   sum (k + 1/2) sdw = sum k sdw + sum sdw / 2,   sum (om0 + om1) = 2 sum om0 + sum sdw.
   double Sw0 = 0.0, S2 = 0.0, Skw = 0.0, So0 = 0.0, Sks = 0.0, J3 = 0.0, J4 = 0.0;
   double swT = 0.0, soT = 0.0;                              // sum dw, sum sigma dW of the lane's cells
+  const float* tsig_f = TRIG ? reinterpret_cast<const float*>(a.tab + 3 * (a.n_fine + 1)) : nullptr;
+  const float* talp_f = TRIG ? tsig_f + (a.n_fine + 1) : nullptr;
+  float* stf = reinterpret_cast<float*>(st);
   for (int64_t rb = 0; rb < L; rb += kRound) {
     // ---- pass 1: normals of this lane's chunk, chunk sums -------------------------
     const int64_t c0 = rb + (int64_t)lane * kChunk;
     const int cnt = (int)max((int64_t)0, min((int64_t)kChunk, L - c0));
-    double sw = 0.0, so = 0.0, z0 = 0.0, z1 = 0.0;
-    for (int q = 0; q < cnt; ++q) {
-      const int64_t fi = f0 + c0 + q;
-      if (q == 0 || (fi & 1) == 0) {
-        if (NF32) brownian_pair_f32(a.seed, gpath, 0u, (uint64_t)(fi >> 1), z0, z1);
-        else brownian_pair(a.seed, gpath, 0u, (uint64_t)(fi >> 1), z0, z1);
+    double sw = 0.0, so = 0.0;
+    if constexpr (NF32) {
+      // float solves: float normals and float sums within the chunk (at most 64 cells,
+      // values relative to the chunk start), folded into the double lane sums per chunk
+      const float sqf = (float)sq;
+      float swf = 0.0f, sof = 0.0f, z0 = 0.0f, z1 = 0.0f;
+      for (int q = 0; q < cnt; ++q) {
+        const int64_t fi = f0 + c0 + q;
+        if (q == 0 || (fi & 1) == 0) brownian_pair_f32f(a.seed, gpath, 0u, (uint64_t)(fi >> 1), z0, z1);
+        const float dw = sqf * ((fi & 1) ? z1 : z0);
+        stf[q * 32 + lane] = dw;
+        swf += dw;
+        if (FULL) sof = fmaf(TRIG ? tsig_f[fi] : (float)sg0, dw, sof);
       }
-      const double dw = sq * ((fi & 1) ? z1 : z0);
-      st[q * 32 + lane] = dw;
-      sw += dw;
-      if (FULL) so += (TRIG ? tsig[fi] : sg0) * dw;
+      sw = (double)swf;
+      so = (double)sof;
+    } else {
+      double z0 = 0.0, z1 = 0.0;
+      for (int q = 0; q < cnt; ++q) {
+        const int64_t fi = f0 + c0 + q;
+        if (q == 0 || (fi & 1) == 0) brownian_pair(a.seed, gpath, 0u, (uint64_t)(fi >> 1), z0, z1);
+        const double dw = sq * ((fi & 1) ? z1 : z0);
+        st[q * 32 + lane] = dw;
+        sw += dw;
+        if (FULL) so += (TRIG ? tsig[fi] : sg0) * dw;
+      }
     }
     const double woff = W0 + warp_excl_scan(sw, lane);
     const double ooff = O0 + warp_excl_scan(so, lane);
@@ -133,28 +157,65 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
     // ---- pass 2: functionals over the staged increments -------------------------
     // Sums are kept without their constant factors (delta/2, delta/3, delta^2/6,
     // delta), applied once at the end; k is carried as a double counter.
-    double w0 = woff, om0 = ooff;
-    double kd = (double)c0;
-    for (int q = 0; q < cnt; ++q) {
-      const int64_t fi = f0 + c0 + q;
-      const double dw = st[q * 32 + lane];
-      const double w1 = w0 + dw;
-      const double ws = w0 + w1;
-      Sw0 += w0;
-      S2 = fma(w0, ws, fma(w1, w1, S2));                     // delta/3 sum (w0^2 + w0 w1 + w1^2)
-      Skw = fma(kd, ws, Skw);                                // sum k (w0 + w1)
-      const double sig = TRIG ? tsig[fi] : sg0;
-      const double sdw = sig * dw;
-      const double om1 = om0 + sdw;
-      So0 += om0;
-      Sks = fma(kd, sdw, Sks);                               // sum k sigma dW
-      if (TRIG) {
-        J3 = fma(talp[fi], om0, fma(talp[fi + 1], om1, J3)); // delta/2 sum (alpha0 om0 + alpha1 om1)
-        J4 = fma(tA[fi] - Astart, sdw, J4);                  // sum alpha_bar(s_mid) sigma dW
+    if constexpr (NF32) {
+      // w = woff + x, om = ooff + y with x, y the float running sums inside the chunk;
+      // k = c0 + kl.  Chunk sums A = sum x0, B = sum (x0^2 + x0 x1 + x1^2), Ck = sum kl (x0 + x1),
+      // E = sum y0, Fk = sum kl sdw, H = sum (alpha0 + alpha1), I = sum (alpha0 y0 + alpha1 y1).
+      float x0 = 0.0f, y0 = 0.0f, kl = 0.0f;
+      float A = 0.0f, Bq = 0.0f, Ck = 0.0f, E = 0.0f, Fk = 0.0f, H = 0.0f, I = 0.0f;
+      for (int q = 0; q < cnt; ++q) {
+        const int64_t fi = f0 + c0 + q;
+        const float dw = stf[q * 32 + lane];
+        const float x1 = x0 + dw, xs = x0 + x1;
+        A += x0;
+        Bq = fmaf(x0, xs, fmaf(x1, x1, Bq));
+        Ck = fmaf(kl, xs, Ck);
+        const float sdw = (TRIG ? tsig_f[fi] : (float)sg0) * dw;
+        const float y1 = y0 + sdw;
+        E += y0;
+        Fk = fmaf(kl, sdw, Fk);
+        if (TRIG) {
+          const float al0 = talp_f[fi], al1 = talp_f[fi + 1];
+          H += al0 + al1;
+          I = fmaf(al0, y0, fmaf(al1, y1, I));
+          J4 = fma(tA[fi] - Astart, (double)sdw, J4);     // sum alpha_bar(s_mid) sigma dW
+        }
+        x0 = x1;
+        y0 = y1;
+        kl += 1.0f;
       }
-      w0 = w1;
-      om0 = om1;
-      kd += 1.0;
+      const double n = (double)cnt, kc = (double)c0, xe = (double)x0;
+      const double sx = 2.0 * (double)A + xe;             // sum (x0 + x1)
+      Sw0 += n * woff + (double)A;
+      S2 += 3.0 * n * woff * woff + 3.0 * woff * sx + (double)Bq;
+      Skw += kc * (2.0 * n * woff + sx) + 2.0 * woff * (0.5 * n * (n - 1.0)) + (double)Ck;
+      So0 += n * ooff + (double)E;
+      Sks += kc * (double)y0 + (double)Fk;
+      if (TRIG) J3 += ooff * (double)H + (double)I;
+    } else {
+      double w0 = woff, om0 = ooff;
+      double kd = (double)c0;
+      for (int q = 0; q < cnt; ++q) {
+        const int64_t fi = f0 + c0 + q;
+        const double dw = st[q * 32 + lane];
+        const double w1 = w0 + dw;
+        const double ws = w0 + w1;
+        Sw0 += w0;
+        S2 = fma(w0, ws, fma(w1, w1, S2));                     // delta/3 sum (w0^2 + w0 w1 + w1^2)
+        Skw = fma(kd, ws, Skw);                                // sum k (w0 + w1)
+        const double sig = TRIG ? tsig[fi] : sg0;
+        const double sdw = sig * dw;
+        const double om1 = om0 + sdw;
+        So0 += om0;
+        Sks = fma(kd, sdw, Sks);                               // sum k sigma dW
+        if (TRIG) {
+          J3 = fma(talp[fi], om0, fma(talp[fi + 1], om1, J3)); // delta/2 sum (alpha0 om0 + alpha1 om1)
+          J4 = fma(tA[fi] - Astart, sdw, J4);                  // sum alpha_bar(s_mid) sigma dW
+        }
+        w0 = w1;
+        om0 = om1;
+        kd += 1.0;
+      }
     }
     __syncwarp();   // the stage buffer is rewritten by the next round
   }
@@ -202,7 +263,7 @@ static msk_status ensure_cell_table(msk_ctx* ctx, cudaStream_t stream) {
     ctx->tab = nullptr;
   }
   if (!ctx->tab) {
-    msk_status st = msk_cuda(ctx, cudaMalloc(&ctx->tab, 3 * (size_t)(ctx->n_fine + 1) * sizeof(double)),
+    msk_status st = msk_cuda(ctx, cudaMalloc(&ctx->tab, 4 * (size_t)(ctx->n_fine + 1) * sizeof(double)),
                              "cell table allocation");
     if (st != MSK_OK) return st;
   }
@@ -281,7 +342,7 @@ msk_status launch_brownian_strided(msk_ctx* ctx, int steps, int64_t paths, doubl
 }
 
 // Variants for callers that supply the per-cell table buffer themselves
-// (3 * (n_fine + 1) doubles); used by the entry point that allocates nothing.
+// (4 * (n_fine + 1) doubles); used by the entry point that allocates nothing.
 msk_status launch_cell_table_into(msk_ctx* ctx, double* tab, cudaStream_t stream) {
   const int64_t n = ctx->n_fine + 1;
   cell_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(coef_dev(ctx->coef), ctx->n_fine, ctx->T, tab);

@@ -58,11 +58,11 @@ __device__ __forceinline__ void brownian_pair(uint64_t seed, uint64_t path, uint
 
 // The same pair with the normals formed in single precision: uniforms
 // (hi + 1/2) 2^-32 from the high word of each half of the counter block
-// (within 2^-32 of the double-precision uniforms), Box-Muller in float,
-// returned as double.  Used by the float solves, where the double-precision
-// Box-Muller would dominate the cost of the Brownian kernel.
-__device__ __forceinline__ void brownian_pair_f32(uint64_t seed, uint64_t path, uint32_t tag, uint64_t j,
-                                                  double& z0, double& z1) {
+// (within 2^-32 of the double-precision uniforms), Box-Muller in float
+// (returned as float, or widened to double).  Used by the float solves, where
+// the double-precision Box-Muller would dominate the cost of the Brownian kernel.
+__device__ __forceinline__ void brownian_pair_f32f(uint64_t seed, uint64_t path, uint32_t tag, uint64_t j,
+                                                   float& z0, float& z1) {
   const uint4 w = philox4x32_10(
       make_uint4((uint32_t)j, (uint32_t)path, (uint32_t)(path >> 32), tag),
       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
@@ -71,6 +71,13 @@ __device__ __forceinline__ void brownian_pair_f32(uint64_t seed, uint64_t path, 
   const float r = sqrtf(-2.0f * logf(u1));
   float s, c;
   sincospif(2.0f * u2, &s, &c);
-  z0 = (double)(r * c);
-  z1 = (double)(r * s);
+  z0 = r * c;
+  z1 = r * s;
+}
+__device__ __forceinline__ void brownian_pair_f32(uint64_t seed, uint64_t path, uint32_t tag, uint64_t j,
+                                                  double& z0, double& z1) {
+  float a, b;
+  brownian_pair_f32f(seed, path, tag, j, a, b);
+  z0 = (double)a;
+  z1 = (double)b;
 }
