@@ -66,6 +66,9 @@ def test_argument_validation_needs_no_device(lib):
     assert lib.msk_last_error(None) == b"null context"
     assert lib.msk_brownian_functionals_ex(None, 1, 1, 0, None, None) == msk.MSK_ERR_ARG
     assert lib.msk_select_steps(None, 1e-3, 1, 8, 1, 0, None, None, None, None) == msk.MSK_ERR_ARG
+    assert lib.msk_set_general_coefficients(None, None) == msk.MSK_ERR_ARG
+    cells = (ctypes.c_int64 * 2)(10, 20)
+    assert lib.msk_solve_magnus_times(None, 3, 4, 1, 0, cells, 2, None, None, None) == msk.MSK_ERR_ARG
     # surrogate: NULL handles and missing arguments are rejected before any device work
     cfg = msk.msk_surrogate_config(16, 64, 512, 4, 4096, 65536, 3, 8, 0)
     assert lib.msk_surrogate_create(ctypes.byref(h), None, ctypes.byref(cfg)) == msk.MSK_ERR_ARG
