@@ -138,6 +138,70 @@ __device__ __forceinline__ double var_alpha_t(const CoefDev& c, double t) {
   return 0.5 * (c.a0 + c.a1 * sinpi(2.0 * t));
 }
 
+// Norm reduction shared by the engines of this file: every warp publishes its
+// maxima in shared memory; with clusters warp 0 of each CTA folds them into one
+// CTA slot and every warp reads the C slots (shared::cluster loads) after the
+// cluster barrier, so all threads of a cluster take identical decisions.  Two
+// slot sets (par = 0, 1) alternate so that a publish never overwrites slots that
+// another warp may still be gathering.
+template <typename T>
+struct NormSlots {
+  T* slots;    // [2][NW][2]
+  T* cslot;    // [2][2]
+  int NW, C, lane, warp;
+  __device__ __forceinline__ void publish(int par, T mn, T ma) const {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = vmax(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      ma = vmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+    }
+    if (lane == 0) {
+      slots[(par * NW + warp) * 2 + 0] = mn;
+      slots[(par * NW + warp) * 2 + 1] = ma;
+    }
+    if (C > 1) {
+      __syncthreads();
+      if (warp == 0) {
+        T x = T(0), y = T(0);
+        for (int q = lane; q < NW; q += 32) {
+          x = vmax(x, slots[(par * NW + q) * 2 + 0]);
+          y = vmax(y, slots[(par * NW + q) * 2 + 1]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          x = vmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+          y = vmax(y, __shfl_xor_sync(0xffffffffu, y, o));
+        }
+        if (lane == 0) {
+          cslot[par * 2 + 0] = x;
+          cslot[par * 2 + 1] = y;
+        }
+      }
+    }
+  }
+  __device__ __forceinline__ void gather(int par, T& gn, T& ga) const {
+    gn = T(0);
+    ga = T(0);
+    if (C > 1) {
+      if (lane < C) {
+        const uint32_t q = cl_addr(cslot + par * 2, lane);
+        gn = cl_ld(q, T(0));
+        ga = cl_ld(q + (uint32_t)sizeof(T), T(0));
+      }
+    } else {
+      for (int q = lane; q < NW; q += 32) {
+        gn = vmax(gn, slots[(par * NW + q) * 2 + 0]);
+        ga = vmax(ga, slots[(par * NW + q) * 2 + 1]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      gn = vmax(gn, __shfl_xor_sync(0xffffffffu, gn, o));
+      ga = vmax(ga, __shfl_xor_sync(0xffffffffu, ga, o));
+    }
+  }
+};
+
 template <typename T, bool EULER>
 __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const VarArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -207,59 +271,9 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
     }
   };
 
-  // Norms: per-warp maxima in shared memory; with clusters warp 0 folds them
-  // into one CTA slot and every warp reads the C slots after the barrier.
-  auto publish = [&](int par, T mn, T ma) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      mn = vmax(mn, __shfl_xor_sync(0xffffffffu, mn, off));
-      ma = vmax(ma, __shfl_xor_sync(0xffffffffu, ma, off));
-    }
-    if (lane == 0) {
-      slots[(par * NW + warp) * 2 + 0] = mn;
-      slots[(par * NW + warp) * 2 + 1] = ma;
-    }
-    if (C > 1) {
-      __syncthreads();
-      if (warp == 0) {
-        T x = T(0), y = T(0);
-        for (int q = lane; q < NW; q += 32) {
-          x = vmax(x, slots[(par * NW + q) * 2 + 0]);
-          y = vmax(y, slots[(par * NW + q) * 2 + 1]);
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          x = vmax(x, __shfl_xor_sync(0xffffffffu, x, off));
-          y = vmax(y, __shfl_xor_sync(0xffffffffu, y, off));
-        }
-        if (lane == 0) {
-          cslot[par * 2 + 0] = x;
-          cslot[par * 2 + 1] = y;
-        }
-      }
-    }
-  };
-  auto gather = [&](int par, T& gn, T& ga) {
-    gn = T(0);
-    ga = T(0);
-    if (C > 1) {
-      if (lane < C) {
-        const uint32_t q = cl_addr(cslot + par * 2, lane);
-        gn = cl_ld(q, T(0));
-        ga = cl_ld(q + (uint32_t)sizeof(T), T(0));
-      }
-    } else {
-      for (int q = lane; q < NW; q += 32) {
-        gn = vmax(gn, slots[(par * NW + q) * 2 + 0]);
-        ga = vmax(ga, slots[(par * NW + q) * 2 + 1]);
-      }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      gn = vmax(gn, __shfl_xor_sync(0xffffffffu, gn, off));
-      ga = vmax(ga, __shfl_xor_sync(0xffffffffu, ga, off));
-    }
-  };
+  const NormSlots<T> norms{slots, cslot, NW, C, lane, warp};
+  auto publish = [&](int par, T mn, T ma) { norms.publish(par, mn, ma); };
+  auto gather = [&](int par, T& gn, T& ga) { norms.gather(par, gn, ga); };
   // row mask: 1 for rows of the grid, 0 for the halo rows beyond its boundary
   auto rowm = [&](int p) -> T { return (r0 + p >= 0 && r0 + p < d) ? T(1) : T(0); };
 
@@ -549,57 +563,9 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
     return fma(__ldg(gA + 4 * dd + g), F[o - W], v);
   };
 
-  auto publish = [&](int par, T mn, T ma) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      mn = vmax(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      ma = vmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
-    }
-    if (lane == 0) {
-      slots[(par * NW + warp) * 2 + 0] = mn;
-      slots[(par * NW + warp) * 2 + 1] = ma;
-    }
-    if (C > 1) {
-      __syncthreads();
-      if (warp == 0) {
-        T x = T(0), y = T(0);
-        for (int q = lane; q < NW; q += 32) {
-          x = vmax(x, slots[(par * NW + q) * 2 + 0]);
-          y = vmax(y, slots[(par * NW + q) * 2 + 1]);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          x = vmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-          y = vmax(y, __shfl_xor_sync(0xffffffffu, y, o));
-        }
-        if (lane == 0) {
-          cslot[par * 2 + 0] = x;
-          cslot[par * 2 + 1] = y;
-        }
-      }
-    }
-  };
-  auto gather = [&](int par, T& gn, T& ga) {
-    gn = T(0);
-    ga = T(0);
-    if (C > 1) {
-      if (lane < C) {
-        const uint32_t q = cl_addr(cslot + par * 2, lane);
-        gn = cl_ld(q, T(0));
-        ga = cl_ld(q + (uint32_t)sizeof(T), T(0));
-      }
-    } else {
-      for (int q = lane; q < NW; q += 32) {
-        gn = vmax(gn, slots[(par * NW + q) * 2 + 0]);
-        ga = vmax(ga, slots[(par * NW + q) * 2 + 1]);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      gn = vmax(gn, __shfl_xor_sync(0xffffffffu, gn, o));
-      ga = vmax(ga, __shfl_xor_sync(0xffffffffu, ga, o));
-    }
-  };
+  const NormSlots<T> norms{slots, cslot, NW, C, lane, warp};
+  auto publish = [&](int par, T mn, T ma) { norms.publish(par, mn, ma); };
+  auto gather = [&](int par, T& gn, T& ga) { norms.gather(par, gn, ga); };
 
   const T tol = sizeof(T) == 4 ? (T)a.tol32 : (T)a.tol64;
   const int64_t cid = blockIdx.x / C, ncl = gridDim.x / C;
