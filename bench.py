@@ -560,6 +560,14 @@ def run_ours(a):
         _, ms_t = timed(lambda: msk.msk_solve_magnus_times(ctx, ORDER, K, Pc, msk.MSK_F32, cells, ut, None,
                                                            stream))
         _, ms_p = timed(lambda: solver.magnus(ORDER, K, paths=Pc, precision=msk.MSK_F32))
+        # the same time-dependent workload with the paper's x profile psi = 1 + 1/(1 + x^2)
+        # (Eq. coeffsLangevinVar): the thirteen-operator composition engine
+        uvar = torch.empty(Pc * w.d * w.d, dtype=torch.float32, device=dev)
+        msk.msk_set_x_profile(ctx, msk.MSK_XPROF_RATIONAL, 1.0)
+        _, ms_v = timed(lambda: msk.msk_solve_magnus(ctx, ORDER, K, Pc, msk.MSK_F32, uvar, None, stream))
+        msk.msk_set_x_profile(ctx, msk.MSK_XPROF_NONE)
+        comparators["x_profile_time_dependent"] = {"paths": Pc, "K": K, "paths_per_s": Pc / (ms_v / 1e3),
+                                                   "engine": "thirteen-operator composition"}
         comparators["output_times"] = {
             "paths": Pc, "n_times": len(cells), "paths_per_s": Pc / (ms_t / 1e3),
             "solutions_per_s": Pc * len(cells) / (ms_t / 1e3), "ms": ms_t, "plain_solve_ms": ms_p,

@@ -136,10 +136,11 @@ msk_status msk_set_coefficients(msk_ctx* ctx, const msk_coeffs* coeffs);
  * msk_magnus_from_weights / msk_solve_euler / msk_select_steps run the
  * variable-coefficient engine, which applies Omega by composing the two base
  * operators B and A0 (exact truncated products) instead of folded stencils.
- * Magnus then needs constant coefficients (MSK_COEF_CONST; time-dependent
- * ones -> MSK_ERR_UNSUPPORTED; Euler accepts both), and msk_magnus_from_weights
- * reads only the weights of BX, A0, A0A0, BX_A0, BXA0_A0 and BXA0_BX, the others
- * being implied (B = Bx + a/2 Bvv).  msk_apply_omega, msk_explicit_solution,
+ * With constant coefficients the engine composes the six operators of
+ * Eq. MagnusFormulas (B = Bx + a/2 Bvv) and msk_magnus_from_weights reads only the
+ * weights of BX, A0, A0A0, BX_A0, BXA0_A0 and BXA0_BX, the others being implied;
+ * with time-dependent ones (MSK_COEF_TRIG) it composes all thirteen MSK_OP_*
+ * operators over Bx, Bvv and A0 and reads all thirteen weights.  msk_apply_omega, msk_explicit_solution,
  * msk_error with MSK_REF_EXPLICIT and batches -> MSK_ERR_UNSUPPORTED (no closed
  * form exists).  Invalid kind, c < 0, non-positive or non-finite values ->
  * MSK_ERR_ARG / MSK_ERR_NONFINITE before any device work. */

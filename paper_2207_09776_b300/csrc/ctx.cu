@@ -110,7 +110,7 @@ extern "C" msk_status msk_set_coefficients(msk_ctx* ctx, const msk_coeffs* c) {
   msk_status st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
   if (st != MSK_OK) return st;
   const bool rebuild = c->drift_sign != ctx->coef.drift_sign;
-  if (rebuild || c->a0 != ctx->coef.a0) ctx->var_dirty = true;
+  if (rebuild || c->a0 != ctx->coef.a0 || c->kind != ctx->coef.kind) ctx->var_dirty = true;
   ctx->coef = *c;
   if (rebuild) return launch_band_tables(ctx, 0);
   return MSK_OK;

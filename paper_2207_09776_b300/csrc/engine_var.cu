@@ -91,10 +91,10 @@ struct VarArgs {
 struct VarLayout {
   int FS, off_acc, off_cx, off_scale, off_slot, off_cslot, total;
 };
-__host__ __device__ inline VarLayout var_layout(int RS, int d, int NT) {
+__host__ __device__ inline VarLayout var_layout(int RS, int d, int NT, int nfields) {
   VarLayout L;
   L.FS = (RS + 4) * (d + 4);
-  L.off_acc = kVarFields * L.FS;
+  L.off_acc = nfields * L.FS;
   L.off_cx = L.off_acc + RS * d;
   L.off_scale = L.off_cx + RS + 4;
   L.off_slot = L.off_scale + kVarMaxTerms + 1;
@@ -202,15 +202,16 @@ struct NormSlots {
   }
 };
 
-template <typename T, bool EULER>
+template <typename T, bool EULER, bool SPLIT>
 __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const VarArgs a) {
+  constexpr int NF = SPLIT ? kVarFields + 1 : kVarFields;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, NT = blockDim.x, NW = NT >> 5;
   const int lane = tid & 31, warp = tid >> 5;
   const int C = a.C, RS = a.RS, d = a.d, W = d + 4;
   const int rank = C > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  const VarLayout L = var_layout(RS, d, NT);
+  const VarLayout L = var_layout(RS, d, NT, NF);
   const int FS = L.FS;
   T* accs = sm + L.off_acc;
   T* cxr = sm + L.off_cx + 2;   // cxr[p], p in [-2, RS + 1]
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
   const int nrows = act ? max(0, min(a.R, rs - p0)) : 0;
 
   // zero the fields once: grid-boundary halos and pad columns are never written again
-  for (int e = tid; e < kVarFields * FS; e += NT) sm[e] = T(0);
+  for (int e = tid; e < NF * FS; e += NT) sm[e] = T(0);
   for (int p = tid - 2; p < RS + 2; p += NT) {
     const int jg = r0 + p;
     const double v = a.av + (double)(jg + 1) * a.dv;
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
 
   const T tol = sizeof(T) == 4 ? (T)a.tol32 : (T)a.tol64;
   const int64_t cid = blockIdx.x / C, ncl = gridDim.x / C;
-  constexpr int FT = 0, FP = 1, FQ = 2;
+  constexpr int FT = 0, FP = 1, FQ = 2, FR = 3;
   int par = 0;
 
   for (int64_t path = cid; path < a.paths; path += ncl) {
@@ -341,6 +342,9 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
         const double* rec = a.Wt + ((size_t)path * a.steps + n) * MSK_NWT;
         const T wB = (T)rec[MSK_OP_BX], wA = (T)rec[MSK_OP_A0], wAA = (T)rec[MSK_OP_A0A0];
         const T wBA = (T)rec[MSK_OP_BX_A0], wBAA = (T)rec[MSK_OP_BXA0_A0], wBAB = (T)rec[MSK_OP_BXA0_BX];
+        T w[MSK_NOPS];   // all thirteen weights (split operators)
+#pragma unroll
+        for (int q = 0; q < MSK_NOPS; ++q) w[q] = SPLIT ? (T)rec[q] : T(0);
         const double mu = rec[MSK_WT_MU];
         const int s_steps = max(1, (int)rec[MSK_WT_S]);
         const int m_terms = min((int)rec[MSK_WT_M], kVarMaxTerms);
@@ -357,7 +361,77 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
             const T scmu = (T)(mu / ((double)s_steps * k));
             // ---- pass A: p, q at the own points from t (a = A0 t and b = B t
             // evaluated at the own point and its four neighbours, zero off the grid)
-            if (nrows > 0) {
+            if constexpr (SPLIT) {
+              // time-dependent coefficients: the thirteen operators over X = Bx, V = Bvv, A = A0,
+              //   Omega u = X pX + V pV + A pA,  x = X t, v = V t, a = A t (at the own point and
+              //   its four neighbours), and the second-level values aa = A a, ax = A x, ... of them
+              if (nrows > 0) {
+                const T* t = sm + FT * FS;
+                int o = at(FT, p0) - FT * FS;
+                T c0 = t[o - W], c1_ = t[o], c2 = t[o + W];
+                T l0 = t[o - W - 1], l1 = t[o - 1], l2 = t[o + W - 1];
+                T q0 = t[o - W + 1], q1 = t[o + 1], q2 = t[o + W + 1];
+                T am, a0, vm, v0, xm, x0;
+                {
+                  const T cm2 = t[o - 2 * W];
+                  const T mrow = rowm(p0 - 1);
+                  am = mrow * ca * (c1_ - cm2);
+                  vm = mrow * cvv * fma(T(-2), c0, c1_ + cm2);
+                  xm = mrow * cxr[p0 - 1] * (q0 - l0);
+                  a0 = ca * (c2 - c0);
+                  v0 = cvv * fma(T(-2), c1_, c2 + c0);
+                  x0 = cxr[p0] * (q1 - l1);
+                }
+                for (int r = 0; r < nrows; ++r, o += W) {
+                  const int p = p0 + r;
+                  const T c3 = t[o + 2 * W];
+                  const T xl = t[o - 2], xr = t[o + 2];
+                  const T cx = cxr[p];
+                  const T mdn = rowm(p + 1);
+                  const T ap = mdn * ca * (c3 - c1_);
+                  const T vp = mdn * cvv * fma(T(-2), c2, c3 + c1_);
+                  const T xp = mdn * cxr[p + 1] * (q2 - l2);
+                  const T aL = mL * caL * (l2 - l0), aR = mR * caR * (q2 - q0);
+                  const T vL = mL * cvvL * fma(T(-2), l1, l2 + l0), vR = mR * cvvR * fma(T(-2), q1, q2 + q0);
+                  const T xL = mL * cx * (c1_ - xl), xR = mR * cx * (xr - c1_);
+                  const T aa = ca * (ap - am), ax = ca * (xp - xm), av = ca * (vp - vm);
+                  const T xa = cx * (aR - aL), xx = cx * (xR - xL), xv = cx * (vR - vL);
+                  const T va = cvv * fma(T(-2), a0, ap + am), vx = cvv * fma(T(-2), x0, xp + xm);
+                  const T vv = cvv * fma(T(-2), v0, vp + vm);
+                  T PX = w[MSK_OP_BX] * c1_;
+                  PX = fma(w[MSK_OP_BX_A0], a0, PX);
+                  PX = fma(w[MSK_OP_BX_BVV], v0, PX);
+                  PX = fma(w[MSK_OP_BXA0_A0], aa, PX);
+                  PX = fma(w[MSK_OP_BXA0_BX], fma(T(2), ax, -xa), PX);
+                  PX = fma(w[MSK_OP_BXA0_BVV], av, PX);
+                  PX = fma(w[MSK_OP_BVVA0_BX], av - va, PX);
+                  T PV = w[MSK_OP_BVV] * c1_;
+                  PV = fma(w[MSK_OP_BVV_A0], a0, PV);
+                  PV = fma(-w[MSK_OP_BX_BVV], x0, PV);
+                  PV = fma(w[MSK_OP_BVVA0_A0], aa, PV);
+                  PV = fma(w[MSK_OP_BXA0_BVV], ax - xa, PV);
+                  PV = fma(w[MSK_OP_BVVA0_BX], ax, PV);
+                  PV = fma(w[MSK_OP_BVVA0_BVV], fma(T(2), av, -va), PV);
+                  T PA = w[MSK_OP_A0] * c1_;
+                  PA = fma(w[MSK_OP_A0A0], a0, PA);
+                  PA = fma(-w[MSK_OP_BX_A0], x0, PA);
+                  PA = fma(-w[MSK_OP_BVV_A0], v0, PA);
+                  PA = fma(-w[MSK_OP_BXA0_A0], fma(T(2), xa, -ax), PA);
+                  PA = fma(-w[MSK_OP_BVVA0_A0], fma(T(2), va, -av), PA);
+                  PA = fma(-w[MSK_OP_BXA0_BX], xx, PA);
+                  PA = fma(-w[MSK_OP_BXA0_BVV], xv, PA);
+                  PA = fma(-w[MSK_OP_BVVA0_BX], vx, PA);
+                  PA = fma(-w[MSK_OP_BVVA0_BVV], vv, PA);
+                  store(FP, p, PX, 1);
+                  store(FQ, p, PV, 1);
+                  store(FR, p, PA, 1);
+                  am = a0; a0 = ap; vm = v0; v0 = vp; xm = x0; x0 = xp;
+                  c0 = c1_; c1_ = c2; c2 = c3;
+                  l0 = l1; l1 = l2; l2 = t[o + 2 * W - 1];
+                  q0 = q1; q1 = q2; q2 = t[o + 2 * W + 1];
+                }
+              }
+            } else if (nrows > 0) {
               const T* t = sm + FT * FS;
               int o = at(FT, p0) - FT * FS;   // row p0, own column
               // window: rows p-1 .. p+1 of the own and both side columns
@@ -404,7 +478,33 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
             sync_all();
             // ---- pass B: next term (B p + A0 q - mu t) / (s k), in place of t
             T mn = T(0), ma = T(0);
-            if (nrows > 0) {
+            if constexpr (SPLIT) {
+              // (X pX + V pV + A pA - mu t) / (s k)
+              if (nrows > 0) {
+                const T* Xf = sm + FP * FS;
+                const T* Vf = sm + FQ * FS;
+                const T* Af = sm + FR * FS;
+                T* t = sm + FT * FS;
+                int o = at(FT, p0) - FT * FS;
+                T vu = Vf[o - W], vc = Vf[o], au = Af[o - W];
+                for (int r = 0; r < nrows; ++r, o += W) {
+                  const int p = p0 + r;
+                  const T vd = Vf[o + W], ad = Af[o + W];
+                  const T Xp = cxr[p] * (Xf[o + 1] - Xf[o - 1]);
+                  const T tot = fma(ca, ad - au, fma(cvv, fma(T(-2), vc, vd + vu), Xp));
+                  const T tn_ = fma(sc, tot, -scmu * t[o]);
+                  store(FT, p, tn_, 2);
+                  T& acc_ = accs[p * d + col];
+                  const T s_ = acc_ + tn_;
+                  acc_ = s_;
+                  mn = vmax(mn, fabs(tn_));
+                  ma = vmax(ma, fabs(s_));
+                  vu = vc;
+                  vc = vd;
+                  au = Af[o];
+                }
+              }
+            } else if (nrows > 0) {
               const T* Pf = sm + FP * FS;
               const T* Qf = sm + FQ * FS;
               T* t = sm + FT * FS;
@@ -761,6 +861,8 @@ struct VarOpsDev {
   double alpha;   // a0 / 2
   const double* psi;
   const double* gen;   // general coefficients: the 14 stencil fields (B then A); else null
+  int split;           // 1: the thirteen operators over X = Bx, V = Bvv, A = A0 (letters 0, 1, 2)
+  int ops;             // number of operators (6 or 13)
 };
 
 __device__ void add_base_row(const VarOpsDev& o, int op, int i, int j, double c, int pi, int pj,
@@ -785,6 +887,23 @@ __device__ void add_base_row(const VarOpsDev& o, int op, int i, int j, double c,
     return;
   }
   const double psi = o.psi[i];
+  if (o.split) {
+    if (op == 0) {
+      const double gx = o.kx * (o.av + (double)(j + 1) * o.dv);
+      put(i + 1, j, gx);
+      put(i - 1, j, -gx);
+    } else if (op == 1) {
+      const double gv = psi / (o.dv * o.dv);
+      put(i, j + 1, gv);
+      put(i, j - 1, gv);
+      put(i, j, -2.0 * gv);
+    } else {
+      const double ga = sqrt(psi) * (0.5 / o.dv);
+      put(i, j + 1, ga);
+      put(i, j - 1, -ga);
+    }
+    return;
+  }
   if (op == 0) {
     const double gx = o.kx * (o.av + (double)(j + 1) * o.dv);
     const double gv = o.alpha * psi / (o.dv * o.dv);
@@ -815,12 +934,28 @@ __constant__ VarWord c_var_words[12] = {
     {2.0, 3, {0, 1, 0}},  {-1.0, 3, {1, 0, 0}}, {-1.0, 3, {0, 0, 1}} // [[B, A0], B]
 };
 __constant__ int c_var_first[kVarOps + 1] = {0, 1, 2, 3, 5, 8, 11};
+// the thirteen operators of time-dependent coefficients (MSK_OP_* order) over X = 0, V = 1, A = 2
+__constant__ VarWord c_var13_words[30] = {
+    {1.0, 1, {0, 0, 0}}, {1.0, 1, {1, 0, 0}}, {1.0, 1, {2, 0, 0}}, {1.0, 2, {2, 2, 0}},   // X, V, A, AA
+    {1.0, 2, {0, 2, 0}}, {-1.0, 2, {2, 0, 0}},                                            // [X,A]
+    {1.0, 2, {1, 2, 0}}, {-1.0, 2, {2, 1, 0}},                                            // [V,A]
+    {1.0, 2, {0, 1, 0}}, {-1.0, 2, {1, 0, 0}},                                            // [X,V]
+    {1.0, 3, {0, 2, 2}}, {-2.0, 3, {2, 0, 2}}, {1.0, 3, {2, 2, 0}},                      // [[X,A],A]
+    {1.0, 3, {1, 2, 2}}, {-2.0, 3, {2, 1, 2}}, {1.0, 3, {2, 2, 1}},                      // [[V,A],A]
+    {2.0, 3, {0, 2, 0}}, {-1.0, 3, {2, 0, 0}}, {-1.0, 3, {0, 0, 2}},                     // [[X,A],X]
+    {1.0, 3, {0, 2, 1}}, {-1.0, 3, {2, 0, 1}}, {-1.0, 3, {1, 0, 2}}, {1.0, 3, {1, 2, 0}}, // [[X,A],V]
+    {1.0, 3, {1, 2, 0}}, {-1.0, 3, {2, 1, 0}}, {-1.0, 3, {0, 1, 2}}, {1.0, 3, {0, 2, 1}}, // [[V,A],X]
+    {2.0, 3, {1, 2, 1}}, {-1.0, 3, {2, 1, 1}}, {-1.0, 3, {1, 1, 2}}                      // [[V,A],V]
+};
+__constant__ int c_var13_first[MSK_NOPS + 1] = {0, 1, 2, 3, 4, 6, 8, 10, 13, 16, 19, 23, 27, 30};
 
 __device__ void op_row(const VarOpsDev& o, int op, int pi, int pj, double (&row)[7][7]) {
   for (int y = 0; y < 7; ++y)
     for (int x = 0; x < 7; ++x) row[y][x] = 0.0;
-  for (int q = c_var_first[op]; q < c_var_first[op + 1]; ++q) {
-    const VarWord wd = c_var_words[q];
+  const int q0 = o.split ? c_var13_first[op] : c_var_first[op];
+  const int q1 = o.split ? c_var13_first[op + 1] : c_var_first[op + 1];
+  for (int q = q0; q < q1; ++q) {
+    const VarWord wd = o.split ? c_var13_words[q] : c_var_words[q];
     double cur[7][7], nxt[7][7];
     for (int y = 0; y < 7; ++y)
       for (int x = 0; x < 7; ++x) cur[y][x] = 0.0;
@@ -886,17 +1021,17 @@ __global__ void var_norm_kernel(VarOpsDev o, const double* tr_part, double* part
   if (threadIdx.x == 0) part[op * NB + b] = red[0];
 }
 
-// tab[0..5] traces, tab[6..11] shifted norms
-__global__ void var_final_kernel(const double* tr_part, const double* nu_part, int NB, double* tab) {
+// tab[0 .. ops) traces, tab[ops .. 2 ops) shifted norms
+__global__ void var_final_kernel(const double* tr_part, const double* nu_part, int NB, int ops, double* tab) {
   const int op = threadIdx.x;
-  if (op >= kVarOps) return;
+  if (op >= ops) return;
   double tr = 0.0, nu = 0.0;
   for (int q = 0; q < NB; ++q) {
     tr += tr_part[op * NB + q];
     nu = fmax(nu, nu_part[op * NB + q]);
   }
   tab[op] = tr;
-  tab[kVarOps + op] = nu;
+  tab[ops + op] = nu;
 }
 
 __global__ void psi_rational_kernel(int d, double ax, double dx, double c, double* psi) {
@@ -913,12 +1048,22 @@ struct VarPlan {
 };
 
 std::mutex g_plan_mu;
-std::map<std::tuple<int, int, int, bool, bool>, VarPlan> g_plans;
+std::map<std::tuple<int, int, int, bool, int>, VarPlan> g_plans;
 
-template <typename T, bool EULER, bool GEN>
+// engine variants: the six-operator composition (constant coefficients), the
+// thirteen-operator one (time-dependent coefficients), general coefficients
+enum { kModeVar = 0, kModeSplit = 1, kModeGen = 2 };
+
+template <typename T, bool EULER, int MODE>
+constexpr auto engine_of() {
+  if constexpr (MODE == kModeGen) return gen_engine_kernel<T, EULER>;
+  else return var_engine_kernel<T, EULER, MODE == kModeSplit>;
+}
+
+template <typename T, bool EULER, int MODE>
 msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
   const int d = ctx->d;
-  const auto key = std::make_tuple(ctx->device, d, (int)sizeof(T), EULER, GEN);
+  const auto key = std::make_tuple(ctx->device, d, (int)sizeof(T), EULER, MODE);
   {
     std::lock_guard<std::mutex> lock(g_plan_mu);
     auto it = g_plans.find(key);
@@ -927,7 +1072,7 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
       return MSK_OK;
     }
   }
-  auto kern = GEN ? gen_engine_kernel<T, EULER> : var_engine_kernel<T, EULER>;
+  auto kern = engine_of<T, EULER, MODE>();
   msk_status st = msk_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                      (int)kVarSmemCap), "smem attribute");
   if (st != MSK_OK) return st;
@@ -944,7 +1089,9 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
     const int ng = std::max(1, std::min(kVarMaxThreads / d, RS / 2));
     const int R = (RS + ng - 1) / ng;
     const int NT = 32 * ((ng * d + 31) / 32);
-    const size_t smem = (size_t)(GEN ? gen_layout(RS, d, NT).total : var_layout(RS, d, NT).total) * sizeof(T);
+    const int total = MODE == kModeGen ? gen_layout(RS, d, NT).total
+                                       : var_layout(RS, d, NT, MODE == kModeSplit ? kVarFields + 1 : kVarFields).total;
+    const size_t smem = (size_t)total * sizeof(T);
     if (smem > kVarSmemCap) continue;
     int clusters = 0;
     if (C == 1) {
@@ -996,10 +1143,10 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
                   "grid size / precision does not fit the variable-coefficient engine (cluster of <= 16 CTAs)");
 }
 
-template <typename T, bool EULER, bool GEN>
+template <typename T, bool EULER, int MODE>
 msk_status launch_var_typed(msk_ctx* ctx, VarArgs a, int64_t paths, cudaStream_t stream) {
   VarPlan pl;
-  msk_status st = plan_var<T, EULER, GEN>(ctx, &pl);
+  msk_status st = plan_var<T, EULER, MODE>(ctx, &pl);
   if (st != MSK_OK) return st;
   a.C = pl.C;
   a.RS = pl.RS;
@@ -1020,8 +1167,7 @@ msk_status launch_var_typed(msk_ctx* ctx, VarArgs a, int64_t paths, cudaStream_t
     cfg.attrs = attr;
     cfg.numAttrs = 1;
   }
-  return msk_cuda(ctx, cudaLaunchKernelEx(&cfg, GEN ? gen_engine_kernel<T, EULER> : var_engine_kernel<T, EULER>, a),
-                  "variable-coefficient engine");
+  return msk_cuda(ctx, cudaLaunchKernelEx(&cfg, engine_of<T, EULER, MODE>(), a), "variable-coefficient engine");
 }
 
 }  // namespace
@@ -1031,11 +1177,17 @@ msk_status launch_psi_rational(msk_ctx* ctx, double c, cudaStream_t stream) {
   return msk_cuda(ctx, cudaGetLastError(), "psi kernel");
 }
 
+int var_table_ops(const msk_ctx* ctx) {
+  return (!ctx->gen && ctx->xprof && ctx->coef.kind == MSK_COEF_TRIG) ? MSK_NOPS : kVarOps;
+}
+
 msk_status ensure_var_tables(msk_ctx* ctx, cudaStream_t stream) {
-  if ((!ctx->xprof && !ctx->gen) || !ctx->var_dirty) return MSK_OK;
+  if (!ctx->xprof && !ctx->gen) return MSK_OK;
+  const int ops = var_table_ops(ctx);
+  if (!ctx->var_dirty && ctx->var_ops_built == ops) return MSK_OK;
   constexpr int NB = kVarNormBlocks;
   if (!ctx->var_tab) {
-    msk_status st = msk_cuda(ctx, cudaMalloc(&ctx->var_tab, (2 * kVarOps + 2 * kVarOps * NB) * sizeof(double)),
+    msk_status st = msk_cuda(ctx, cudaMalloc(&ctx->var_tab, (2 * MSK_NOPS + 2 * MSK_NOPS * NB) * sizeof(double)),
                              "operator table allocation");
     if (st != MSK_OK) return st;
   }
@@ -1047,13 +1199,18 @@ msk_status ensure_var_tables(msk_ctx* ctx, cudaStream_t stream) {
   o.alpha = 0.5 * ctx->coef.a0;
   o.psi = ctx->psi;
   o.gen = ctx->gen ? ctx->gen64 : nullptr;
-  double* tr_part = ctx->var_tab + 2 * kVarOps;
-  double* nu_part = tr_part + kVarOps * NB;
-  var_trace_kernel<<<dim3(kVarOps, NB), 256, 0, stream>>>(o, tr_part);
-  var_norm_kernel<<<dim3(kVarOps, NB), 256, 0, stream>>>(o, tr_part, nu_part);
-  var_final_kernel<<<1, 32, 0, stream>>>(tr_part, nu_part, NB, ctx->var_tab);
+  o.split = ops == MSK_NOPS;
+  o.ops = ops;
+  double* tr_part = ctx->var_tab + 2 * MSK_NOPS;
+  double* nu_part = tr_part + MSK_NOPS * NB;
+  var_trace_kernel<<<dim3(ops, NB), 256, 0, stream>>>(o, tr_part);
+  var_norm_kernel<<<dim3(ops, NB), 256, 0, stream>>>(o, tr_part, nu_part);
+  var_final_kernel<<<1, 32, 0, stream>>>(tr_part, nu_part, NB, ops, ctx->var_tab);
   msk_status st = msk_cuda(ctx, cudaGetLastError(), "operator norm kernels");
-  if (st == MSK_OK) ctx->var_dirty = false;
+  if (st == MSK_OK) {
+    ctx->var_dirty = false;
+    ctx->var_ops_built = ops;
+  }
   return st;
 }
 
@@ -1061,10 +1218,6 @@ msk_status launch_engine_var(msk_ctx* ctx, bool euler, int steps, int64_t paths,
                              const double* Wt, const double* dW, void* out, uint32_t* status,
                              cudaStream_t stream, const EngineSnap& x) {
   if (paths == 0) return MSK_OK;
-  if (!euler && !ctx->gen && ctx->coef.kind != MSK_COEF_CONST)
-    return msk_fail(ctx, MSK_ERR_UNSUPPORTED,
-                    "Magnus with an x profile needs constant coefficients (time-dependent ones are built for "
-                    "the constant-coefficient operators only)");
   VarArgs a{};
   a.u0 = ctx->u0;
   a.Wt = Wt;
@@ -1095,16 +1248,20 @@ msk_status launch_engine_var(msk_ctx* ctx, bool euler, int steps, int64_t paths,
     a.gB = precision == MSK_F32 ? (const void*)ctx->gen32 : (const void*)ctx->gen64;
     a.gA = precision == MSK_F32 ? (const void*)(ctx->gen32 + 9 * dd) : (const void*)(ctx->gen64 + 9 * dd);
     if (precision == MSK_F32)
-      return euler ? launch_var_typed<float, true, true>(ctx, a, paths, stream)
-                   : launch_var_typed<float, false, true>(ctx, a, paths, stream);
-    return euler ? launch_var_typed<double, true, true>(ctx, a, paths, stream)
-                 : launch_var_typed<double, false, true>(ctx, a, paths, stream);
+      return euler ? launch_var_typed<float, true, kModeGen>(ctx, a, paths, stream)
+                   : launch_var_typed<float, false, kModeGen>(ctx, a, paths, stream);
+    return euler ? launch_var_typed<double, true, kModeGen>(ctx, a, paths, stream)
+                 : launch_var_typed<double, false, kModeGen>(ctx, a, paths, stream);
   }
-  if (precision == MSK_F32)
-    return euler ? launch_var_typed<float, true, false>(ctx, a, paths, stream)
-                 : launch_var_typed<float, false, false>(ctx, a, paths, stream);
-  return euler ? launch_var_typed<double, true, false>(ctx, a, paths, stream)
-               : launch_var_typed<double, false, false>(ctx, a, paths, stream);
+  const bool split = ctx->coef.kind == MSK_COEF_TRIG;   // Magnus with time-dependent coefficients
+  if (precision == MSK_F32) {
+    if (euler) return launch_var_typed<float, true, kModeVar>(ctx, a, paths, stream);
+    return split ? launch_var_typed<float, false, kModeSplit>(ctx, a, paths, stream)
+                 : launch_var_typed<float, false, kModeVar>(ctx, a, paths, stream);
+  }
+  if (euler) return launch_var_typed<double, true, kModeVar>(ctx, a, paths, stream);
+  return split ? launch_var_typed<double, false, kModeSplit>(ctx, a, paths, stream)
+               : launch_var_typed<double, false, kModeVar>(ctx, a, paths, stream);
 }
 
 extern "C" msk_status msk_set_x_profile(msk_ctx* ctx, int kind, double c, const double* psi_host) {

@@ -41,6 +41,7 @@ struct msk_ctx {
   double* psi = nullptr;      // [d] psi(x_i), device
   double* var_tab = nullptr;  // 6 traces, 6 shifted norms of the variable-coefficient operators; partials
   bool var_dirty = true;      // var_tab must be rebuilt (profile, a0, drift or general coefficients changed)
+  int var_ops_built = 0;      // operators var_tab holds: 6 (constant coefficients) or 13 (time-dependent)
   // general coefficients of Eq. generalSPDE (msk_set_general_coefficients)
   int gen = 0;
   double* gen64 = nullptr;    // [14][d][d] stencil fields: B (9), A (5)
@@ -111,6 +112,7 @@ msk_status launch_engine_var(msk_ctx* ctx, bool euler, int steps, int64_t paths,
                              const double* Wt, const double* dW, void* out, uint32_t* status,
                              cudaStream_t stream, const EngineSnap& x);
 msk_status ensure_var_tables(msk_ctx* ctx, cudaStream_t stream);
+int var_table_ops(const msk_ctx* ctx);
 msk_status launch_psi_rational(msk_ctx* ctx, double c, cudaStream_t stream);
 
 // Device-side coefficient profiles.

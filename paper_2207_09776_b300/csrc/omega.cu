@@ -31,7 +31,8 @@ __constant__ double c_theta32[MSK_THETA_MMAX_F32];
 struct OmegaArgs {
   const double* band;
   const double* trace;
-  const double* var;   // x profile: traces [0, 6) and shifted norms [6, 12) of the six operators; else null
+  const double* var;   // x profile / general coefficients: traces [0, ops) and shifted norms [ops, 2 ops); else null
+  int var_ops;         // 6: the six operators of constant coefficients; 13: the MSK_OP_* basis
   const double* job_th;   // interval mode: (t0, h) per record; else null (step n: t0 = n h, h = T / steps)
   int D, order, steps, precision;
   int64_t paths;
@@ -135,7 +136,16 @@ __global__ void omega_kernel(OmegaArgs a, const double* __restrict__ F, double* 
   magnus_weights(a, tn, h, F + idx * MSK_NF, w);
   const int D = a.D;
   double mu, nrm = 0.0;
-  if (a.var) {
+  if (a.var && a.var_ops == MSK_NOPS) {
+    // x profile, time-dependent coefficients: the thirteen basis operators, each
+    // with its exact trace and shifted norm
+    double tr = 0.0;
+    for (int k = 0; k < MSK_NOPS; ++k) {
+      tr += w[k] * a.var[k];
+      nrm += fabs(w[k]) * a.var[MSK_NOPS + k];
+    }
+    mu = tr / ((double)D * D);
+  } else if (a.var) {
     // x profile (constant coefficients): Omega over the six operators B, A0, A0^2,
     // [B,A0], [[B,A0],A0], [[B,A0],B] with B = Bx + alpha Bvv; the bound is the sum
     // of |weight| x the exact norm of each operator minus its own trace shift
@@ -228,8 +238,8 @@ msk_status launch_omega(msk_ctx* ctx, int order, int steps, int64_t paths, int p
     st0 = ensure_var_tables(ctx, stream);
     if (st0 != MSK_OK) return st0;
   }
-  OmegaArgs a{ctx->band, ctx->aux, (ctx->xprof || ctx->gen) ? ctx->var_tab : nullptr, nullptr, ctx->d, order, steps,
-              precision, paths, ctx->T, ctx->dx, omega_coef(ctx), kMskScaleCap};
+  OmegaArgs a{ctx->band, ctx->aux, (ctx->xprof || ctx->gen) ? ctx->var_tab : nullptr, var_table_ops(ctx), nullptr,
+              ctx->d, order, steps, precision, paths, ctx->T, ctx->dx, omega_coef(ctx), kMskScaleCap};
   omega_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(a, F, Wt);
   return msk_cuda(ctx, cudaGetLastError(), "omega kernel");
 }
@@ -245,8 +255,8 @@ msk_status launch_omega_jobs(msk_ctx* ctx, int order, int64_t njobs, int precisi
     st0 = ensure_var_tables(ctx, stream);
     if (st0 != MSK_OK) return st0;
   }
-  OmegaArgs a{ctx->band, ctx->aux, (ctx->xprof || ctx->gen) ? ctx->var_tab : nullptr, job_th_dev, ctx->d, order, 1,
-              precision, njobs, ctx->T, ctx->dx, omega_coef(ctx), kMskScaleCap};
+  OmegaArgs a{ctx->band, ctx->aux, (ctx->xprof || ctx->gen) ? ctx->var_tab : nullptr, var_table_ops(ctx),
+              job_th_dev, ctx->d, order, 1, precision, njobs, ctx->T, ctx->dx, omega_coef(ctx), kMskScaleCap};
   omega_kernel<<<(unsigned)((njobs + 127) / 128), 128, 0, stream>>>(a, F, Wt);
   return msk_cuda(ctx, cudaGetLastError(), "omega kernel (intervals)");
 }

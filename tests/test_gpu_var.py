@@ -209,14 +209,63 @@ def test_unsupported_combinations_are_reported():
     with pytest.raises(msk.MskError) as e:
         msk.msk_explicit_solution(s.ctx, 1, out)
     assert e.value.status == msk.MSK_ERR_UNSUPPORTED
-    msk.msk_set_coefficients(s.ctx, -1, COEF_TRIG, 1.1, 0.2, 0.3, 0.1)
-    with pytest.raises(msk.MskError) as e:
-        msk.msk_solve_magnus(s.ctx, 3, 4, 1, msk.MSK_F64, out)
-    assert e.value.status == msk.MSK_ERR_UNSUPPORTED
     for kind, c, vals, status in ((7, 1.0, None, msk.MSK_ERR_ARG), (msk.MSK_XPROF_RATIONAL, -1.0, None, msk.MSK_ERR_ARG),
                                   (msk.MSK_XPROF_RATIONAL, float("nan"), None, msk.MSK_ERR_NONFINITE),
                                   (msk.MSK_XPROF_VALUES, 0.0, [1.0] * 31 + [0.0], msk.MSK_ERR_ARG)):
         with pytest.raises(msk.MskError) as e:
             msk.msk_set_x_profile(s.ctx, kind, c, vals)
         assert e.value.status == status
+    s.close()
+
+
+# ---------------------------------------------------------------- time-dependent coefficients
+def trig_case(d, **kw):
+    base = dict(kind=COEF_TRIG, a1=0.4, s1=0.3, n_fine=256)
+    base.update(kw)
+    return var_case(d, **base)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_time_dependent_coefficients_with_a_profile_match_the_oracle(order):
+    """The thirteen-operator composition (X = Bx, V = Bvv, A = A0 with the profile)."""
+    w = trig_case(24, paths=3)
+    s = msk.Solver(w)
+    ref = omagnus.solve(w, order, 4, list(range(w.paths)))
+    assert rel_l2(s.magnus(order, 4, precision=msk.MSK_F64).cpu().numpy(), ref).max() <= TOL64
+    assert rel_l2(s.magnus(order, 4, precision=msk.MSK_F32).cpu().numpy(), ref).max() <= TOL32
+    s.close()
+
+
+def test_time_dependent_coefficients_with_a_profile_on_a_cluster():
+    w = trig_case(90, paths=2, n_fine=128)
+    s = msk.Solver(w)
+    got = s.magnus(3, 2, precision=msk.MSK_F64).cpu().numpy()
+    assert rel_l2(got, omagnus.solve(w, 3, 2, [0, 1])).max() <= TOL64
+    s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(msk.MSK_F64, 1e-12), (msk.MSK_F32, TOL32)])
+def test_unit_profile_with_time_dependent_coefficients_equals_the_main_engine(prec, tol):
+    from workloads import LANGEVIN_TRIG_128
+    w = LANGEVIN_TRIG_128.with_(d=64, paths=4, n_fine=1024)
+    s = msk.Solver(w)
+    ref = s.magnus(3, 8, precision=prec).double().cpu().numpy()
+    msk.msk_set_x_profile(s.ctx, msk.MSK_XPROF_VALUES, 0.0, [1.0] * w.d)
+    got = s.magnus(3, 8, precision=prec).double().cpu().numpy()
+    assert rel_l2(got, ref).max() <= tol
+    s.close()
+
+
+def test_thirteen_operator_traces_and_norm_bounds():
+    w = trig_case(16, paths=2, n_fine=64, s0=0.8)
+    s = msk.Solver(w)
+    Wt = s.weights(3, 4, precision=msk.MSK_F64).cpu().numpy()
+    n = w.d * w.d
+    for p in range(w.paths):
+        for k in range(4):
+            Y = omagnus.omega_matrix(w, 3, 4, p, k).toarray()
+            mu = np.trace(Y) / n
+            assert abs(Wt[p, k, msk.MSK_WT_MU] - mu) <= 1e-12 * max(1.0, abs(mu))
+            exact = np.abs(Y - mu * np.eye(n)).sum(axis=1).max()
+            assert exact <= Wt[p, k, msk.MSK_WT_NORM] * (1 + 1e-12) <= 3.0 * exact * (1 + 1e-12)
     s.close()
