@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
         const int s_steps = max(1, (int)rec[MSK_WT_S]);
         const int m_terms = min((int)rec[MSK_WT_M], kVarMaxTerms);
         if (rec[MSK_WT_S] >= a.s_cap) scale_cap = true;
-        const T te = (T)exp(mu / s_steps);
+        const T te = (T)exp(mu / s_steps), muT = (T)mu;
         for (int k = tid; k <= kVarMaxTerms; k += NT)
           scale_tab[k] = (T)(k == 0 ? 1.0 : 1.0 / ((double)s_steps * k));
         __syncthreads();
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
           T c1 = unorm;   // norm of the previous Taylor term (term 0 = the state)
           for (int k = 1; k <= m_terms; ++k) {
             const T sc = scale_tab[k];
-            const T scmu = (T)(mu / ((double)s_steps * k));
+            const T scmu = sc * muT;   // mu / (s k) without double arithmetic per term
             // ---- pass A: p, q at the own points from t (a = A0 t and b = B t
             // evaluated at the own point and its four neighbours, zero off the grid)
             if constexpr (SPLIT) {
@@ -725,7 +725,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
         const int s_steps = max(1, (int)rec[MSK_WT_S]);
         const int m_terms = min((int)rec[MSK_WT_M], kVarMaxTerms);
         if (rec[MSK_WT_S] >= a.s_cap) scale_cap = true;
-        const T te = (T)exp(mu / s_steps);
+        const T te = (T)exp(mu / s_steps), muT = (T)mu;
         for (int k = tid; k <= kVarMaxTerms; k += NT)
           scale_tab[k] = (T)(k == 0 ? 1.0 : 1.0 / ((double)s_steps * k));
         __syncthreads();
@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
           T c1n = unorm;
           for (int k = 1; k <= m_terms; ++k) {
             const T sc = scale_tab[k];
-            const T scmu = (T)(mu / ((double)s_steps * k));
+            const T scmu = sc * muT;   // mu / (s k) without double arithmetic per term
             {   // pass 1: a = A t, b = B t
               const T* t = sm + ft * FS;
               for (int r = 0; r < nrows; ++r) {
