@@ -225,11 +225,18 @@ extern "C" msk_status msk_solve_euler(msk_ctx* ctx, int steps, int64_t paths, in
   cudaStream_t s = (cudaStream_t)stream;
   st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
   if (st != MSK_OK) return st;
-  st = msk_ensure_scratch(ctx, (size_t)paths * steps * sizeof(double));
+  // scratch: increments [paths][steps], then the per-step coefficient table (2 doubles + 2 floats)
+  st = msk_ensure_scratch(ctx, ((size_t)paths * steps + 3 * (size_t)steps) * sizeof(double));
   if (st != MSK_OK) return st;
   double* dW = reinterpret_cast<double*>(ctx->scratch);
+  EngineSnap x;
+  double* em_d = dW + (size_t)paths * steps;
+  x.em_d = em_d;
+  x.em_f = reinterpret_cast<float*>(em_d + 2 * (size_t)steps);
   st = launch_brownian(ctx, steps, paths, dW, true, s, precision == MSK_F32);
-  if (st == MSK_OK) st = launch_engine(ctx, true, steps, paths, precision, nullptr, dW, u_out_dev, path_status_dev, s);
+  if (st == MSK_OK) st = launch_em_table(ctx, steps, em_d, const_cast<float*>(x.em_f), s);
+  if (st == MSK_OK)
+    st = launch_engine_ex(ctx, true, steps, paths, precision, nullptr, dW, u_out_dev, path_status_dev, s, x);
   return st;
 }
 

@@ -92,7 +92,23 @@ msk_status dispatch(msk_ctx* ctx, int precision, const EngineArgs& a, cudaStream
   return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "grid size / precision combination not built");
 }
 
+__global__ void em_table_kernel(CoefDev c, double T, int steps, double* em_d, float* em_f) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= steps) return;
+  const double dt = T / steps, tn = n * dt;
+  const double al = alpha_t(c, tn) * dt, sg = sigma_t(c, tn);
+  em_d[2 * n] = al;
+  em_d[2 * n + 1] = sg;
+  em_f[2 * n] = (float)al;
+  em_f[2 * n + 1] = (float)sg;
+}
+
 }  // namespace
+
+msk_status launch_em_table(msk_ctx* ctx, int steps, double* em_d, float* em_f, cudaStream_t stream) {
+  em_table_kernel<<<(steps + 255) / 256, 256, 0, stream>>>(coef_dev(ctx->coef), ctx->T, steps, em_d, em_f);
+  return msk_cuda(ctx, cudaGetLastError(), "euler table");
+}
 
 msk_status launch_engine(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
                          const double* Wt, const double* dW, void* out, uint32_t* status,
@@ -112,6 +128,8 @@ msk_status launch_engine_ex(msk_ctx* ctx, bool euler, int steps, int64_t paths, 
   a.snap_cnt = x.snap_cnt;
   a.n_out = x.n_out;
   a.u0_self = x.u0_self;
+  a.em_d = x.em_d;
+  a.em_f = x.em_f;
   a.band = ctx->band;
   a.u0 = ctx->u0;
   a.Wt = Wt;

@@ -64,6 +64,9 @@ struct EngineArgs {
   const int* snap_cnt;
   int n_out;
   int u0_self;        // 1: each path starts from its own out[path] (T) instead of u0
+  // Euler: per step alpha(t_n) dt and sigma(t_n) ([steps][2], double and float copies)
+  const double* em_d;
+  const float* em_f;
   uint32_t* status;
   unsigned long long* work;
   int64_t paths;
@@ -97,8 +100,15 @@ struct Cfg {
   // the registers, and the register-resident sum spills there.
   static constexpr bool ACC_SMEM = C > 1;
   static constexpr size_t OFF_CSLOT = OFF_SLOT + 4 * NW;           // 2 x 2 CTA-level norm slots
-  static constexpr size_t OFF_ACC = (OFF_CSLOT + 4 + 3) / 4 * 4;
-  static constexpr size_t NELEM = ACC_SMEM ? OFF_ACC + (size_t)RS * D : OFF_CSLOT + 4;
+  // unit-weight tables (built once per path): the twelve coefficients of the five
+  // row classes for each basis operator alone, and the V1 centre of each of the six
+  // D^x-class operators per local row; a step's tables are their weighted sums
+  static constexpr int NDX = 6;
+  static constexpr size_t OFF_EU = OFF_CSLOT + 4;                  // MSK_NOPS x 5 x 12
+  static constexpr size_t OFF_BU = OFF_EU + (size_t)MSK_NOPS * 5 * MSK_NCOEF;   // NDX x RS
+  static constexpr size_t OFF_END = OFF_BU + (size_t)NDX * RS;
+  static constexpr size_t OFF_ACC = (OFF_END + 3) / 4 * 4;
+  static constexpr size_t NELEM = ACC_SMEM ? OFF_ACC + (size_t)RS * D : OFF_END;
   static constexpr size_t SMEM = NELEM * sizeof(T);
   static_assert(SMEM <= 232448, "slab does not fit the 227 KB of shared memory per CTA");
 };
@@ -394,6 +404,29 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
     par ^= 1;
     bool scale_cap = false;
     unsigned long long nmv = 0;
+    const T dtT = (T)(a.T / a.steps);
+
+    // ---- unit-weight tables of this context (see Cfg::OFF_EU) ---------------------
+    {
+      T* eu = sm + K::OFF_EU;
+      T* bu = sm + K::OFF_BU;
+      for (int e = tid; e < MSK_NOPS * 5; e += NT) {
+        const int k = e / 5, r = e % 5;
+        const int jr = r < 4 ? special_row(r, D) : 2;
+        double wv[MSK_NOPS];
+        for (int q = 0; q < MSK_NOPS; ++q) wv[q] = q == k ? 1.0 : 0.0;
+        double cf[MSK_NCOEF];
+        fold_row(a.band, D, jr, wv, 0.0, inv2dx, inv4dx2, cf);
+        for (int q = 0; q < MSK_NCOEF; ++q) eu[(size_t)e * MSK_NCOEF + q] = (T)cf[q];
+      }
+      constexpr int dx[K::NDX] = {MSK_OP_BX, MSK_OP_BX_A0, MSK_OP_BX_BVV, MSK_OP_BXA0_A0, MSK_OP_BXA0_BVV,
+                                  MSK_OP_BVVA0_BX};
+      for (int e = tid; e < K::NDX * RS; e += NT) {
+        const int c = e / RS, jl = e % RS;
+        bu[e] = (T)(a.band[((size_t)dx[c] * D + r0 + jl) * MSK_BAND + 2] * inv2dx);
+      }
+      sync_all.local();
+    }
 
     // snapshots of the state at the start of step n (n = steps: the final state)
     auto snapshot = [&](int n) {
@@ -409,40 +442,57 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
     for (int n = 0; n < a.steps; ++n) {
       snapshot(n);
       // ---- this step's operator: coefficient tables and Taylor parameters ---------
-      double w[MSK_NOPS];
-      double shift;
+      // The step's weights in the working precision: lane k (< 13) of every warp
+      // converts weight k and lane 13 the diagonal shift (one conversion per warp);
+      // shuffles broadcast them.  The tables are the weighted sums of the unit
+      // tables (no double arithmetic per step on the slow double pipe).
       int s_steps = 1, m_terms = 1;
-      double eta = 1.0;
+      double mu = 0.0;
+      T wl = T(0);
       if constexpr (EULER) {
-        const double dt = a.T / a.steps, tn = n * dt;
-        const double dWn = a.dW[path * a.steps + n];
-        for (int k = 0; k < MSK_NOPS; ++k) w[k] = 0.0;
-        w[MSK_OP_BX] = dt;
-        w[MSK_OP_BVV] = alpha_t(a.c, tn) * dt;
-        w[MSK_OP_A0] = sigma_t(a.c, tn) * dWn;
-        shift = 1.0;
+        const T* em = sizeof(T) == 4 ? reinterpret_cast<const T*>(a.em_f) : reinterpret_cast<const T*>(a.em_d);
+        if (lane == MSK_OP_BX) wl = dtT;
+        else if (lane == MSK_OP_BVV) wl = em[2 * n];                                   // alpha(t_n) dt
+        else if (lane == MSK_OP_A0) wl = em[2 * n + 1] * (T)a.dW[path * a.steps + n];   // sigma(t_n) dW_n
+        else if (lane == MSK_NOPS) wl = T(1);                                           // I + ...
       } else {
         const double* rec = a.Wt + ((size_t)path * a.steps + n) * MSK_NWT;
-        for (int k = 0; k < MSK_NOPS; ++k) w[k] = rec[k];
-        const double mu = rec[MSK_WT_MU];
+        mu = rec[MSK_WT_MU];
         s_steps = (int)rec[MSK_WT_S];
         m_terms = min((int)rec[MSK_WT_M], kMaxTerms);
         if (rec[MSK_WT_S] >= a.s_cap) scale_cap = true;
-        shift = -mu;
-        eta = exp(mu / s_steps);
+        if (lane < MSK_NOPS) wl = (T)rec[lane];
+        else if (lane == MSK_NOPS) wl = (T)(-mu);
       }
-      if (tid < 5) {
-        const int jr = tid < 4 ? special_row(tid, D) : 2;
-        double cf[MSK_NCOEF];
-        fold_row(a.band, D, jr, w, shift, inv2dx, inv4dx2, cf);
+      T wT[MSK_NOPS + 1];
 #pragma unroll
-        for (int q = 0; q < MSK_NCOEF; ++q) coef[tid * MSK_NCOEF + q] = (T)cf[q];
+      for (int k = 0; k <= MSK_NOPS; ++k) wT[k] = __shfl_sync(0xffffffffu, wl, k);
+      for (int q = tid; q < 5 * MSK_NCOEF; q += NT) {
+        const T* e = sm + K::OFF_EU + q;
+        T v = (q % MSK_NCOEF == CF_A + 2) ? wT[MSK_NOPS] : T(0);
+#pragma unroll
+        for (int k = 0; k < MSK_NOPS; ++k) v = fma(wT[k], e[k * 5 * MSK_NCOEF], v);
+        coef[q] = v;
       }
       for (int k = tid; k <= kMaxTerms; k += NT)
-        scale_tab[k] = EULER ? T(1) : (T)(k == 0 ? 1.0 : 1.0 / ((double)s_steps * k));
-      for (int jl = tid; jl < RS; jl += NT) b0row[jl] = (T)fold_b0(a.band, D, r0 + jl, w, inv2dx);
+        scale_tab[k] = (EULER || k == 0) ? T(1) : T(1) / ((T)s_steps * (T)k);
+      {
+        constexpr int dx[K::NDX] = {MSK_OP_BX, MSK_OP_BX_A0, MSK_OP_BX_BVV, MSK_OP_BXA0_A0, MSK_OP_BXA0_BVV,
+                                    MSK_OP_BVVA0_BX};   // the D^x-class operators
+        const T* bu = sm + K::OFF_BU;
+        for (int jl = tid; jl < RS; jl += NT) {
+          T v = T(0);
+#pragma unroll
+          for (int c = 0; c < K::NDX; ++c) v = fma(wT[dx[c]], bu[c * RS + jl], v);
+          b0row[jl] = v;
+        }
+      }
       sync_all.local();
-      const T te = (T)eta;
+      T te = T(1);
+      if constexpr (!EULER) {
+        if constexpr (sizeof(T) == 4) te = (T)expf((float)mu / (float)s_steps);
+        else te = (T)exp(mu / s_steps);
+      }
 
       for (int sub = 0; sub < s_steps; ++sub) {
         T c1 = unorm;   // norm of the previous Taylor term (term 0 = the state)

@@ -76,6 +76,8 @@ struct VarArgs {
   int n_out, u0_self;
   const void* gB;     // general coefficients: B stencil [9][d][d] and A stencil [5][d][d] (T)
   const void* gA;
+  const double* em_d;  // Euler: alpha(t_n) dt, sigma(t_n) per step (double / float)
+  const float* em_f;
   int64_t paths;
   int steps, d, C, RS, ng, R;
   double dx, dv, av, kappa, T, s_cap;
@@ -257,6 +259,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
   colc(act ? col - 1 : -1, cvBL, caL, cvvL);
   colc(act ? col + 1 : -1, cvBR, caR, cvvR);
   const T mL = (act && col > 0) ? T(1) : T(0), mR = (act && col < d - 1) ? T(1) : T(0);
+  const T dtT = (T)(a.T / a.steps);
   sync_all();   // every CTA zeroed before any halo store reaches it
 
   const uint32_t peer_lo = (C > 1 && rank > 0) ? cl_addr(sm, rank - 1) : 0u;
@@ -315,11 +318,10 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
     for (int n = 0; n < a.steps; ++n) {
       snapshot(n);
       if constexpr (EULER) {
-        const double dt = a.T / a.steps, tn = n * dt;
-        const double dWn = a.dW[path * a.steps + n];
-        const T kx = (T)dt;
-        const T kv = (T)(var_alpha_t(a.c, tn) * dt) * cvv;
-        const T ka = (T)(var_sigma_t(a.c, tn) * dWn) * ca;
+        const T* em = sizeof(T) == 4 ? reinterpret_cast<const T*>(a.em_f) : reinterpret_cast<const T*>(a.em_d);
+        const T kx = dtT;
+        const T kv = em[2 * n] * cvv;                                       // alpha(t_n) dt psi / dv^2
+        const T ka = em[2 * n + 1] * (T)a.dW[path * a.steps + n] * ca;      // sigma(t_n) dW_n sqrt(psi) / (2 dv)
         if (nrows > 0) {
           const T* t = sm + ft * FS;
           int o = at(ft, p0) - ft * FS;
@@ -617,6 +619,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
   const T* __restrict__ gB = reinterpret_cast<const T*>(a.gB);
   const T* __restrict__ gA = reinterpret_cast<const T*>(a.gA);
   const int dd = d * d;
+  const T kt = (T)(a.T / a.steps);
 
   auto sync_all = [&]() {
     if (C > 1) cg::this_cluster().sync();
@@ -704,7 +707,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
       snapshot(n);
       if constexpr (EULER) {
         // t + dt B t + dW A t (time-independent coefficients)
-        const T kt = (T)(a.T / a.steps), kw = (T)a.dW[path * a.steps + n];
+        const T kw = (T)a.dW[path * a.steps + n];
         const T* t = sm + ft * FS;
         for (int r = 0; r < nrows; ++r) {
           const int p = p0 + r, o = off(p), g = (r0 + p) * d + col;
@@ -1231,6 +1234,8 @@ msk_status launch_engine_var(msk_ctx* ctx, bool euler, int steps, int64_t paths,
   a.snap_cnt = x.snap_cnt;
   a.n_out = x.n_out;
   a.u0_self = x.u0_self;
+  a.em_d = x.em_d;
+  a.em_f = x.em_f;
   a.paths = paths;
   a.steps = steps;
   a.d = ctx->d;

@@ -97,7 +97,12 @@ struct EngineSnap {
   const int* snap_cnt = nullptr;
   int n_out = 0;
   int u0_self = 0;
+  // Euler-Maruyama: alpha(t_n) dt and sigma(t_n) per step ([steps][2], double and float)
+  const double* em_d = nullptr;
+  const float* em_f = nullptr;
 };
+// Fill the Euler table of `steps` steps: em_d[2n] = alpha(t_n) dt, em_d[2n+1] = sigma(t_n), em_f the same in float.
+msk_status launch_em_table(msk_ctx* ctx, int steps, double* em_d, float* em_f, cudaStream_t stream);
 msk_status launch_engine_ex(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
                             const double* Wt, const double* dW, void* out, uint32_t* status,
                             cudaStream_t stream, const EngineSnap& x);
