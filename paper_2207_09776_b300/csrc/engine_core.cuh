@@ -456,17 +456,23 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
         else if (lane == MSK_OP_A0) wl = em[2 * n + 1] * (T)a.dW[path * a.steps + n];   // sigma(t_n) dW_n
         else if (lane == MSK_NOPS) wl = T(1);                                           // I + ...
       } else {
+        // lanes 14, 15 carry s and m (exact in float: s <= 2^14, m <= 64)
         const double* rec = a.Wt + ((size_t)path * a.steps + n) * MSK_NWT;
-        mu = rec[MSK_WT_MU];
-        s_steps = (int)rec[MSK_WT_S];
-        m_terms = min((int)rec[MSK_WT_M], kMaxTerms);
-        if (rec[MSK_WT_S] >= a.s_cap) scale_cap = true;
         if (lane < MSK_NOPS) wl = (T)rec[lane];
-        else if (lane == MSK_NOPS) wl = (T)(-mu);
+        else if (lane == MSK_NOPS) wl = (T)(-rec[MSK_WT_MU]);
+        else if (lane == MSK_NOPS + 1) wl = (T)rec[MSK_WT_S];
+        else if (lane == MSK_NOPS + 2) wl = (T)rec[MSK_WT_M];
       }
       T wT[MSK_NOPS + 1];
 #pragma unroll
       for (int k = 0; k <= MSK_NOPS; ++k) wT[k] = __shfl_sync(0xffffffffu, wl, k);
+      if constexpr (!EULER) {
+        const T sv = __shfl_sync(0xffffffffu, wl, MSK_NOPS + 1), mv = __shfl_sync(0xffffffffu, wl, MSK_NOPS + 2);
+        s_steps = (int)sv;
+        m_terms = min((int)mv, kMaxTerms);
+        if (sv >= (T)a.s_cap) scale_cap = true;
+        mu = -(double)wT[MSK_NOPS];
+      }
       for (int q = tid; q < 5 * MSK_NCOEF; q += NT) {
         const T* e = sm + K::OFF_EU + q;
         T v = (q % MSK_NCOEF == CF_A + 2) ? wT[MSK_NOPS] : T(0);
@@ -490,7 +496,7 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
       sync_all.local();
       T te = T(1);
       if constexpr (!EULER) {
-        if constexpr (sizeof(T) == 4) te = (T)expf((float)mu / (float)s_steps);
+        if constexpr (sizeof(T) == 4) te = (T)expf(-(float)wT[MSK_NOPS] / (float)s_steps);
         else te = (T)exp(mu / s_steps);
       }
 
