@@ -267,7 +267,7 @@ msk_status msk_solve_magnus_times(msk_ctx* ctx, int order, int steps, int64_t pa
  * file-scope __device__ array of 2^21 doubles (16 MiB) that every GPU loading
  * the library holds until exit.  No cudaMalloc, cudaFree or allocating
  * library routine is called.  Requests needing more than the array
- * (paths * steps * (MSK_NF + MSK_NWT) doubles, plus 4 (n_fine + 1) for
+ * (paths * steps * (MSK_NF + MSK_NWT) doubles, plus 6 (n_fine + 1) for
  * MSK_COEF_TRIG) fail with MSK_ERR_ARG before any device work.  The first call
  * on a device looks up the array's address (once per device); make it before
  * any stream capture.  All calls share the array and it keeps the last call's

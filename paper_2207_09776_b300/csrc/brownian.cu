@@ -39,8 +39,9 @@ struct BrownArgs {
   int steps;
   double T;
   CoefDev c;
-  // TRIG: [3][n_fine + 1] doubles sigma(mid), alpha(node), A(mid), then [2][n_fine + 1]
-  // floats sigma(mid), alpha(node); null for CONST
+  // TRIG: [4][n_fine + 1] doubles sigma(mid), alpha(node), A(mid), A(node), then
+  // [4][n_fine + 1] floats sigma(mid), alpha(node), A(node+1) - A(node), A(mid) - A(node);
+  // null for CONST
   const double* tab;
   // Interval mode (steps = 1, paths = number of intervals): interval i covers the
   // fine cells jobs[3i+1] .. jobs[3i+1] + jobs[3i+2] - 1 of local path jobs[3i].
@@ -60,10 +61,14 @@ __global__ void cell_table_kernel(CoefDev c, int64_t n_fine, double T, double* t
   const double sig = c.s0 * (1.0 + c.s1 * cospi(2.0 * tm)), alp = 0.5 * (c.a0 + c.a1 * sinpi(2.0 * tk));
   tab[k] = sig;                                                                    // sigma at cell midpoint
   tab[(n_fine + 1) + k] = alp;                                                     // alpha at node
-  tab[2 * (n_fine + 1) + k] = alpha_anti(c, tm);                                   // A at cell midpoint
-  float* tf = reinterpret_cast<float*>(tab + 3 * (n_fine + 1));                   // float copies
+  const double Am = alpha_anti(c, tm), An = alpha_anti(c, tk);
+  tab[2 * (n_fine + 1) + k] = Am;                                                  // A at cell midpoint
+  tab[3 * (n_fine + 1) + k] = An;                                                  // A at node
+  float* tf = reinterpret_cast<float*>(tab + 4 * (n_fine + 1));                   // float copies
   tf[k] = (float)sig;
   tf[(n_fine + 1) + k] = (float)alp;
+  tf[2 * (n_fine + 1) + k] = (float)(alpha_anti(c, tk + delta) - An);             // int of alpha over the cell
+  tf[3 * (n_fine + 1) + k] = (float)(Am - An);                                     // ... over its first half
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -113,8 +118,11 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
   //   sum (k + 1/2) sdw = sum k sdw + sum sdw / 2,   sum (om0 + om1) = 2 sum om0 + sum sdw.
   double Sw0 = 0.0, S2 = 0.0, Skw = 0.0, So0 = 0.0, Sks = 0.0, J3 = 0.0, J4 = 0.0;
   double swT = 0.0, soT = 0.0;                              // sum dw, sum sigma dW of the lane's cells
-  const float* tsig_f = TRIG ? reinterpret_cast<const float*>(a.tab + 3 * (a.n_fine + 1)) : nullptr;
+  const float* tsig_f = TRIG ? reinterpret_cast<const float*>(a.tab + 4 * (a.n_fine + 1)) : nullptr;
   const float* talp_f = TRIG ? tsig_f + (a.n_fine + 1) : nullptr;
+  const float* tia_f = TRIG ? tsig_f + 2 * (a.n_fine + 1) : nullptr;   // int of alpha over cell k
+  const float* tah_f = TRIG ? tsig_f + 3 * (a.n_fine + 1) : nullptr;   // ... over its first half
+  const double* tAn = TRIG ? a.tab + 3 * (a.n_fine + 1) : nullptr;     // A at the nodes
   float* stf = reinterpret_cast<float*>(st);
   for (int64_t rb = 0; rb < L; rb += kRound) {
     // ---- pass 1: normals of this lane's chunk, chunk sums -------------------------
@@ -160,9 +168,11 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
     if constexpr (NF32) {
       // w = woff + x, om = ooff + y with x, y the float running sums inside the chunk;
       // k = c0 + kl.  Chunk sums A = sum x0, B = sum (x0^2 + x0 x1 + x1^2), Ck = sum kl (x0 + x1),
-      // E = sum y0, Fk = sum kl sdw, H = sum (alpha0 + alpha1), I = sum (alpha0 y0 + alpha1 y1).
-      float x0 = 0.0f, y0 = 0.0f, kl = 0.0f;
-      float A = 0.0f, Bq = 0.0f, Ck = 0.0f, E = 0.0f, Fk = 0.0f, H = 0.0f, I = 0.0f;
+      // E = sum y0, Fk = sum kl sdw, H = sum (alpha0 + alpha1), I = sum (alpha0 y0 + alpha1 y1),
+      // Jz = sum (z + ah) sdw with alpha_bar(s_mid) = zoff + z + ah: zoff = A(chunk start) -
+      // A(step start) (double, once per chunk), z the float running integral of alpha.
+      float x0 = 0.0f, y0 = 0.0f, kl = 0.0f, z = 0.0f;
+      float A = 0.0f, Bq = 0.0f, Ck = 0.0f, E = 0.0f, Fk = 0.0f, H = 0.0f, I = 0.0f, Jz = 0.0f;
       for (int q = 0; q < cnt; ++q) {
         const int64_t fi = f0 + c0 + q;
         const float dw = stf[q * 32 + lane];
@@ -178,7 +188,8 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
           const float al0 = talp_f[fi], al1 = talp_f[fi + 1];
           H += al0 + al1;
           I = fmaf(al0, y0, fmaf(al1, y1, I));
-          J4 = fma(tA[fi] - Astart, (double)sdw, J4);     // sum alpha_bar(s_mid) sigma dW
+          Jz = fmaf(z + tah_f[fi], sdw, Jz);
+          z += tia_f[fi];
         }
         x0 = x1;
         y0 = y1;
@@ -191,7 +202,10 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
       Skw += kc * (2.0 * n * woff + sx) + 2.0 * woff * (0.5 * n * (n - 1.0)) + (double)Ck;
       So0 += n * ooff + (double)E;
       Sks += kc * (double)y0 + (double)Fk;
-      if (TRIG) J3 += ooff * (double)H + (double)I;
+      if (TRIG) {
+        J3 += ooff * (double)H + (double)I;
+        if (cnt > 0) J4 += (tAn[f0 + c0] - Astart) * (double)y0 + (double)Jz;   // y0 = sum sdw of the chunk
+      }
     } else {
       double w0 = woff, om0 = ooff;
       double kd = (double)c0;
@@ -263,7 +277,7 @@ static msk_status ensure_cell_table(msk_ctx* ctx, cudaStream_t stream) {
     ctx->tab = nullptr;
   }
   if (!ctx->tab) {
-    msk_status st = msk_cuda(ctx, cudaMalloc(&ctx->tab, 4 * (size_t)(ctx->n_fine + 1) * sizeof(double)),
+    msk_status st = msk_cuda(ctx, cudaMalloc(&ctx->tab, 6 * (size_t)(ctx->n_fine + 1) * sizeof(double)),
                              "cell table allocation");
     if (st != MSK_OK) return st;
   }
@@ -342,7 +356,7 @@ msk_status launch_brownian_strided(msk_ctx* ctx, int steps, int64_t paths, doubl
 }
 
 // Variants for callers that supply the per-cell table buffer themselves
-// (4 * (n_fine + 1) doubles); used by the entry point that allocates nothing.
+// (6 * (n_fine + 1) doubles); used by the entry point that allocates nothing.
 msk_status launch_cell_table_into(msk_ctx* ctx, double* tab, cudaStream_t stream) {
   const int64_t n = ctx->n_fine + 1;
   cell_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(coef_dev(ctx->coef), ctx->n_fine, ctx->T, tab);

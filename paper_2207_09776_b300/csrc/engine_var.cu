@@ -341,19 +341,29 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
         fo = sw;
         ++nmv;
       } else {
+        // the record in the working precision: lane q of every warp converts entry q
+        // (weights 0..12, then mu, s, m) once, shuffles broadcast it
         const double* rec = a.Wt + ((size_t)path * a.steps + n) * MSK_NWT;
-        const T wB = (T)rec[MSK_OP_BX], wA = (T)rec[MSK_OP_A0], wAA = (T)rec[MSK_OP_A0A0];
-        const T wBA = (T)rec[MSK_OP_BX_A0], wBAA = (T)rec[MSK_OP_BXA0_A0], wBAB = (T)rec[MSK_OP_BXA0_BX];
-        T w[MSK_NOPS];   // all thirteen weights (split operators)
+        T rl = T(0);
+        if (lane < MSK_NOPS) rl = (T)rec[lane];
+        else if (lane == MSK_NOPS) rl = (T)rec[MSK_WT_MU];
+        else if (lane == MSK_NOPS + 1) rl = (T)rec[MSK_WT_S];
+        else if (lane == MSK_NOPS + 2) rl = (T)rec[MSK_WT_M];
+        T w[MSK_NOPS];
 #pragma unroll
-        for (int q = 0; q < MSK_NOPS; ++q) w[q] = SPLIT ? (T)rec[q] : T(0);
-        const double mu = rec[MSK_WT_MU];
-        const int s_steps = max(1, (int)rec[MSK_WT_S]);
-        const int m_terms = min((int)rec[MSK_WT_M], kVarMaxTerms);
-        if (rec[MSK_WT_S] >= a.s_cap) scale_cap = true;
-        const T te = (T)exp(mu / s_steps), muT = (T)mu;
+        for (int q = 0; q < MSK_NOPS; ++q) w[q] = __shfl_sync(0xffffffffu, rl, q);
+        const T wB = w[MSK_OP_BX], wA = w[MSK_OP_A0], wAA = w[MSK_OP_A0A0];
+        const T wBA = w[MSK_OP_BX_A0], wBAA = w[MSK_OP_BXA0_A0], wBAB = w[MSK_OP_BXA0_BX];
+        const T muT = __shfl_sync(0xffffffffu, rl, MSK_NOPS);
+        const T sT = __shfl_sync(0xffffffffu, rl, MSK_NOPS + 1), mT = __shfl_sync(0xffffffffu, rl, MSK_NOPS + 2);
+        const int s_steps = max(1, (int)sT);               // exact: s <= 2^14, m <= 64
+        const int m_terms = min((int)mT, kVarMaxTerms);
+        if (sT >= (T)a.s_cap) scale_cap = true;
+        T te;
+        if constexpr (sizeof(T) == 4) te = (T)expf((float)muT / (float)s_steps);
+        else te = (T)exp(rec[MSK_WT_MU] / s_steps);
         for (int k = tid; k <= kVarMaxTerms; k += NT)
-          scale_tab[k] = (T)(k == 0 ? 1.0 : 1.0 / ((double)s_steps * k));
+          scale_tab[k] = k == 0 ? T(1) : T(1) / ((T)s_steps * (T)k);
         __syncthreads();
 
         for (int sub = 0; sub < s_steps; ++sub) {
@@ -722,15 +732,25 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
         ++nmv;
       } else {
         const double* rec = a.Wt + ((size_t)path * a.steps + n) * MSK_NWT;
-        const T wB = (T)rec[MSK_OP_BX], wA = (T)rec[MSK_OP_A0], wAA = (T)rec[MSK_OP_A0A0];
-        const T wBA = (T)rec[MSK_OP_BX_A0], wBAA = (T)rec[MSK_OP_BXA0_A0], wBAB = (T)rec[MSK_OP_BXA0_BX];
-        const double mu = rec[MSK_WT_MU];
-        const int s_steps = max(1, (int)rec[MSK_WT_S]);
-        const int m_terms = min((int)rec[MSK_WT_M], kVarMaxTerms);
-        if (rec[MSK_WT_S] >= a.s_cap) scale_cap = true;
-        const T te = (T)exp(mu / s_steps), muT = (T)mu;
+        T rl = T(0);   // see the variable-coefficient engine: one conversion per warp, shuffles
+        if (lane < MSK_NOPS) rl = (T)rec[lane];
+        else if (lane == MSK_NOPS) rl = (T)rec[MSK_WT_MU];
+        else if (lane == MSK_NOPS + 1) rl = (T)rec[MSK_WT_S];
+        else if (lane == MSK_NOPS + 2) rl = (T)rec[MSK_WT_M];
+        const T wB = __shfl_sync(0xffffffffu, rl, MSK_OP_BX), wA = __shfl_sync(0xffffffffu, rl, MSK_OP_A0);
+        const T wAA = __shfl_sync(0xffffffffu, rl, MSK_OP_A0A0), wBA = __shfl_sync(0xffffffffu, rl, MSK_OP_BX_A0);
+        const T wBAA = __shfl_sync(0xffffffffu, rl, MSK_OP_BXA0_A0);
+        const T wBAB = __shfl_sync(0xffffffffu, rl, MSK_OP_BXA0_BX);
+        const T muT = __shfl_sync(0xffffffffu, rl, MSK_NOPS);
+        const T sT = __shfl_sync(0xffffffffu, rl, MSK_NOPS + 1), mT = __shfl_sync(0xffffffffu, rl, MSK_NOPS + 2);
+        const int s_steps = max(1, (int)sT);
+        const int m_terms = min((int)mT, kVarMaxTerms);
+        if (sT >= (T)a.s_cap) scale_cap = true;
+        T te;
+        if constexpr (sizeof(T) == 4) te = (T)expf((float)muT / (float)s_steps);
+        else te = (T)exp(rec[MSK_WT_MU] / s_steps);
         for (int k = tid; k <= kVarMaxTerms; k += NT)
-          scale_tab[k] = (T)(k == 0 ? 1.0 : 1.0 / ((double)s_steps * k));
+          scale_tab[k] = k == 0 ? T(1) : T(1) / ((T)s_steps * (T)k);
         __syncthreads();
         for (int sub = 0; sub < s_steps; ++sub) {
           T c1n = unorm;

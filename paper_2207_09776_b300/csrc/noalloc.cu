@@ -14,7 +14,7 @@
 //    loads this library holds it from the moment the library's device code is
 //    loaded there until the process exits.
 //  - A request needs paths * steps * (MSK_NF + MSK_NWT) doubles, plus
-//    4 * (n_fine + 1) for time-dependent coefficients; larger requests are
+//    6 * (n_fine + 1) for time-dependent coefficients; larger requests are
 //    rejected with MSK_ERR_ARG before any device work.
 //  - The first call on a device looks up the array's device address (set-up,
 //    once per device, with that device current); make that first call before
@@ -74,12 +74,12 @@ extern "C" msk_status msk_solve_magnus_noalloc(msk_ctx* ctx, int order, int step
   if (!u_out_dev) return msk_fail(ctx, MSK_ERR_ARG, "null output");
   const bool trig = ctx->coef.kind == MSK_COEF_TRIG;
   const size_t nF = (size_t)paths * steps * MSK_NF, nW = (size_t)paths * steps * MSK_NWT;
-  const size_t nT = trig ? 4 * (size_t)(ctx->n_fine + 1) : 0;
+  const size_t nT = trig ? 6 * (size_t)(ctx->n_fine + 1) : 0;
   if (nF + nW + nT > kNoAllocScratchDoubles)
     return msk_fail(ctx, MSK_ERR_ARG,
                     "request needs " + std::to_string(nF + nW + nT) + " doubles of scratch; the static scratch of "
                     "msk_solve_magnus_noalloc holds " + std::to_string(kNoAllocScratchDoubles) +
-                    " (paths * steps * " + std::to_string(MSK_NF + MSK_NWT) + " + 4 (n_fine + 1) if time-dependent)");
+                    " (paths * steps * " + std::to_string(MSK_NF + MSK_NWT) + " + 6 (n_fine + 1) if time-dependent)");
   cudaStream_t s = (cudaStream_t)stream;
   msk_status st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
   if (st != MSK_OK) return st;
