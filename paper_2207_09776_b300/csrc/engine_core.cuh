@@ -527,25 +527,36 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
             const int jg = r0 + p;
             const V4<T> cw4 = ld4(src + at(p + 2, i0));
             xterms(cw3, src, p + 1, d12, s22);
-            RowCoef<T> c = ci;
-            if (is_special_row(jg, D)) c = make(coef + special_index(jg, D) * MSK_NCOEF);
-            else c.b1 = b0row[p] * sc;
-            V4<T> out;
+            auto stencil = [&](const RowCoef<T>& c) -> V4<T> {
+              V4<T> o;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const T a1 = q == 0 ? c.a1q0 : (q == 3 ? c.a1q3 : c.a1);
-              const T a3 = q == 0 ? c.a3q0 : (q == 3 ? c.a3q3 : c.a3);
-              T v = c.a0 * get(cw0, q);
-              v = fma(a1, get(cw1, q), v);
-              v = fma(c.a2, get(cw2, q), v);
-              v = fma(a3, get(cw3, q), v);
-              v = fma(c.a4, get(cw4, q), v);
-              v = fma(c.b0, get(d10, q), v);
-              v = fma(c.b1, get(d11, q), v);
-              v = fma(c.b2, get(d12, q), v);
-              v = fma(c.c0, get(s20, q), v);
-              v = fma(c.c1, get(s22, q), v);
-              set(out, q, v);
+              for (int q = 0; q < 4; ++q) {
+                const T a1 = q == 0 ? c.a1q0 : (q == 3 ? c.a1q3 : c.a1);
+                const T a3 = q == 0 ? c.a3q0 : (q == 3 ? c.a3q3 : c.a3);
+                T v = c.a0 * get(cw0, q);
+                v = fma(a1, get(cw1, q), v);
+                v = fma(c.a2, get(cw2, q), v);
+                v = fma(a3, get(cw3, q), v);
+                v = fma(c.a4, get(cw4, q), v);
+                v = fma(c.b0, get(d10, q), v);
+                v = fma(c.b1, get(d11, q), v);
+                v = fma(c.b2, get(d12, q), v);
+                v = fma(c.c0, get(s20, q), v);
+                v = fma(c.c1, get(s22, q), v);
+                set(o, q, v);
+              }
+              return o;
+            };
+            // The four boundary rows (rows of two warps at most, the branch is warp-uniform)
+            // take their own coefficient set; every other row the interior set with its own
+            // V1 centre.  Two separate evaluations keep the interior path free of selects.
+            V4<T> out;
+            if (__builtin_expect(is_special_row(jg, D), 0)) {
+              out = stencil(make(coef + special_index(jg, D) * MSK_NCOEF));
+            } else {
+              RowCoef<T> c = ci;
+              c.b1 = b0row[p] * sc;
+              out = stencil(c);
             }
             store_row(nxt, p, out);
             if constexpr (EULER) {
