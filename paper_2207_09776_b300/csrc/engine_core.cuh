@@ -147,6 +147,17 @@ template <typename T> __device__ __forceinline__ T amax4(const V4<T>& v) {
 }
 template <typename T> __device__ __forceinline__ T absnan(T x) { return (x == x) ? tabs(x) : T(INFINITY); }
 
+// Warp maximum of non-negative values: for float one redux.sync on the bit patterns
+// (non-negative floats order like their bit patterns), for double a shuffle tree.
+__device__ __forceinline__ float warp_max_nonneg(float x) {
+  return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(x)));
+}
+__device__ __forceinline__ double warp_max_nonneg(double x) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, off));
+  return x;
+}
+
 __device__ __forceinline__ double sigma_t(const CoefDev& c, double t) {
   return c.s0 * (1.0 + c.s1 * cospi(2.0 * t));
 }
@@ -322,18 +333,12 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
         ga = tmax(ga, slots[(par * NW + q) * 2 + 1]);
       }
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      gn = tmax(gn, __shfl_xor_sync(0xffffffffu, gn, off));
-      ga = tmax(ga, __shfl_xor_sync(0xffffffffu, ga, off));
-    }
+    gn = warp_max_nonneg(gn);
+    ga = warp_max_nonneg(ga);
   };
   auto publish = [&](int par, T mn, T ma) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      mn = tmax(mn, __shfl_xor_sync(0xffffffffu, mn, off));
-      ma = tmax(ma, __shfl_xor_sync(0xffffffffu, ma, off));
-    }
+    mn = warp_max_nonneg(mn);
+    ma = warp_max_nonneg(ma);
     if (lane == 0) {
       slots[(par * NW + warp) * 2 + 0] = mn;
       slots[(par * NW + warp) * 2 + 1] = ma;
@@ -346,11 +351,8 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
           a = tmax(a, slots[(par * NW + q) * 2 + 0]);
           b = tmax(b, slots[(par * NW + q) * 2 + 1]);
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          a = tmax(a, __shfl_xor_sync(0xffffffffu, a, off));
-          b = tmax(b, __shfl_xor_sync(0xffffffffu, b, off));
-        }
+        a = warp_max_nonneg(a);
+        b = warp_max_nonneg(b);
         if (lane == 0) {
           cslot[par * 2 + 0] = a;
           cslot[par * 2 + 1] = b;
