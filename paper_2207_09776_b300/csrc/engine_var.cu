@@ -131,6 +131,15 @@ __device__ __forceinline__ double cl_ld(uint32_t addr, double) {
 
 __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+// warp maximum of non-negative values (float: one redux.sync on the bit patterns)
+__device__ __forceinline__ float wmax(float x) {
+  return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(x)));
+}
+__device__ __forceinline__ double wmax(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
 template <typename T> __device__ __forceinline__ T vabsnan(T x) { return (x == x) ? fabs(x) : T(INFINITY); }
 
 __device__ __forceinline__ double var_sigma_t(const CoefDev& c, double t) {
@@ -152,11 +161,8 @@ struct NormSlots {
   T* cslot;    // [2][2]
   int NW, C, lane, warp;
   __device__ __forceinline__ void publish(int par, T mn, T ma) const {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      mn = vmax(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      ma = vmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
-    }
+    mn = wmax(mn);
+    ma = wmax(ma);
     if (lane == 0) {
       slots[(par * NW + warp) * 2 + 0] = mn;
       slots[(par * NW + warp) * 2 + 1] = ma;
@@ -169,11 +175,8 @@ struct NormSlots {
           x = vmax(x, slots[(par * NW + q) * 2 + 0]);
           y = vmax(y, slots[(par * NW + q) * 2 + 1]);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          x = vmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-          y = vmax(y, __shfl_xor_sync(0xffffffffu, y, o));
-        }
+        x = wmax(x);
+        y = wmax(y);
         if (lane == 0) {
           cslot[par * 2 + 0] = x;
           cslot[par * 2 + 1] = y;
@@ -196,11 +199,8 @@ struct NormSlots {
         ga = vmax(ga, slots[(par * NW + q) * 2 + 1]);
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      gn = vmax(gn, __shfl_xor_sync(0xffffffffu, gn, o));
-      ga = vmax(ga, __shfl_xor_sync(0xffffffffu, ga, o));
-    }
+    gn = wmax(gn);
+    ga = wmax(ga);
   }
 };
 
