@@ -504,6 +504,16 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
 
       for (int sub = 0; sub < s_steps; ++sub) {
         T c1 = unorm;   // norm of the previous Taylor term (term 0 = the state)
+        // the first four window rows of the next term are loaded right after the
+        // barrier, before the termination test (wasted only when the series stops)
+        V4<T> pw0, pw1, pw2, pw3;
+        {
+          const T* src = sm + cur * K::BUF;
+          pw0 = ld4(src + at(j0 - 2, i0));
+          pw1 = ld4(src + at(j0 - 1, i0));
+          pw2 = ld4(src + at(j0, i0));
+          pw3 = ld4(src + at(j0 + 1, i0));
+        }
         for (int k = 1; k <= m_terms; ++k) {
           const T sc = scale_tab[k];
           auto make = [&](const T* q) -> RowCoef<T> {
@@ -518,8 +528,7 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
           const T* src = sm + cur * K::BUF;
           T mn = T(0), ma = T(0);
           // sliding window: own columns of rows j-2..j+2, x terms of rows j-1..j+1
-          V4<T> cw0 = ld4(src + at(j0 - 2, i0)), cw1 = ld4(src + at(j0 - 1, i0));
-          V4<T> cw2 = ld4(src + at(j0, i0)), cw3 = ld4(src + at(j0 + 1, i0));
+          V4<T> cw0 = pw0, cw1 = pw1, cw2 = pw2, cw3 = pw3;
           V4<T> d10, s20, d11, s21, d12, s22;
           xterms(cw1, src, j0 - 1, d10, s20);
           xterms(cw2, src, j0, d11, s21);
@@ -584,6 +593,13 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
           } else {
             publish(par, mn, ma);
             sync_all();
+            {
+              const T* srcn = sm + nxt * K::BUF;
+              pw0 = ld4(srcn + at(j0 - 2, i0));
+              pw1 = ld4(srcn + at(j0 - 1, i0));
+              pw2 = ld4(srcn + at(j0, i0));
+              pw3 = ld4(srcn + at(j0 + 1, i0));
+            }
             T gn, ga;
             gather(par, gn, ga);
             par ^= 1;
