@@ -147,6 +147,18 @@ template <typename T> __device__ __forceinline__ T amax4(const V4<T>& v) {
 }
 template <typename T> __device__ __forceinline__ T absnan(T x) { return (x == x) ? tabs(x) : T(INFINITY); }
 
+// max(m, |v.x|, |v.y|, |v.z|, |v.w|): two three-input maxima in float (max.f32 with three
+// operands), four two-input ones in double; NaN is ignored as by fmax.
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float accmax4(float m, const V4<float>& v) {
+  return max3f(fabsf(v.x), fabsf(v.y), max3f(fabsf(v.z), fabsf(v.w), m));
+}
+__device__ __forceinline__ double accmax4(double m, const V4<double>& v) { return fmax(m, amax4(v)); }
+
 // Warp maximum of non-negative values: for float one redux.sync on the bit patterns
 // (non-negative floats order like their bit patterns), for double a shuffle tree.
 __device__ __forceinline__ float warp_max_nonneg(float x) {
@@ -579,8 +591,8 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
               ac.z += out.z;
               ac.w += out.w;
               acc_put(r, ac);
-              mn = tmax(mn, amax4(out));
-              ma = tmax(ma, amax4(ac));
+              mn = accmax4(mn, out);
+              ma = accmax4(ma, ac);
             }
             cw0 = cw1; cw1 = cw2; cw2 = cw3; cw3 = cw4;
             d10 = d11; s20 = s21; d11 = d12; s21 = s22;
