@@ -231,6 +231,24 @@ msk_status msk_apply_omega(msk_ctx* ctx, const double* weights_dev, int64_t path
 msk_status msk_solve_magnus(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
                             void* u_out_dev, uint32_t* path_status_dev, void* stream);
 
+/* msk_solve_magnus with the initial datum and the results in host memory
+ * (Section 3, "Implementation": the solutions of all paths are produced on the
+ * GPU; this call returns them to the host without a separate copy step).
+ * u0_host: optional double[nv][nx] initial datum (NULL keeps the context's);
+ * it is copied to the device on `stream` before the solve (any host memory;
+ * page-locked memory makes the copy asynchronous).  u_out_host: [paths][v][x]
+ * of double (MSK_F64) or float (MSK_F32); path_status_host: optional
+ * uint32[paths].  Both must be page-locked and mapped into the device's address
+ * space (cudaHostAlloc, a pinned torch tensor, or cudaHostRegister with
+ * cudaHostRegisterMapped); otherwise the call returns MSK_ERR_ARG before any
+ * work is enqueued.  The solver's kernels store each finished path directly
+ * into u_out_host, so the device-to-host transfer overlaps the solve of the
+ * remaining paths.  Caller-owned buffers; the results are complete once
+ * `stream` has reached the end of the call (synchronise it before reading). */
+msk_status msk_solve_magnus_host(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
+                                 const double* u0_host, void* u_out_host, uint32_t* path_status_host,
+                                 void* stream);
+
 /* S5b + S6 only: the iterated Magnus solve from precomputed per-(path, step)
  * records Wt_dev (layout of msk_omega_weights, double[paths * steps * MSK_NWT],
  * caller-owned).  msk_solve_magnus = msk_brownian_functionals +

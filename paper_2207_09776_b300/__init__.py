@@ -83,6 +83,7 @@ SIGNATURES = {
     "msk_omega_weights": (_INT, [_P, _INT, _INT, _I64, _INT, _P, _P, _P]),
     "msk_apply_omega": (_INT, [_P, _P, _I64, _P, _P, _P]),
     "msk_solve_magnus": (_INT, [_P, _INT, _INT, _I64, _INT, _P, _P, _P]),
+    "msk_solve_magnus_host": (_INT, [_P, _INT, _INT, _I64, _INT, _P, _P, _P, _P]),
     "msk_solve_euler": (_INT, [_P, _INT, _I64, _INT, _P, _P, _P]),
     "msk_magnus_from_weights": (_INT, [_P, _INT, _I64, _INT, _P, _P, _P, _P]),
     "msk_solve_magnus_noalloc": (_INT, [_P, _INT, _INT, _I64, _INT, _P, _P, _P]),
@@ -158,6 +159,14 @@ def _ptr(t) -> Optional[int]:
         return None
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("device buffers must be contiguous CUDA tensors")
+    return t.data_ptr()
+
+
+def _host_ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("host buffers must be contiguous CPU tensors")
     return t.data_ptr()
 
 
@@ -276,6 +285,18 @@ def msk_solve_magnus(ctx, order, steps, paths, precision, u_out, status=None, st
     _need(u_out, 1, _dtype(precision), "u_out")
     _check(load_library().msk_solve_magnus(ctx, order, steps, paths, precision, _ptr(u_out), _ptr(status),
                                            _stream(stream)), ctx)
+
+
+def msk_solve_magnus_host(ctx, order, steps, paths, precision, u0, u_out, status=None, stream=None):
+    """msk_solve_magnus with host buffers: u0 optional float64 CPU tensor of d*d values (the initial
+    datum, copied on the stream), u_out and status page-locked CPU tensors (tensor.pin_memory()),
+    into which the kernels store each finished path.  Synchronise the stream before reading."""
+    import torch
+    _need(u_out, 1, _dtype(precision), "u_out")
+    if u0 is not None:
+        _need(u0, 1, torch.float64, "u0")
+    _check(load_library().msk_solve_magnus_host(ctx, order, steps, paths, precision, _host_ptr(u0),
+                                                _host_ptr(u_out), _host_ptr(status), _stream(stream)), ctx)
 
 
 def msk_solve_magnus_noalloc(ctx, order, steps, paths, precision, u_out, status=None, stream=None):
@@ -551,6 +572,18 @@ class Solver:
         u = self.state(paths, precision) if out is None else out
         st = torch.zeros(max(paths, 1), dtype=torch.int32, device=self.device) if status else None
         msk_solve_magnus(self.ctx, order, steps, paths, precision, u, st)
+        return (u, st) if status else u
+
+    def magnus_host(self, order, steps, paths=None, precision=MSK_F64, status=False, u0=None):
+        """The solve with page-locked host results (shape (paths, d, d)); waits for the stream."""
+        import torch
+        paths = self.w.paths if paths is None else paths
+        n = max(paths, 1) * self.w.d * self.w.d
+        u = torch.empty(n, dtype=_dtype(precision), pin_memory=True)[: paths * self.w.d ** 2]
+        st = torch.zeros(max(paths, 1), dtype=torch.int32, pin_memory=True) if status else None
+        msk_solve_magnus_host(self.ctx, order, steps, paths, precision, u0, u, st)
+        torch.cuda.current_stream().synchronize()
+        u = u.view(paths, self.w.d, self.w.d)
         return (u, st) if status else u
 
     def magnus_times(self, order, steps, times_cells, paths=None, precision=MSK_F64, status=False):

@@ -214,6 +214,53 @@ extern "C" msk_status msk_solve_magnus(msk_ctx* ctx, int order, int steps, int64
   return st;
 }
 
+// The device address of a page-locked, mapped host buffer (nullptr if it is not one).
+static void* mapped_device_ptr(void* host) {
+  if (!host) return nullptr;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost) return nullptr;
+  void* dev = nullptr;
+  if (cudaHostGetDevicePointer(&dev, host, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return dev;
+}
+
+extern "C" msk_status msk_solve_magnus_host(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
+                                            const double* u0_host, void* u_out_host, uint32_t* path_status_host,
+                                            void* stream) {
+  if (!ctx) return MSK_ERR_ARG;
+  if (order < 1 || order > 3) return msk_fail(ctx, MSK_ERR_ARG, "order must be 1, 2 or 3");
+  if (precision != MSK_F64 && precision != MSK_F32) return msk_fail(ctx, MSK_ERR_ARG, "bad precision");
+  msk_status st = check_steps(ctx, steps, paths);
+  if (st != MSK_OK) return st;
+  if (paths == 0) return MSK_OK;
+  if (!u_out_host) return msk_fail(ctx, MSK_ERR_ARG, "null output");
+  st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
+  if (st != MSK_OK) return st;
+  void* out = mapped_device_ptr(u_out_host);
+  if (!out) return msk_fail(ctx, MSK_ERR_ARG, "u_out_host is not page-locked host memory mapped into the device");
+  uint32_t* status = nullptr;
+  if (path_status_host) {
+    status = static_cast<uint32_t*>(mapped_device_ptr(path_status_host));
+    if (!status)
+      return msk_fail(ctx, MSK_ERR_ARG, "path_status_host is not page-locked host memory mapped into the device");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (u0_host) {
+    const size_t dd = (size_t)ctx->d * ctx->d;
+    st = msk_cuda(ctx, cudaMemcpyAsync(ctx->u0, u0_host, dd * sizeof(double), cudaMemcpyHostToDevice, s),
+                  "copy u0 from the host");
+    if (st != MSK_OK) return st;
+  }
+  return msk_solve_magnus(ctx, order, steps, paths, precision, out, status, stream);
+}
+
 extern "C" msk_status msk_solve_euler(msk_ctx* ctx, int steps, int64_t paths, int precision, void* u_out_dev,
                                       uint32_t* path_status_dev, void* stream) {
   if (!ctx) return MSK_ERR_ARG;

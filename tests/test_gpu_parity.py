@@ -193,6 +193,37 @@ def test_fp64_and_fp32_agree_on_many_paths():
     s.close()
 
 
+@pytest.mark.parametrize("precision,tol", [(msk.MSK_F32, TOL32), (msk.MSK_F64, TOL64)])
+def test_solve_with_host_buffers(precision, tol):
+    """msk_solve_magnus_host: the kernels store every path straight into page-locked
+    host memory; the results equal the device-buffer solve bit for bit (same kernels,
+    ragged path count), an initial datum passed from the host replaces the context's,
+    and pageable output memory is refused before any work is enqueued."""
+    w = LANGEVIN_TRIG_128.with_(d=64, paths=301, n_fine=1024)
+    s = solver(w)
+    u_dev, st_dev = s.magnus(3, 8, precision=precision, status=True)
+    u_host, st_host = s.magnus_host(3, 8, precision=precision, status=True)
+    assert not u_host.is_cuda and u_host.is_pinned()
+    np.testing.assert_array_equal(u_host.numpy(), u_dev.cpu().numpy())
+    np.testing.assert_array_equal(st_host.numpy()[:w.paths], st_dev.cpu().numpy()[:w.paths])
+    ref = omagnus.solve_path(w, 3, 8, 200)
+    assert rel_l2(u_host[200:201].numpy(), ref[None])[0] <= tol
+    # a host initial datum (a skewed Gaussian) replaces the context's
+    g = disc.gaussian_initial(w.with_(u0_mean=(-1.0, 0.5), u0_cov=(0.8, 0.2, 0.6)))
+    u0 = torch.from_numpy(np.ascontiguousarray(disc.vec(g)))
+    got = s.magnus_host(3, 8, paths=3, precision=precision, u0=u0).numpy()
+    ref = np.stack([omagnus.solve_path(w, 3, 8, p, u0=u0.numpy()) for p in range(3)])
+    assert rel_l2(got, ref).max() <= tol
+    # pageable host memory cannot be written by the kernels: refused
+    bad = torch.empty(3 * w.d * w.d, dtype=torch.float32 if precision == msk.MSK_F32 else torch.float64)
+    with pytest.raises(msk.MskError) as e:
+        msk.msk_solve_magnus_host(s.ctx, 3, 8, 3, precision, None, bad)
+    assert e.value.status == msk.MSK_ERR_ARG
+    with pytest.raises(ValueError):
+        msk.msk_solve_magnus_host(s.ctx, 3, 8, 3, precision, None, u_dev)   # a device tensor
+    s.close()
+
+
 def test_euler_parity():
     w = LANGEVIN_32.with_(paths=6)
     s = solver(w)
