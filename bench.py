@@ -117,18 +117,92 @@ def host_cores():
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
+    """SM clock, power and clock-event reasons of one GPU, read (never set) every 10 ms
+    through NVML in a background thread while the timed region runs; nvidia-smi at
+    200 ms where the NVML library cannot be loaded.  The samples are also kept in a
+    CSV file among the run's outputs."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.thread = None
+        self.rows = []
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
 
+    def _nvml_index(self):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if ids and all(v.isdigit() for v in ids) and self.index < len(ids):
+            return int(ids[self.index])
+        return self.index
+
+    class _Nvml:
+        """The few read-only NVML queries the sampler needs, through ctypes on the
+        driver's libnvidia-ml (no Python NVML package required)."""
+        SM = 1   # NVML_CLOCK_SM
+        # clock-event reason bits: hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap
+        BITS = [0x8, 0x40, 0x20, 0x4]
+
+        def __init__(self, index):
+            import ctypes
+            self.c = ctypes
+            self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.lib.nvmlInit_v2() != 0:
+                raise RuntimeError("nvmlInit failed")
+            self.h = ctypes.c_void_p()
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+                raise RuntimeError("no NVML handle")
+            self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+        def _u(self, fn, *args):
+            v = self.c.c_uint()
+            if fn(self.h, *args, self.c.byref(v)) != 0:
+                raise RuntimeError("NVML query failed")
+            return v.value
+
+        def sm_clock(self):
+            return self._u(self.lib.nvmlDeviceGetClockInfo, self.c.c_int(self.SM))
+
+        def sm_max_clock(self):
+            return self._u(self.lib.nvmlDeviceGetMaxClockInfo, self.c.c_int(self.SM))
+
+        def power_w(self):
+            return self._u(self.lib.nvmlDeviceGetPowerUsage) / 1000.0
+
+        def reasons(self):
+            v = self.c.c_ulonglong()
+            if self.reasons_fn(self.h, self.c.byref(v)) != 0:
+                raise RuntimeError("NVML query failed")
+            return v.value
+
+    def _nvml_loop(self, nv, stop):
+        smax = nv.sm_max_clock()
+        while not stop.is_set():
+            try:
+                sm, rs, pw = nv.sm_clock(), nv.reasons(), nv.power_w()
+                self.rows.append((float(sm), float(smax), ["Active" if rs & b else "Not Active" for b in nv.BITS], pw))
+            except Exception:
+                pass
+            stop.wait(0.01)
+
     def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        self.rows = []
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            import threading
+            nv = self._Nvml(self._nvml_index())
+            self.stop_ev = threading.Event()
+            self.thread = threading.Thread(target=self._nvml_loop, args=(nv, self.stop_ev), daemon=True)
+            self.thread.start()
+            return
+        except Exception:
+            self.thread = None
+        try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -137,29 +211,37 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
-        if self.proc is None:
-            return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.f.close()
         rows = []
-        for line in open(self.path):
-            t = [x.strip() for x in line.split(",")]
-            if len(t) < 9:
-                continue
+        source = "nvml"
+        if self.thread is not None:
+            self.stop_ev.set()
+            self.thread.join(timeout=5)
+            rows = [(r[0], r[1], r[2]) for r in self.rows]
+            with open(self.path, "w") as f:
+                f.write("sm_mhz,sm_max_mhz,hw_slowdown,hw_thermal_slowdown,sw_thermal_slowdown,sw_power_cap,power_w\n")
+                for r in self.rows:
+                    f.write(",".join([str(r[0]), str(r[1])] + r[2] + [f"{r[3]:.1f}"]) + "\n")
+        elif self.proc is not None:
+            source = "nvidia-smi"
+            self.proc.terminate()
             try:
-                rows.append((float(t[1]), float(t[2]), t[5:9]))
-            except ValueError:
-                continue
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+            for line in open(self.path):
+                t = [x.strip() for x in line.split(",")]
+                if len(t) < 9:
+                    continue
+                try:
+                    rows.append((float(t[1]), float(t[2]), t[5:9]))
+                except ValueError:
+                    continue
         if not rows:
             return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        reasons = sorted({self.NAMES[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
         return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "source": source}
 
 
 # ------------------------------------------------------------------ helpers

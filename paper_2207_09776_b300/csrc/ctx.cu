@@ -203,14 +203,18 @@ extern "C" msk_status msk_solve_magnus(msk_ctx* ctx, int order, int steps, int64
   cudaStream_t s = (cudaStream_t)stream;
   st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
   if (st != MSK_OK) return st;
+  // scratch: functionals, weights, then the path order and queue counter of the engine
   const size_t nF = (size_t)paths * steps * MSK_NF, nW = (size_t)paths * steps * MSK_NWT;
-  st = msk_ensure_scratch(ctx, (nF + nW) * sizeof(double));
+  st = msk_ensure_scratch(ctx, (nF + nW + (size_t)paths + 1) * sizeof(double));
   if (st != MSK_OK) return st;
   double* F = reinterpret_cast<double*>(ctx->scratch);
   double* Wt = F + nF;
+  long long* order_buf = reinterpret_cast<long long*>(Wt + nW);
+  unsigned long long* queue = reinterpret_cast<unsigned long long*>(order_buf + paths);
   st = launch_brownian(ctx, steps, paths, F, false, s, precision == MSK_F32);
   if (st == MSK_OK) st = launch_omega(ctx, order, steps, paths, precision, F, Wt, s);
-  if (st == MSK_OK) st = launch_engine(ctx, false, steps, paths, precision, Wt, nullptr, u_out_dev, path_status_dev, s);
+  if (st == MSK_OK)
+    st = launch_magnus_queued(ctx, steps, paths, precision, Wt, u_out_dev, path_status_dev, s, order_buf, queue);
   return st;
 }
 

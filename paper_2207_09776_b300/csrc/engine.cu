@@ -6,7 +6,10 @@ extern const double kMskScaleCap;
 
 namespace {
 
-template <typename T, int D, int C, int NT, bool EULER>
+// The dynamic-queue kernels keep the next path index in 16 bytes past the slab.
+__host__ __device__ constexpr size_t queue_slot_offset(size_t slab) { return (slab + 15) / 16 * 16; }
+
+template <typename T, int D, int C, int NT, bool EULER, bool QUEUE>
 __global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -18,6 +21,22 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineArgs a) {
     const ClusterSync sync;
     slab_init<T, D, C, NT>(sm, tid, rank, sync);
     for (int64_t path = cid; path < a.paths; path += ncl) solve_path<T, D, C, NT, EULER>(a, path, sm, tid, rank, sync);
+  } else if constexpr (QUEUE) {
+    // dynamic assignment: queue position q -> path order[q]
+    const CtaSync sync;
+    slab_init<T, D, C, NT>(sm, tid, rank, sync);
+    // the next path lives just past the slab (launch_one adds 16 bytes of dynamic shared memory)
+    volatile long long* next_path = reinterpret_cast<long long*>(smem_raw + queue_slot_offset(Cfg<T, D, C, NT>::SMEM));
+    for (;;) {
+      if (tid == 0) {
+        const unsigned long long q = atomicAdd(a.queue, 1ull);
+        *next_path = q < (unsigned long long)a.paths ? a.order[q] : -1;
+      }
+      sync();
+      const long long path = *next_path;   // rewritten only after solve_path's closing barrier
+      if (path < 0) break;
+      solve_path<T, D, C, NT, EULER>(a, path, sm, tid, rank, sync);
+    }
   } else {
     const CtaSync sync;
     slab_init<T, D, C, NT>(sm, tid, rank, sync);
@@ -25,12 +44,82 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineArgs a) {
   }
 }
 
+// Counting sort of the paths by decreasing estimated cost sum_n s_n m_n, in one
+// block: histogram of the (capped) costs in shared memory, a block-wide
+// exclusive scan, then a scatter.  Paths of equal cost keep no particular order
+// (the solution of a path does not depend on which CTA solves it).
+constexpr int kOrderBuckets = 4096;
+constexpr int kOrderThreads = 1024;
+
+__device__ __forceinline__ int order_bucket(const double* Wt, int steps, int64_t p) {
+  double c = 0.0;
+  for (int n = 0; n < steps; ++n) {
+    const double* o = Wt + ((size_t)p * steps + n) * MSK_NWT;
+    c += o[MSK_WT_S] * o[MSK_WT_M];
+  }
+  const int ci = c < (double)(kOrderBuckets - 1) ? (int)c : kOrderBuckets - 1;   // NaN -> cap
+  return kOrderBuckets - 1 - ci;   // costliest first
+}
+
+__global__ void __launch_bounds__(kOrderThreads) path_order_kernel(const double* Wt, int steps, int64_t paths,
+                                                                   long long* order, unsigned long long* queue) {
+  __shared__ int cnt[kOrderBuckets];
+  __shared__ int wsum[kOrderThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < kOrderBuckets; i += kOrderThreads) cnt[i] = 0;
+  __syncthreads();
+  for (int64_t p = tid; p < paths; p += kOrderThreads) atomicAdd(&cnt[order_bucket(Wt, steps, p)], 1);
+  __syncthreads();
+  // exclusive scan: each thread owns kOrderBuckets / kOrderThreads consecutive buckets
+  constexpr int PER = kOrderBuckets / kOrderThreads;
+  int local[PER], tot = 0;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    local[j] = cnt[tid * PER + j];
+    tot += local[j];
+  }
+  int incl = tot;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += v;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int v = lane < kOrderThreads / 32 ? wsum[lane] : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, off);
+      if (lane >= off) v += u;
+    }
+    if (lane < kOrderThreads / 32) wsum[lane] = v;   // inclusive over warps
+  }
+  __syncthreads();
+  int base = incl - tot + (warp > 0 ? wsum[warp - 1] : 0);
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    cnt[tid * PER + j] = base;
+    base += local[j];
+  }
+  __syncthreads();
+  for (int64_t p = tid; p < paths; p += kOrderThreads) {
+    const int pos = atomicAdd(&cnt[order_bucket(Wt, steps, p)], 1);
+    order[pos] = p;
+  }
+  if (tid == 0) *queue = 0ull;
+}
+
 template <typename T, int D, int C, int NT, bool EULER>
 msk_status launch_one(msk_ctx* ctx, const EngineArgs& a, cudaStream_t stream) {
   using K = Cfg<T, D, C, NT>;
-  auto kern = engine_kernel<T, D, C, NT, EULER>;
+  // the dynamic path queue exists for single-CTA Magnus configurations only
+  constexpr bool kQ = C == 1 && !EULER;
+  const bool queued = kQ && a.queue;
+  auto kern = queued ? engine_kernel<T, D, C, NT, EULER, kQ> : engine_kernel<T, D, C, NT, EULER, false>;
+  const size_t smem = queued ? queue_slot_offset(K::SMEM) + 16 : K::SMEM;
   msk_status st = msk_cuda(
-      ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM),
+      ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
       "smem attribute");
   if (st != MSK_OK) return st;
   if (C > 8) {
@@ -41,7 +130,7 @@ msk_status launch_one(msk_ctx* ctx, const EngineArgs& a, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   cfg.blockDim = dim3(NT, 1, 1);
-  cfg.dynamicSmemBytes = K::SMEM;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
   int64_t clusters = 0;
   if (C > 1) {
@@ -59,7 +148,7 @@ msk_status launch_one(msk_ctx* ctx, const EngineArgs& a, cudaStream_t stream) {
     clusters = nc;
   } else {
     int per_sm = 0;
-    st = msk_cuda(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, K::SMEM),
+    st = msk_cuda(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem),
                   "occupancy");
     if (st != MSK_OK) return st;
     if (per_sm < 1) return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "kernel does not fit on an SM");
@@ -110,6 +199,27 @@ msk_status launch_em_table(msk_ctx* ctx, int steps, double* em_d, float* em_f, c
   return msk_cuda(ctx, cudaGetLastError(), "euler table");
 }
 
+msk_status launch_path_order(msk_ctx* ctx, const double* Wt, int steps, int64_t paths, long long* order,
+                             unsigned long long* queue, cudaStream_t stream) {
+  if (paths > (int64_t)INT32_MAX) return msk_fail(ctx, MSK_ERR_ARG, "too many paths for the path queue");
+  path_order_kernel<<<1, kOrderThreads, 0, stream>>>(Wt, steps, paths, order, queue);
+  return msk_cuda(ctx, cudaGetLastError(), "path order");
+}
+
+msk_status launch_magnus_queued(msk_ctx* ctx, int steps, int64_t paths, int precision, const double* Wt, void* out,
+                                uint32_t* status, cudaStream_t stream, long long* order_buf,
+                                unsigned long long* queue) {
+  EngineSnap x;
+  // the queue pays off once every CTA solves several paths of unequal cost
+  if (order_buf && queue && paths > 2 * (int64_t)ctx->num_sms && !ctx->xprof && !ctx->gen) {
+    msk_status st = launch_path_order(ctx, Wt, steps, paths, order_buf, queue, stream);
+    if (st != MSK_OK) return st;
+    x.order = order_buf;
+    x.queue = queue;
+  }
+  return launch_engine_ex(ctx, false, steps, paths, precision, Wt, nullptr, out, status, stream, x);
+}
+
 msk_status launch_engine(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
                          const double* Wt, const double* dW, void* out, uint32_t* status,
                          cudaStream_t stream) {
@@ -130,6 +240,8 @@ msk_status launch_engine_ex(msk_ctx* ctx, bool euler, int steps, int64_t paths, 
   a.u0_self = x.u0_self;
   a.em_d = x.em_d;
   a.em_f = x.em_f;
+  a.order = x.order;
+  a.queue = x.queue;
   a.band = ctx->band;
   a.u0 = ctx->u0;
   a.Wt = Wt;

@@ -69,6 +69,12 @@ struct EngineArgs {
   const float* em_f;
   uint32_t* status;
   unsigned long long* work;
+  // Optional dynamic path queue (single-CTA configurations): CTAs take queue
+  // positions q = 0, 1, ... by an atomic counter and solve path order[q]; order
+  // lists the paths by decreasing estimated cost, so the last paths handed out
+  // are the cheapest (longest-processing-time-first).  Null: static striding.
+  const long long* order;
+  unsigned long long* queue;
   int64_t paths;
   int steps;
   double dx, T, s_cap;
@@ -186,6 +192,10 @@ template <typename T> struct RowCoef { T a0, a1, a2, a3, a4, b0, b1, b2, c0, c1,
 // thread-block cluster, or one named barrier over a subset of a CTA's warps.
 // operator() spans every thread that shares the slab; local() the threads of
 // the calling CTA (or of the named group) that share the per-step tables.
+// The D^x-class operators (their V1 centre varies over the interior rows).
+__constant__ int c_dx_ops[6] = {MSK_OP_BX, MSK_OP_BX_A0, MSK_OP_BX_BVV, MSK_OP_BXA0_A0, MSK_OP_BXA0_BVV,
+                                MSK_OP_BVVA0_BX};
+
 struct CtaSync {
   __device__ __forceinline__ void operator()() const { __syncthreads(); }
   __device__ __forceinline__ void local() const { __syncthreads(); }
@@ -433,11 +443,9 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
         fold_row(a.band, D, jr, wv, 0.0, inv2dx, inv4dx2, cf);
         for (int q = 0; q < MSK_NCOEF; ++q) eu[(size_t)e * MSK_NCOEF + q] = (T)cf[q];
       }
-      constexpr int dx[K::NDX] = {MSK_OP_BX, MSK_OP_BX_A0, MSK_OP_BX_BVV, MSK_OP_BXA0_A0, MSK_OP_BXA0_BVV,
-                                  MSK_OP_BVVA0_BX};
       for (int e = tid; e < K::NDX * RS; e += NT) {
         const int c = e / RS, jl = e % RS;
-        bu[e] = (T)(a.band[((size_t)dx[c] * D + r0 + jl) * MSK_BAND + 2] * inv2dx);
+        bu[e] = (T)(a.band[((size_t)c_dx_ops[c] * D + r0 + jl) * MSK_BAND + 2] * inv2dx);
       }
       sync_all.local();
     }

@@ -100,7 +100,21 @@ struct EngineSnap {
   // Euler-Maruyama: alpha(t_n) dt and sigma(t_n) per step ([steps][2], double and float)
   const double* em_d = nullptr;
   const float* em_f = nullptr;
+  // Magnus solves on one CTA per path: the path order and queue counter written by
+  // launch_path_order (null: static assignment of paths to CTAs)
+  const long long* order = nullptr;
+  unsigned long long* queue = nullptr;
 };
+// Order the paths by decreasing estimated Taylor cost sum_n s_n m_n (from the
+// records Wt) into order[paths] and reset *queue to 0, for the engine's dynamic queue.
+msk_status launch_path_order(msk_ctx* ctx, const double* Wt, int steps, int64_t paths, long long* order,
+                             unsigned long long* queue, cudaStream_t stream);
+// The Magnus engine from the records Wt, with the paths ordered by decreasing
+// estimated cost and handed out by a queue when that pays off (order_buf:
+// paths entries, queue: one counter; both scratch; null: static assignment).
+msk_status launch_magnus_queued(msk_ctx* ctx, int steps, int64_t paths, int precision, const double* Wt, void* out,
+                                uint32_t* status, cudaStream_t stream, long long* order_buf,
+                                unsigned long long* queue);
 // Fill the Euler table of `steps` steps: em_d[2n] = alpha(t_n) dt, em_d[2n+1] = sigma(t_n), em_f the same in float.
 msk_status launch_em_table(msk_ctx* ctx, int steps, double* em_d, float* em_f, cudaStream_t stream);
 msk_status launch_engine_ex(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,

@@ -409,14 +409,17 @@ msk_status reference_solve(msk_surrogate* s, uint64_t first, uint64_t stride, in
   for (int64_t o = 0; o < paths; o += kRefChunk) {
     const int64_t P = std::min<int64_t>(kRefChunk, paths - o);
     const size_t nF = (size_t)P * steps * MSK_NF, nW = (size_t)P * steps * MSK_NWT;
-    msk_status st = sgrow(s, &s->rs, &s->rs_bytes, (nF + nW) * sizeof(double), "reference scratch");
+    msk_status st = sgrow(s, &s->rs, &s->rs_bytes, (nF + nW + (size_t)P + 1) * sizeof(double), "reference scratch");
     if (st != MSK_OK) return st;
     double* F = reinterpret_cast<double*>(s->rs);
     double* Wt = F + nF;
+    long long* order_buf = reinterpret_cast<long long*>(Wt + nW);
+    unsigned long long* queue = reinterpret_cast<unsigned long long*>(order_buf + P);
     st = from_ctx(s, launch_brownian_strided(ctx, steps, P, F, first + (uint64_t)o * stride, stride, stream, true));
     if (st == MSK_OK) st = from_ctx(s, launch_omega(ctx, order, steps, P, MSK_F32, F, Wt, stream));
     if (st == MSK_OK)
-      st = from_ctx(s, launch_engine(ctx, false, steps, P, MSK_F32, Wt, nullptr, U + (size_t)o * s->n, nullptr, stream));
+      st = from_ctx(s, launch_magnus_queued(ctx, steps, P, MSK_F32, Wt, U + (size_t)o * s->n, nullptr, stream,
+                                            order_buf, queue));
     if (st != MSK_OK) return st;
   }
   return MSK_OK;

@@ -224,6 +224,22 @@ def test_solve_with_host_buffers(precision, tol):
     s.close()
 
 
+@pytest.mark.parametrize("precision", [msk.MSK_F32, msk.MSK_F64])
+def test_dynamic_path_queue_matches_static_assignment(precision):
+    """Above two paths per SM the engine hands out paths from an atomic queue in
+    order of decreasing estimated cost; every path's solution must be identical
+    (bit for bit) to the static assignment used for small path counts."""
+    w = LANGEVIN_TRIG_128.with_(d=64, paths=700, n_fine=1024)
+    s = solver(w)
+    full = s.magnus(3, 8, precision=precision).cpu().numpy()        # 700 paths: queued
+    parts = []
+    for lo, hi in ((0, 250), (250, 500), (500, 700)):                # <= 2 per SM: static
+        msk.msk_set_seed(s.ctx, w.seed, lo, w.n_fine, w.T)
+        parts.append(s.magnus(3, 8, paths=hi - lo, precision=precision).cpu().numpy())
+    np.testing.assert_array_equal(full, np.concatenate(parts))
+    s.close()
+
+
 def test_euler_parity():
     w = LANGEVIN_32.with_(paths=6)
     s = solver(w)
