@@ -114,7 +114,13 @@ struct Cfg {
   static constexpr size_t OFF_BU = OFF_EU + (size_t)MSK_NOPS * 5 * MSK_NCOEF;   // NDX x RS
   static constexpr size_t OFF_END = OFF_BU + (size_t)NDX * RS;
   static constexpr size_t OFF_ACC = (OFF_END + 3) / 4 * 4;
-  static constexpr size_t NELEM = ACC_SMEM ? OFF_ACC + (size_t)RS * D : OFF_END;
+  // Single-CTA slabs also keep each step's interior-row coefficients pre-scaled by
+  // 1/(s k) for every term k (16 slots: the twelve coefficients, padded for vector
+  // loads), so a Taylor term loads them instead of scaling them.
+  static constexpr size_t OFF_KC = (OFF_END + 3) / 4 * 4;                 // (kMaxTerms + 1) x 16
+  static constexpr size_t END_KTAB = OFF_KC + (size_t)(kMaxTerms + 1) * 16;
+  static constexpr bool KTAB = !ACC_SMEM && END_KTAB * sizeof(T) <= 232448;
+  static constexpr size_t NELEM = ACC_SMEM ? OFF_ACC + (size_t)RS * D : (KTAB ? END_KTAB : OFF_END);
   static constexpr size_t SMEM = NELEM * sizeof(T);
   static_assert(SMEM <= 232448, "slab does not fit the 227 KB of shared memory per CTA");
 };
@@ -516,6 +522,15 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
         }
       }
       sync_all.local();
+      if constexpr (K::KTAB && !EULER) {
+        // the step's coefficients scaled for each term k = 1 .. m
+        T* kc = sm + K::OFF_KC;
+        for (int e = tid; e < (m_terms + 1) * 16; e += NT) {
+          const int k = e >> 4, q = e & 15;
+          kc[e] = q < MSK_NCOEF ? coef[4 * MSK_NCOEF + q] * scale_tab[k] : T(0);
+        }
+        sync_all.local();
+      }
       T te = T(1);
       if constexpr (!EULER) {
         if constexpr (sizeof(T) == 4) te = (T)expf(-(float)wT[MSK_NOPS] / (float)s_steps);
@@ -543,7 +558,15 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
                     q[CF_B + 0] * sc, q[CF_B + 1] * sc, q[CF_B + 2] * sc, q[CF_C + 0] * sc, q[CF_C + 1] * sc,
                     edgeL ? e1 : a1, edgeL ? e3 : a3, edgeR ? e1 : a1, edgeR ? e3 : a3};
           };
-          const RowCoef<T> ci = make(coef + 4 * MSK_NCOEF);
+          RowCoef<T> ci;
+          if constexpr (K::KTAB && !EULER) {
+            const T* kc = sm + K::OFF_KC + k * 16;
+            const V4<T> q0 = ld4(kc), q1 = ld4(kc + 4), q2 = ld4(kc + 8);
+            ci = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y,
+                  edgeL ? q2.z : q0.y, edgeL ? q2.w : q0.w, edgeR ? q2.z : q0.y, edgeR ? q2.w : q0.w};
+          } else {
+            ci = make(coef + 4 * MSK_NCOEF);
+          }
           const int nxt = cur ^ 1;
           const T* src = sm + cur * K::BUF;
           T mn = T(0), ma = T(0);
