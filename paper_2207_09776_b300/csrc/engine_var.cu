@@ -80,24 +80,37 @@ struct VarArgs {
   const float* em_f;
   int64_t paths;
   int steps, d, C, RS, ng, R;
+  int pitch;   // shared-memory row pitch of the fields and the partial sum (var_pitch)
   double dx, dv, av, kappa, T, s_cap;
   float tol32;
   double tol64;
   CoefDev c;
 };
 
+// Row pitch W >= d + pad of the shared fields and partial sum.  Threads take
+// (row group, column) pairs in group-major order, so a warp can span the end of
+// group g and the start of group g + 1, whose rows lie R rows apart; with
+// R W = d (mod 32) the two parts of such a warp fall on distinct banks (every
+// lane's word is its thread index modulo 32 away from a common base).
+__host__ __device__ inline int var_pitch(int d, int R, int ng, int pad) {
+  if (ng > 1)
+    for (int W = d + pad; W < d + pad + 32; ++W)
+      if ((R * W - d) % 32 == 0) return W;
+  return d + pad;
+}
+
 // Shared memory of one CTA in elements of T: three fields of (RS + 4) x W
-// (W = d + 4), the partial sum [RS][d], the per-row Bx coefficient of the rows
-// -2 .. RS+1, 1/(s k), and the norm slots.  (All offsets fit 32 bits: the
-// layout is capped at 227 KB.)
+// (W = var_pitch(d, R, ng, 4)), the partial sum [RS][W], the per-row Bx
+// coefficient of the rows -2 .. RS+1, 1/(s k), and the norm slots.  (All
+// offsets fit 32 bits: the layout is capped at 227 KB.)
 struct VarLayout {
   int FS, off_acc, off_cx, off_scale, off_slot, off_cslot, total;
 };
-__host__ __device__ inline VarLayout var_layout(int RS, int d, int NT, int nfields) {
+__host__ __device__ inline VarLayout var_layout(int RS, int W, int NT, int nfields) {
   VarLayout L;
-  L.FS = (RS + 4) * (d + 4);
+  L.FS = (RS + 4) * W;
   L.off_acc = nfields * L.FS;
-  L.off_cx = L.off_acc + RS * d;
+  L.off_cx = L.off_acc + RS * W;
   L.off_scale = L.off_cx + RS + 4;
   L.off_slot = L.off_scale + kVarMaxTerms + 1;
   L.off_cslot = L.off_slot + 4 * (NT / 32);
@@ -211,9 +224,9 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, NT = blockDim.x, NW = NT >> 5;
   const int lane = tid & 31, warp = tid >> 5;
-  const int C = a.C, RS = a.RS, d = a.d, W = d + 4;
+  const int C = a.C, RS = a.RS, d = a.d, W = a.pitch;
   const int rank = C > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  const VarLayout L = var_layout(RS, d, NT, NF);
+  const VarLayout L = var_layout(RS, W, NT, NF);
   const int FS = L.FS;
   T* accs = sm + L.off_acc;
   T* cxr = sm + L.off_cx + 2;   // cxr[p], p in [-2, RS + 1]
@@ -294,7 +307,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
       const int p = p0 + r;
       const size_t g = (size_t)(r0 + p) * d + col;
       const T v = self0 ? self0[g] : (T)a.u0[g];
-      accs[p * d + col] = v;
+      accs[p * W + col] = v;
       store(ft, p, v, 2);
       m0 = vmax(m0, vabsnan(v));
     }
@@ -312,7 +325,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
       const int q0 = a.snap_first[n], nq = a.snap_cnt[n];
       for (int q = q0; q < q0 + nq; ++q) {
         T* dst = reinterpret_cast<T*>(a.snap) + ((size_t)path * a.n_out + q) * d * d;
-        for (int r = 0; r < nrows; ++r) dst[(size_t)(r0 + p0 + r) * d + col] = accs[(p0 + r) * d + col];
+        for (int r = 0; r < nrows; ++r) dst[(size_t)(r0 + p0 + r) * d + col] = accs[(p0 + r) * W + col];
       }
     };
     for (int n = 0; n < a.steps; ++n) {
@@ -330,7 +343,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
             const T dn = t[o + W], l = t[o - 1], rr = t[o + 1];
             const T tn_ = fma(kx * cxr[p0 + r], rr - l, fma(kv, fma(T(-2), ce, dn + up), fma(ka, dn - up, ce)));
             store(fo, p0 + r, tn_, 2);
-            accs[(p0 + r) * d + col] = tn_;
+            accs[(p0 + r) * W + col] = tn_;
             up = ce;
             ce = dn;
           }
@@ -506,7 +519,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
                   const T tot = fma(ca, ad - au, fma(cvv, fma(T(-2), vc, vd + vu), Xp));
                   const T tn_ = fma(sc, tot, -scmu * t[o]);
                   store(FT, p, tn_, 2);
-                  T& acc_ = accs[p * d + col];
+                  T& acc_ = accs[p * W + col];
                   const T s_ = acc_ + tn_;
                   acc_ = s_;
                   mn = vmax(mn, fabs(tn_));
@@ -528,7 +541,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
                 const T Bp = fma(cxr[p], pr - pl, cvB * fma(T(-2), pc, pd + pu));
                 const T tn_ = fma(sc, fma(ca, qd - qu, Bp), -scmu * t[o]);
                 store(FT, p, tn_, 2);
-                T& ac = accs[p * d + col];
+                T& ac = accs[p * W + col];
                 const T s_ = ac + tn_;
                 ac = s_;
                 mn = vmax(mn, fabs(tn_));
@@ -551,7 +564,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
           }
           // u <- e^{mu/s} (partial sum), which is also the next sub-step's t
           for (int r = 0; r < nrows; ++r) {
-            T& ac = accs[(p0 + r) * d + col];
+            T& ac = accs[(p0 + r) * W + col];
             const T v = ac * te;
             ac = v;
             store(FT, p0 + r, v, 2);
@@ -566,7 +579,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
     // ---- solution, work counter and path status
     T mfin = T(0);
     for (int r = 0; r < nrows; ++r) {
-      const T v = accs[(p0 + r) * d + col];
+      const T v = accs[(p0 + r) * W + col];
       if (a.out) reinterpret_cast<T*>(a.out)[(size_t)path * d * d + (size_t)(r0 + p0 + r) * d + col] = v;
       mfin = vmax(mfin, vabsnan(v));
     }
@@ -601,11 +614,11 @@ constexpr int kGenFields = 5;
 struct GenLayout {
   int FS, off_acc, off_scale, off_slot, off_cslot, total;
 };
-__host__ __device__ inline GenLayout gen_layout(int RS, int d, int NT) {
+__host__ __device__ inline GenLayout gen_layout(int RS, int W, int NT) {
   GenLayout L;
-  L.FS = (RS + 2) * (d + 2);
+  L.FS = (RS + 2) * W;
   L.off_acc = kGenFields * L.FS;
-  L.off_scale = L.off_acc + RS * d;
+  L.off_scale = L.off_acc + RS * W;
   L.off_slot = L.off_scale + kVarMaxTerms + 1;
   L.off_cslot = L.off_slot + 4 * (NT / 32);
   L.total = L.off_cslot + 4;
@@ -618,9 +631,9 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int tid = threadIdx.x, NT = blockDim.x, NW = NT >> 5;
   const int lane = tid & 31, warp = tid >> 5;
-  const int C = a.C, RS = a.RS, d = a.d, W = d + 2;
+  const int C = a.C, RS = a.RS, d = a.d, W = a.pitch;
   const int rank = C > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  const GenLayout L = gen_layout(RS, d, NT);
+  const GenLayout L = gen_layout(RS, W, NT);
   const int FS = L.FS;
   T* accs = sm + L.off_acc;
   T* scale_tab = sm + L.off_scale;
@@ -693,7 +706,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
       const int p = p0 + r;
       const size_t g = (size_t)(r0 + p) * d + col;
       const T v = self0 ? self0[g] : (T)a.u0[g];
-      accs[p * d + col] = v;
+      accs[p * W + col] = v;
       store(ft, p, v);
       m0 = vmax(m0, vabsnan(v));
     }
@@ -709,7 +722,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
       const int q0 = a.snap_first[n], nq = a.snap_cnt[n];
       for (int q = q0; q < q0 + nq; ++q) {
         T* dst = reinterpret_cast<T*>(a.snap) + ((size_t)path * a.n_out + q) * dd;
-        for (int r = 0; r < nrows; ++r) dst[(size_t)(r0 + p0 + r) * d + col] = accs[(p0 + r) * d + col];
+        for (int r = 0; r < nrows; ++r) dst[(size_t)(r0 + p0 + r) * d + col] = accs[(p0 + r) * W + col];
       }
     };
 
@@ -723,7 +736,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
           const int p = p0 + r, o = off(p), g = (r0 + p) * d + col;
           const T tn_ = fma(kt, applyB(t, o, g), fma(kw, applyA(t, o, g), t[o]));
           store(fa, p, tn_);
-          accs[p * d + col] = tn_;
+          accs[p * W + col] = tn_;
         }
         sync_all();
         const int sw = ft;
@@ -791,7 +804,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
                 const int p = p0 + r, o = off(p), g = (r0 + p) * d + col;
                 const T tn_ = fma(sc, applyB(Pf, o, g) + applyA(Qf, o, g), -scmu * t[o]);
                 store(fa, p, tn_);
-                T& ac = accs[p * d + col];
+                T& ac = accs[p * W + col];
                 const T s_ = ac + tn_;
                 ac = s_;
                 mn = vmax(mn, fabs(tn_));
@@ -812,7 +825,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
             c1n = gn;
           }
           for (int r = 0; r < nrows; ++r) {
-            T& ac = accs[(p0 + r) * d + col];
+            T& ac = accs[(p0 + r) * W + col];
             const T v = ac * te;
             ac = v;
             store(fa, p0 + r, v);
@@ -829,7 +842,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
     snapshot(a.steps);
     T mfin = T(0);
     for (int r = 0; r < nrows; ++r) {
-      const T v = accs[(p0 + r) * d + col];
+      const T v = accs[(p0 + r) * W + col];
       if (a.out) reinterpret_cast<T*>(a.out)[(size_t)path * dd + (size_t)(r0 + p0 + r) * d + col] = v;
       mfin = vmax(mfin, vabsnan(v));
     }
@@ -1066,7 +1079,7 @@ __global__ void psi_rational_kernel(int d, double ax, double dx, double c, doubl
 
 // ------------------------------------------------------------------ launch planning
 struct VarPlan {
-  int C = 0, RS = 0, ng = 0, R = 0, NT = 0, clusters = 0;
+  int C = 0, RS = 0, ng = 0, R = 0, NT = 0, pitch = 0, clusters = 0;
   size_t smem = 0;
 };
 
@@ -1112,9 +1125,15 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
     const int ng = std::max(1, std::min(kVarMaxThreads / d, RS / 2));
     const int R = (RS + ng - 1) / ng;
     const int NT = 32 * ((ng * d + 31) / 32);
-    const int total = MODE == kModeGen ? gen_layout(RS, d, NT).total
-                                       : var_layout(RS, d, NT, MODE == kModeSplit ? kVarFields + 1 : kVarFields).total;
-    const size_t smem = (size_t)total * sizeof(T);
+    // the bank-aligned pitch where it fits, else the plain one (same cluster size)
+    const int pad = MODE == kModeGen ? 2 : 4;
+    auto total_of = [&](int W) {
+      return MODE == kModeGen ? gen_layout(RS, W, NT).total
+                              : var_layout(RS, W, NT, MODE == kModeSplit ? kVarFields + 1 : kVarFields).total;
+    };
+    int W = var_pitch(d, R, ng, pad);
+    if ((size_t)total_of(W) * sizeof(T) > kVarSmemCap) W = d + pad;
+    const size_t smem = (size_t)total_of(W) * sizeof(T);
     if (smem > kVarSmemCap) continue;
     int clusters = 0;
     if (C == 1) {
@@ -1148,6 +1167,7 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
     p.ng = ng;
     p.R = R;
     p.NT = NT;
+    p.pitch = W;
     p.clusters = clusters;
     p.smem = smem;
     cands.push_back(p);
@@ -1175,6 +1195,7 @@ msk_status launch_var_typed(msk_ctx* ctx, VarArgs a, int64_t paths, cudaStream_t
   a.RS = pl.RS;
   a.ng = pl.ng;
   a.R = pl.R;
+  a.pitch = pl.pitch;
   const int64_t clusters = std::min<int64_t>(pl.clusters, paths);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
