@@ -211,7 +211,7 @@ msk_status launch_magnus_queued(msk_ctx* ctx, int steps, int64_t paths, int prec
                                 unsigned long long* queue) {
   EngineSnap x;
   // the queue pays off once every CTA solves several paths of unequal cost
-  if (order_buf && queue && paths > 2 * (int64_t)ctx->num_sms && !ctx->xprof && !ctx->gen) {
+  if (order_buf && queue && paths > 2 * (int64_t)ctx->num_sms) {
     msk_status st = launch_path_order(ctx, Wt, steps, paths, order_buf, queue, stream);
     if (st != MSK_OK) return st;
     x.order = order_buf;

@@ -78,6 +78,10 @@ struct VarArgs {
   const void* gA;
   const double* em_d;  // Euler: alpha(t_n) dt, sigma(t_n) per step (double / float)
   const float* em_f;
+  // Magnus: optional dynamic path queue (positions q = 0, 1, ... of an atomic
+  // counter map to paths order[q], costliest first); null: static striding
+  const long long* order;
+  unsigned long long* queue;
   int64_t paths;
   int steps, d, C, RS, ng, R;
   int pitch;   // shared-memory row pitch of the fields and the partial sum (var_pitch)
@@ -104,7 +108,7 @@ __host__ __device__ inline int var_pitch(int d, int R, int ng, int pad) {
 // coefficient of the rows -2 .. RS+1, 1/(s k), and the norm slots.  (All
 // offsets fit 32 bits: the layout is capped at 227 KB.)
 struct VarLayout {
-  int FS, off_acc, off_cx, off_scale, off_slot, off_cslot, total;
+  int FS, off_acc, off_cx, off_scale, off_slot, off_cslot, off_q, total;
 };
 __host__ __device__ inline VarLayout var_layout(int RS, int W, int NT, int nfields) {
   VarLayout L;
@@ -114,7 +118,8 @@ __host__ __device__ inline VarLayout var_layout(int RS, int W, int NT, int nfiel
   L.off_scale = L.off_cx + RS + 4;
   L.off_slot = L.off_scale + kVarMaxTerms + 1;
   L.off_cslot = L.off_slot + 4 * (NT / 32);
-  L.total = L.off_cslot + 4;
+  L.off_q = (L.off_cslot + 4 + 1) / 2 * 2;   // the cluster's next path (8 bytes)
+  L.total = L.off_q + 2;
   return L;
 }
 
@@ -140,6 +145,34 @@ __device__ __forceinline__ double cl_ld(uint32_t addr, double) {
   double v;
   asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
   return v;
+}
+__device__ __forceinline__ long long cl_ld_s64(uint32_t addr) {
+  long long v;
+  asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// The next path of this cluster: static striding (path += ncl), or with a queue
+// rank 0's thread 0 takes a position from the atomic counter and publishes the
+// path in its slot, which every CTA reads after the cluster barrier (the slot is
+// rewritten only after the path's closing barrier; with C > 1 a second barrier
+// follows the remote reads).  -1: no path left.
+template <class Sync>
+__device__ __forceinline__ long long var_next_path(const long long* order, unsigned long long* queue, int64_t paths,
+                                                   long long* slot, int tid, int rank, int C, int64_t static_path,
+                                                   const Sync& sync_all) {
+  if (!queue) return static_path < paths ? static_path : -1;
+  if (rank == 0 && tid == 0) {
+    const unsigned long long q = atomicAdd(queue, 1ull);
+    *reinterpret_cast<volatile long long*>(slot) = q < (unsigned long long)paths ? order[q] : -1;
+  }
+  sync_all();
+  if (C == 1) return *reinterpret_cast<volatile long long*>(slot);
+  const long long path = cl_ld_s64(cl_addr(slot, 0));
+  // no CTA may leave (path -1) while another still reads rank 0's slot remotely:
+  // a CTA's shared memory must not be accessed through the cluster after it exits
+  sync_all();
+  return path;
 }
 
 __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
@@ -299,7 +332,12 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
   constexpr int FT = 0, FP = 1, FQ = 2, FR = 3;
   int par = 0;
 
-  for (int64_t path = cid; path < a.paths; path += ncl) {
+  long long* qslot = reinterpret_cast<long long*>(sm + L.off_q);
+  // (the double engines, used for checks, keep the static assignment and their registers)
+  unsigned long long* queue = (EULER || sizeof(T) == 8) ? nullptr : a.queue;
+  for (int64_t it = cid;; it += ncl) {
+    const int64_t path = var_next_path(a.order, queue, a.paths, qslot, tid, rank, C, it, sync_all);
+    if (path < 0) break;
     int ft = FT, fo = FP;   // Euler ping-pongs t between fields 0 and 1
     T m0 = T(0);
     const T* self0 = a.u0_self ? reinterpret_cast<const T*>(a.out) + (size_t)path * d * d : nullptr;
@@ -612,7 +650,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
 constexpr int kGenFields = 5;
 
 struct GenLayout {
-  int FS, off_acc, off_scale, off_slot, off_cslot, total;
+  int FS, off_acc, off_scale, off_slot, off_cslot, off_q, total;
 };
 __host__ __device__ inline GenLayout gen_layout(int RS, int W, int NT) {
   GenLayout L;
@@ -621,7 +659,8 @@ __host__ __device__ inline GenLayout gen_layout(int RS, int W, int NT) {
   L.off_scale = L.off_acc + RS * W;
   L.off_slot = L.off_scale + kVarMaxTerms + 1;
   L.off_cslot = L.off_slot + 4 * (NT / 32);
-  L.total = L.off_cslot + 4;
+  L.off_q = (L.off_cslot + 4 + 1) / 2 * 2;   // the cluster's next path (8 bytes)
+  L.total = L.off_q + 2;
   return L;
 }
 
@@ -698,7 +737,12 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
   constexpr int FB = 2, FP = 3, FQ = 4;
   int par = 0;
 
-  for (int64_t path = cid; path < a.paths; path += ncl) {
+  long long* qslot = reinterpret_cast<long long*>(sm + L.off_q);
+  // (the double engines, used for checks, keep the static assignment and their registers)
+  unsigned long long* queue = (EULER || sizeof(T) == 8) ? nullptr : a.queue;
+  for (int64_t it = cid;; it += ncl) {
+    const int64_t path = var_next_path(a.order, queue, a.paths, qslot, tid, rank, C, it, sync_all);
+    if (path < 0) break;
     int ft = 0, fa = 1;
     T m0 = T(0);
     const T* self0 = a.u0_self ? reinterpret_cast<const T*>(a.out) + (size_t)path * dd : nullptr;
@@ -1277,6 +1321,8 @@ msk_status launch_engine_var(msk_ctx* ctx, bool euler, int steps, int64_t paths,
   a.u0_self = x.u0_self;
   a.em_d = x.em_d;
   a.em_f = x.em_f;
+  a.order = euler ? nullptr : x.order;
+  a.queue = euler ? nullptr : x.queue;
   a.paths = paths;
   a.steps = steps;
   a.d = ctx->d;

@@ -192,6 +192,23 @@ def test_paper_grids_float_against_double(d, K):
     s.close()
 
 
+@pytest.mark.parametrize("d", [24, 200])
+def test_dynamic_path_queue_matches_static_assignment(d):
+    """More than two paths per SM: the float variable-coefficient engine takes paths
+    from an atomic queue, costliest first (d = 200: rank 0 of each 3-CTA cluster
+    takes them and the other CTAs read the path through distributed shared memory).
+    Every path must equal, bit for bit, the static assignment of smaller batches."""
+    w = PAPER_VAR[0].with_(d=d, paths=320, T=0.1, n_fine=64)
+    s = msk.Solver(w)
+    full = s.magnus(3, 4, precision=msk.MSK_F32).cpu().numpy()
+    parts = []
+    for lo, hi in ((0, 160), (160, 320)):
+        msk.msk_set_seed(s.ctx, w.seed, lo, w.n_fine, w.T)
+        parts.append(s.magnus(3, 4, paths=hi - lo, precision=msk.MSK_F32).cpu().numpy())
+    np.testing.assert_array_equal(full, np.concatenate(parts))
+    s.close()
+
+
 def test_paper_grid_300_float_against_the_oracle():
     """d = 300 (a cluster of 7 CTAs per path in float) on a short horizon."""
     w = PAPER_VAR[2].with_(paths=1, T=0.02, n_fine=200)
