@@ -293,6 +293,7 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
   const bool ldsL = (TPR > 32) && (lane == 0) && hasL;     // left neighbour in another warp
   const bool ldsR = (TPR > 32) && (lane == 31) && hasR;
   const bool edgeL = !hasL, edgeR = !hasR;                 // thread holds column 0 / column d-1
+  const bool top_strip = r0 + j0 == 0, bot_strip = r0 + j0 + R == D;   // strip holds grid rows 0, 1 / d-2, d-1
   const T mL = hasL ? T(1) : T(0), mR = hasR ? T(1) : T(0);
   const double inv2dx = 0.5 / a.dx, inv4dx2 = 0.25 / (a.dx * a.dx);
   const T tol = sizeof(T) == 4 ? (T)a.tol32 : (T)a.tol64;
@@ -578,7 +579,6 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const int p = j0 + r;
-            const int jg = r0 + p;
             const V4<T> cw4 = ld4(src + at(p + 2, i0));
             xterms(cw3, src, p + 1, d12, s22);
             auto stencil = [&](const RowCoef<T>& c) -> V4<T> {
@@ -604,9 +604,13 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
             // The four boundary rows (rows of two warps at most, the branch is warp-uniform)
             // take their own coefficient set; every other row the interior set with its own
             // V1 centre.  Two separate evaluations keep the interior path free of selects.
+            // With r a compile-time index, rows 2 .. R-3 of a strip never test anything: only
+            // the first two rows of the top strip and the last two of the bottom strip are
+            // boundary rows (precomputed per thread), and their class index is a constant.
             V4<T> out;
-            if (__builtin_expect(is_special_row(jg, D), 0)) {
-              out = stencil(make(coef + special_index(jg, D) * MSK_NCOEF));
+            const bool special = (r < 2 && top_strip) || (r >= R - 2 && bot_strip);
+            if (__builtin_expect(special, 0)) {
+              out = stencil(make(coef + (r < 2 && top_strip ? r : 4 - R + r) * MSK_NCOEF));
             } else {
               RowCoef<T> c = ci;
               c.b1 = b0row[p] * sc;
