@@ -227,7 +227,8 @@ msk_status msk_apply_omega(msk_ctx* ctx, const double* weights_dev, int64_t path
  * the Brownian functionals, weights, norm bound and (s, m) in double.
  * u_out_dev: [paths][v][x] of double (MSK_F64) or float (MSK_F32).
  * path_status_dev: optional uint32[paths] of MSK_PATH_* bits (may be NULL).
- * Scratch (functionals and weights) is library-owned and grows on demand. */
+ * Scratch (functionals, weights, the engine's path order) is library-owned
+ * and grows on demand. */
 msk_status msk_solve_magnus(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
                             void* u_out_dev, uint32_t* path_status_dev, void* stream);
 
@@ -252,7 +253,10 @@ msk_status msk_solve_magnus_host(msk_ctx* ctx, int order, int steps, int64_t pat
 /* S5b + S6 only: the iterated Magnus solve from precomputed per-(path, step)
  * records Wt_dev (layout of msk_omega_weights, double[paths * steps * MSK_NWT],
  * caller-owned).  msk_solve_magnus = msk_brownian_functionals +
- * msk_omega_weights + this call, with library-owned scratch. */
+ * msk_omega_weights + this call, with library-owned scratch.  With more than
+ * two paths per SM the paths are solved in order of decreasing estimated cost
+ * sum_n s_n m_n (a path order and a counter in the library's scratch, which
+ * grows on demand); each path's result is independent of that order. */
 msk_status msk_magnus_from_weights(msk_ctx* ctx, int steps, int64_t paths, int precision,
                                    const double* Wt_dev, void* u_out_dev,
                                    uint32_t* path_status_dev, void* stream);

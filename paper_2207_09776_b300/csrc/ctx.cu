@@ -302,8 +302,13 @@ extern "C" msk_status msk_magnus_from_weights(msk_ctx* ctx, int steps, int64_t p
   if (!Wt_dev || !u_out_dev) return msk_fail(ctx, MSK_ERR_ARG, "null buffer");
   st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
   if (st != MSK_OK) return st;
-  return launch_engine(ctx, false, steps, paths, precision, Wt_dev, nullptr, u_out_dev, path_status_dev,
-                       (cudaStream_t)stream);
+  // scratch: the engine's path order and queue counter
+  st = msk_ensure_scratch(ctx, ((size_t)paths + 1) * sizeof(double));
+  if (st != MSK_OK) return st;
+  long long* order_buf = reinterpret_cast<long long*>(ctx->scratch);
+  unsigned long long* queue = reinterpret_cast<unsigned long long*>(order_buf + paths);
+  return launch_magnus_queued(ctx, steps, paths, precision, Wt_dev, u_out_dev, path_status_dev,
+                              (cudaStream_t)stream, order_buf, queue);
 }
 
 extern "C" msk_status msk_work_counter(msk_ctx* ctx, uint64_t* matvecs_host, int reset, void* stream) {
