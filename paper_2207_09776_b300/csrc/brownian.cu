@@ -24,6 +24,8 @@
 // summed over the warp at the end.  The deterministic per-cell values
 // (sigma at cell midpoints, alpha at the nodes, the antiderivative of alpha at
 // the midpoints) come from a table built once per (T, n_fine, coefficients).
+#include <type_traits>
+
 #include "philox.cuh"
 #include "msk_internal.cuh"
 
@@ -88,13 +90,19 @@ __device__ __forceinline__ double warp_excl_scan(double v, int lane) {
 
 template <bool FULL, bool TRIG, bool NF32>
 __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, double* __restrict__ out) {
-  __shared__ double stage[kWarps][32 * kChunk];
+  // staged increments of one round (float in the float solves: half the shared
+  // memory, so more warps fit on an SM)
+  __shared__ typename std::conditional<NF32, float, double>::type stage[kWarps][32 * kChunk];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t idx = (int64_t)blockIdx.x * kWarps + wib;   // (path, step) pair of this warp
-  if (idx >= a.paths * a.steps) return;                     // whole warp leaves together
-  int64_t p = idx / a.steps;
+  const int64_t wi = (int64_t)blockIdx.x * kWarps + wib;    // work item of this warp
+  if (wi >= a.paths * a.steps) return;                      // whole warp leaves together
+  // step-major order: the warps resident at one time work on the same step of
+  // different paths, so the step's slice of the per-cell tables stays in L1
+  const int64_t n_step = wi / a.paths;
+  int64_t p = wi % a.paths;
+  const int64_t idx = p * a.steps + n_step;                 // (path, step) record of this warp
   int64_t L = a.n_fine / a.steps;                           // cells of the step
-  int64_t f0 = (idx % a.steps) * L;                         // first fine cell of the step
+  int64_t f0 = n_step * L;                                  // first fine cell of the step
   if (a.jobs) {
     p = a.jobs[3 * idx];
     f0 = a.jobs[3 * idx + 1];
@@ -106,7 +114,8 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
   const double* tsig = a.tab;
   const double* talp = a.tab + (a.n_fine + 1);
   const double* tA = a.tab + 2 * (a.n_fine + 1);
-  double* st = stage[wib];
+  double* st = reinterpret_cast<double*>(stage[wib]);   // double solves
+  float* stf = reinterpret_cast<float*>(stage[wib]);    // float solves
   const double Astart = TRIG ? alpha_anti(a.c, delta * (double)f0) : 0.0;   // A at the step start
   const double sg0 = a.c.s0, al0 = 0.5 * a.c.a0;
 
@@ -123,7 +132,6 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
   const float* tia_f = TRIG ? tsig_f + 2 * (a.n_fine + 1) : nullptr;   // int of alpha over cell k
   const float* tah_f = TRIG ? tsig_f + 3 * (a.n_fine + 1) : nullptr;   // ... over its first half
   const double* tAn = TRIG ? a.tab + 3 * (a.n_fine + 1) : nullptr;     // A at the nodes
-  float* stf = reinterpret_cast<float*>(st);
   for (int64_t rb = 0; rb < L; rb += kRound) {
     // ---- pass 1: normals of this lane's chunk, chunk sums -------------------------
     const int64_t c0 = rb + (int64_t)lane * kChunk;

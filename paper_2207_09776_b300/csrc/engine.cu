@@ -50,9 +50,11 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineArgs a) {
 // (the solution of a path does not depend on which CTA solves it).
 constexpr int kOrderBuckets = 4096;
 constexpr int kOrderThreads = 1024;
+constexpr int kOrderCache = 8192;   // paths whose bucket is kept in shared memory between the passes
 
 __device__ __forceinline__ int order_bucket(const double* Wt, int steps, int64_t p) {
   double c = 0.0;
+#pragma unroll 4
   for (int n = 0; n < steps; ++n) {
     const double* o = Wt + ((size_t)p * steps + n) * MSK_NWT;
     c += o[MSK_WT_S] * o[MSK_WT_M];
@@ -65,10 +67,15 @@ __global__ void __launch_bounds__(kOrderThreads) path_order_kernel(const double*
                                                                    long long* order, unsigned long long* queue) {
   __shared__ int cnt[kOrderBuckets];
   __shared__ int wsum[kOrderThreads / 32];
+  __shared__ unsigned short cache[kOrderCache];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < kOrderBuckets; i += kOrderThreads) cnt[i] = 0;
   __syncthreads();
-  for (int64_t p = tid; p < paths; p += kOrderThreads) atomicAdd(&cnt[order_bucket(Wt, steps, p)], 1);
+  for (int64_t p = tid; p < paths; p += kOrderThreads) {
+    const int b = order_bucket(Wt, steps, p);
+    if (p < kOrderCache) cache[p] = (unsigned short)b;
+    atomicAdd(&cnt[b], 1);
+  }
   __syncthreads();
   // exclusive scan: each thread owns kOrderBuckets / kOrderThreads consecutive buckets
   constexpr int PER = kOrderBuckets / kOrderThreads;
@@ -104,7 +111,7 @@ __global__ void __launch_bounds__(kOrderThreads) path_order_kernel(const double*
   }
   __syncthreads();
   for (int64_t p = tid; p < paths; p += kOrderThreads) {
-    const int pos = atomicAdd(&cnt[order_bucket(Wt, steps, p)], 1);
+    const int pos = atomicAdd(&cnt[p < kOrderCache ? (int)cache[p] : order_bucket(Wt, steps, p)], 1);
     order[pos] = p;
   }
   if (tid == 0) *queue = 0ull;
