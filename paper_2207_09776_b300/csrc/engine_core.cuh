@@ -407,7 +407,6 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
     int cur = 0, par = 0;
     // ---- initial datum: own rows, plus the halo rows facing other CTAs ----------
     T m0 = T(0);
-#pragma unroll
     // own points of the initial datum (u0, or the path's own output slot)
     const T* self0 = a.u0_self ? reinterpret_cast<const T*>(a.out) + (size_t)path * D * D : nullptr;
     auto load0 = [&](int jg) -> V4<T> {
