@@ -113,7 +113,7 @@ struct msk_batch {
   int device = 0;
   std::vector<msk_batch_item> items;
   std::vector<EngineArgs> args;
-  std::vector<size_t> f_off, w_off;
+  std::vector<size_t> f_off, w_off, o_off;   // functionals, weights, path order + queue counter
   double* scratch = nullptr;
   EngineArgs* d_args = nullptr;
   BatchUnit* d_units = nullptr;
@@ -222,8 +222,10 @@ msk_status enqueue(msk_batch* b, cudaStream_t s) {
     for (size_t k = 0; k < b->items.size() && st == MSK_OK; ++k) {
       const msk_batch_item& it = b->items[k];
       if (it.paths == 0) continue;
-      st = launch_engine(it.ctx, false, it.steps, it.paths, MSK_F32, b->scratch + b->w_off[k], nullptr, it.u_out_dev,
-                         it.status_dev, s);
+      long long* order_buf = reinterpret_cast<long long*>(b->scratch + b->o_off[k]);
+      st = launch_magnus_queued(it.ctx, it.steps, it.paths, MSK_F32, b->scratch + b->w_off[k], it.u_out_dev,
+                                it.status_dev, s, order_buf,
+                                reinterpret_cast<unsigned long long*>(order_buf + it.paths));
       if (st != MSK_OK) b->err = it.ctx->err;
     }
     return st;
@@ -315,6 +317,8 @@ extern "C" msk_status msk_batch_create(msk_batch** out, const msk_batch_item* it
     total += (size_t)items[k].paths * items[k].steps * MSK_NF;
     b->w_off.push_back(total);
     total += (size_t)items[k].paths * items[k].steps * MSK_NWT;
+    b->o_off.push_back(total);
+    total += (size_t)items[k].paths + 1;
   }
   if (st == MSK_OK) st = bcuda(b, cudaMalloc(&b->scratch, std::max<size_t>(total, 1) * sizeof(double)), "scratch");
   if (st == MSK_OK) st = bcuda(b, cudaMalloc(&b->d_counter, sizeof(unsigned int)), "counter");
