@@ -17,7 +17,27 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineArgs a) {
   int rank = 0;
   if constexpr (C > 1) rank = (int)cg::this_cluster().block_rank();
   const int64_t cid = blockIdx.x / C, ncl = gridDim.x / C;
-  if constexpr (C > 1) {
+  if constexpr (C > 1 && QUEUE) {
+    // dynamic assignment on a cluster: rank 0 takes the queue position and publishes
+    // the path in its slot; every CTA reads it through the cluster, and a second
+    // cluster barrier keeps rank 0 from rewriting the slot or exiting while another
+    // CTA still reads it (a CTA's shared memory must not be accessed after it exits)
+    const ClusterSync sync;
+    slab_init<T, D, C, NT>(sm, tid, rank, sync);
+    volatile long long* slot = reinterpret_cast<long long*>(smem_raw + queue_slot_offset(Cfg<T, D, C, NT>::SMEM));
+    const uint32_t slot0 = dsmem_addr(const_cast<long long*>(slot), 0);
+    for (;;) {
+      if (rank == 0 && tid == 0) {
+        const unsigned long long q = atomicAdd(a.queue, 1ull);
+        *slot = q < (unsigned long long)a.paths ? a.order[q] : -1;
+      }
+      sync();
+      const long long path = dsmem_ld_s64(slot0);
+      sync();
+      if (path < 0) break;
+      solve_path<T, D, C, NT, EULER>(a, path, sm, tid, rank, sync);
+    }
+  } else if constexpr (C > 1) {
     const ClusterSync sync;
     slab_init<T, D, C, NT>(sm, tid, rank, sync);
     for (int64_t path = cid; path < a.paths; path += ncl) solve_path<T, D, C, NT, EULER>(a, path, sm, tid, rank, sync);
@@ -47,8 +67,8 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineArgs a) {
 template <typename T, int D, int C, int NT, bool EULER>
 msk_status launch_one(msk_ctx* ctx, const EngineArgs& a, cudaStream_t stream) {
   using K = Cfg<T, D, C, NT>;
-  // the dynamic path queue exists for single-CTA Magnus configurations only
-  constexpr bool kQ = C == 1 && !EULER;
+  // the dynamic path queue (Magnus solves) needs 16 bytes past the slab
+  constexpr bool kQ = !EULER && queue_slot_offset(K::SMEM) + 16 <= 232448;
   const bool queued = kQ && a.queue;
   auto kern = queued ? engine_kernel<T, D, C, NT, EULER, kQ> : engine_kernel<T, D, C, NT, EULER, false>;
   const size_t smem = queued ? queue_slot_offset(K::SMEM) + 16 : K::SMEM;

@@ -234,6 +234,11 @@ __device__ __forceinline__ double dsmem_ld(uint32_t addr, double) {
   asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
   return v;
 }
+__device__ __forceinline__ long long dsmem_ld_s64(uint32_t addr) {
+  long long v;
+  asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+  return v;
+}
 
 struct ClusterSync {
   __device__ __forceinline__ void operator()() const { cg::this_cluster().sync(); }

@@ -224,16 +224,20 @@ def test_solve_with_host_buffers(precision, tol):
     s.close()
 
 
-@pytest.mark.parametrize("precision", [msk.MSK_F32, msk.MSK_F64])
-def test_dynamic_path_queue_matches_static_assignment(precision):
+@pytest.mark.parametrize("d,precision,paths", [(64, msk.MSK_F32, 700), (64, msk.MSK_F64, 700),
+                                               (256, msk.MSK_F32, 320), (128, msk.MSK_F64, 320)])
+def test_dynamic_path_queue_matches_static_assignment(d, precision, paths):
     """Above two paths per SM the engine hands out paths from an atomic queue in
-    order of decreasing estimated cost; every path's solution must be identical
-    (bit for bit) to the static assignment used for small path counts."""
-    w = LANGEVIN_TRIG_128.with_(d=64, paths=700, n_fine=1024)
+    order of decreasing estimated cost (on clusters -- 256^2 float: 4 CTAs, 128^2
+    double: 2 CTAs -- rank 0 takes the position and the others read it through
+    distributed shared memory); every path's solution must be identical (bit for
+    bit) to the static assignment used for small path counts."""
+    w = LANGEVIN_TRIG_128.with_(d=d, paths=paths, n_fine=1024)
     s = solver(w)
-    full = s.magnus(3, 8, precision=precision).cpu().numpy()        # 700 paths: queued
+    full = s.magnus(3, 8, precision=precision).cpu().numpy()        # queued
     parts = []
-    for lo, hi in ((0, 250), (250, 500), (500, 700)):                # <= 2 per SM: static
+    cuts = [0, paths // 3, 2 * paths // 3, paths]
+    for lo, hi in zip(cuts[:-1], cuts[1:]):                          # <= 2 per SM: static
         msk.msk_set_seed(s.ctx, w.seed, lo, w.n_fine, w.T)
         parts.append(s.magnus(3, 8, paths=hi - lo, precision=precision).cpu().numpy())
     np.testing.assert_array_equal(full, np.concatenate(parts))
