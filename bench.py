@@ -246,6 +246,13 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ helpers
 
+def queued(paths):
+    """1 if a Magnus solve of `paths` paths launches the path-order kernel (the library
+    orders the paths by estimated cost once every SM gets more than two)."""
+    import torch
+    return 1 if paths > 2 * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count else 0
+
+
 def engine_source_hash():
     h = hashlib.sha256()
     for f in ("engine.cu", "engine_core.cuh", "stencil.cuh"):
@@ -703,7 +710,7 @@ def run_ours(a):
         "e2e": {"value": world * P / (e2e_ms / 1e3), "unit": "paths/s",
                 "h2d_bytes_per_step": u0_host.numel() * 8, "d2h_bytes_per_step": out_host.numel() * 4},
         "clocks": clk,
-        "gpu_launches": 3 * a.steps,
+        "gpu_launches": (3 + queued(P)) * a.steps,   # functionals, weights, [path order,] engine
         "path_status_max": status_bits,
         "comparators": comparators,
     }
@@ -827,7 +834,11 @@ def run_batch(a):
                        "parallelism": f"replicas x{world} (path ranges)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": None, "kernel": "batch_kernel (whole step)"},
-            "clocks": clk, "gpu_launches": 2 * len(ws) + 2,
+            "clocks": clk,
+            # per batch run: functionals and weights per grid, then the megakernel or, for the
+            # per-grid variant, each grid's [path order and] engine launch
+            "gpu_launches": a.steps * (2 * len(ws) + (sum(1 + queued(w.paths) for w in ws)
+                                                      if variant == 4 else 1)),
             "comparators": {"per_grid_launches_ms": seq_ms,
                             "per_grid_paths_per_s": total / (seq_ms / 1e3)}}
     msk.msk_batch_destroy(b)
@@ -934,8 +945,10 @@ def run_surrogate(a):
             "e2e": {"value": world * SURR_SERVE / (e2e_ms / 1e3), "unit": "paths/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": SURR_SERVE * n * 4},
             "clocks": clk,
-            # per step: features, layers + 1 GEMMs, decode GEMM, audit (functionals, weights, engine, audit)
-            "gpu_launches": a.steps * (1 + (SURR_CFG["layers"] + 1) + 1 + 4),
+            # per step: features, layers + 1 GEMMs, decode GEMM, audit (functionals, weights,
+            # [path order,] engine, audit)
+            "gpu_launches": a.steps * (1 + (SURR_CFG["layers"] + 1) + 1 + 4
+                                       + queued(SURR_SERVE // SURR_AUDIT_EVERY)),
             "serve": serve, "accuracy": acc, "training": tinfo}
     msk.msk_surrogate_destroy(s)
     solver.close()
@@ -1082,7 +1095,7 @@ def run_large512(a):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": None,
                          "kernel": "engine_kernel<float,512,16,512> (16-CTA clusters, DSMEM halos)"},
-            "per_sigma": per_sigma, "clocks": clk, "gpu_launches": 3 * 3 * reps}
+            "per_sigma": per_sigma, "clocks": clk, "gpu_launches": 3 * (3 + queued(P)) * reps}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -1245,7 +1258,7 @@ def run_paper_var(a):
         total_ms += ms
         total_paths += P
         total_flops += flops
-        launches += 3 * reps
+        launches += (3 + queued(P)) * reps
         s.close()
     clk = clocks.stop()
     if world > 1:
