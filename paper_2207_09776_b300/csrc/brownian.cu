@@ -142,7 +142,25 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
       // values relative to the chunk start), folded into the double lane sums per chunk
       const float sqf = (float)sq;
       float swf = 0.0f, sof = 0.0f, z0 = 0.0f, z1 = 0.0f;
-      for (int q = 0; q < cnt; ++q) {
+      int q = 0;
+      if (((f0 + c0) & 1) == 0) {
+        // even start: cells 2i, 2i+1 of the chunk share a Philox call; two independent
+        // calls per iteration (the same values and summation order as one cell at a time)
+        for (; q + 4 <= cnt; q += 4) {
+          const int64_t fi = f0 + c0 + q;
+          float za0, za1, zb0, zb1;
+          brownian_pair_f32f(a.seed, gpath, 0u, (uint64_t)(fi >> 1), za0, za1);
+          brownian_pair_f32f(a.seed, gpath, 0u, (uint64_t)(fi >> 1) + 1, zb0, zb1);
+          const float dw[4] = {sqf * za0, sqf * za1, sqf * zb0, sqf * zb1};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            stf[(q + e) * 32 + lane] = dw[e];
+            swf += dw[e];
+            if (FULL) sof = fmaf(TRIG ? tsig_f[fi + e] : (float)sg0, dw[e], sof);
+          }
+        }
+      }
+      for (; q < cnt; ++q) {
         const int64_t fi = f0 + c0 + q;
         if (q == 0 || (fi & 1) == 0) brownian_pair_f32f(a.seed, gpath, 0u, (uint64_t)(fi >> 1), z0, z1);
         const float dw = sqf * ((fi & 1) ? z1 : z0);
