@@ -57,6 +57,8 @@ def test_argument_validation_needs_no_device(lib):
     assert lib.msk_create(None, ctypes.byref(g), 0) == msk.MSK_ERR_ARG
     # calls on a NULL context fail with MSK_ERR_ARG, destroy(NULL) is a no-op
     assert lib.msk_solve_magnus(None, 2, 1, 1, 0, None, None, None) == msk.MSK_ERR_ARG
+    assert lib.msk_solve_magnus_host(None, 2, 1, 1, 0, None, None, None, None) == msk.MSK_ERR_ARG
+    assert lib.msk_magnus_from_weights(None, 1, 1, 0, None, None, None, None) == msk.MSK_ERR_ARG
     assert lib.msk_set_x_profile(None, msk.MSK_XPROF_RATIONAL, 1.0, None) == msk.MSK_ERR_ARG
     assert lib.msk_solve_euler(None, 1, 1, 0, None, None, None) == msk.MSK_ERR_ARG
     assert lib.msk_set_seed(None, 1, 0, 100, 1.0) == msk.MSK_ERR_ARG
