@@ -114,7 +114,13 @@ typedef struct {
 msk_status msk_create(msk_ctx** out, const msk_grid* grid, int device);
 
 /* Release the context and every library-owned device buffer.  NULL is a no-op.
- * Must not be called while work using the context is in flight. */
+ * Must not be called while work using the context is in flight.
+ * A context's scratch (functionals, weights, path order) is shared by its
+ * solves: calls on one context are ordered on one stream, or the caller
+ * synchronises between calls issued on different streams or host threads.
+ * Growing the scratch frees the old buffer (cudaFree, which waits for the
+ * device) and is not possible while a stream of the device is being captured
+ * into a graph: size it with one uncaptured call first. */
 void msk_destroy(msk_ctx* ctx);
 
 /* Last error message of the context ("" if none).  For ctx NULL: the message
