@@ -66,11 +66,10 @@ __global__ void cell_table_kernel(CoefDev c, int64_t n_fine, double T, double* t
   const double Am = alpha_anti(c, tm), An = alpha_anti(c, tk);
   tab[2 * (n_fine + 1) + k] = Am;                                                  // A at cell midpoint
   tab[3 * (n_fine + 1) + k] = An;                                                  // A at node
-  float* tf = reinterpret_cast<float*>(tab + 4 * (n_fine + 1));                   // float copies
-  tf[k] = (float)sig;
-  tf[(n_fine + 1) + k] = (float)alp;
-  tf[2 * (n_fine + 1) + k] = (float)(alpha_anti(c, tk + delta) - An);             // int of alpha over the cell
-  tf[3 * (n_fine + 1) + k] = (float)(Am - An);                                     // ... over its first half
+  // float copies, one float4 per cell: sigma(mid), alpha(node), the integral of alpha
+  // over the cell and over its first half
+  float4* tf = reinterpret_cast<float4*>(tab + 4 * (n_fine + 1));
+  tf[k] = make_float4((float)sig, (float)alp, (float)(alpha_anti(c, tk + delta) - An), (float)(Am - An));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -127,10 +126,8 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
   //   sum (k + 1/2) sdw = sum k sdw + sum sdw / 2,   sum (om0 + om1) = 2 sum om0 + sum sdw.
   double Sw0 = 0.0, S2 = 0.0, Skw = 0.0, So0 = 0.0, Sks = 0.0, J3 = 0.0, J4 = 0.0;
   double swT = 0.0, soT = 0.0;                              // sum dw, sum sigma dW of the lane's cells
-  const float* tsig_f = TRIG ? reinterpret_cast<const float*>(a.tab + 4 * (a.n_fine + 1)) : nullptr;
-  const float* talp_f = TRIG ? tsig_f + (a.n_fine + 1) : nullptr;
-  const float* tia_f = TRIG ? tsig_f + 2 * (a.n_fine + 1) : nullptr;   // int of alpha over cell k
-  const float* tah_f = TRIG ? tsig_f + 3 * (a.n_fine + 1) : nullptr;   // ... over its first half
+  // per cell k: {sigma(mid), alpha(node k), int of alpha over the cell, ... over its first half}
+  const float4* tf4 = TRIG ? reinterpret_cast<const float4*>(a.tab + 4 * (a.n_fine + 1)) : nullptr;
   const double* tAn = TRIG ? a.tab + 3 * (a.n_fine + 1) : nullptr;     // A at the nodes
   for (int64_t rb = 0; rb < L; rb += kRound) {
     // ---- pass 1: normals of this lane's chunk, chunk sums -------------------------
@@ -156,7 +153,7 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
           for (int e = 0; e < 4; ++e) {
             stf[(q + e) * 32 + lane] = dw[e];
             swf += dw[e];
-            if (FULL) sof = fmaf(TRIG ? tsig_f[fi + e] : (float)sg0, dw[e], sof);
+            if (FULL) sof = fmaf(TRIG ? tf4[fi + e].x : (float)sg0, dw[e], sof);
           }
         }
       }
@@ -166,7 +163,7 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
         const float dw = sqf * ((fi & 1) ? z1 : z0);
         stf[q * 32 + lane] = dw;
         swf += dw;
-        if (FULL) sof = fmaf(TRIG ? tsig_f[fi] : (float)sg0, dw, sof);
+        if (FULL) sof = fmaf(TRIG ? tf4[fi].x : (float)sg0, dw, sof);
       }
       sw = (double)swf;
       so = (double)sof;
@@ -199,6 +196,9 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
       // A(step start) (double, once per chunk), z the float running integral of alpha.
       float x0 = 0.0f, y0 = 0.0f, kl = 0.0f, z = 0.0f;
       float A = 0.0f, Bq = 0.0f, Ck = 0.0f, E = 0.0f, Fk = 0.0f, H = 0.0f, I = 0.0f, Jz = 0.0f;
+      // this cell's table entry; the next one (node k + 1 <= n_fine) supplies alpha(t_{k+1})
+      float4 cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (TRIG && cnt > 0) cur = tf4[f0 + c0];
       for (int q = 0; q < cnt; ++q) {
         const int64_t fi = f0 + c0 + q;
         const float dw = stf[q * 32 + lane];
@@ -206,16 +206,18 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
         A += x0;
         Bq = fmaf(x0, xs, fmaf(x1, x1, Bq));
         Ck = fmaf(kl, xs, Ck);
-        const float sdw = (TRIG ? tsig_f[fi] : (float)sg0) * dw;
+        const float sdw = (TRIG ? cur.x : (float)sg0) * dw;
         const float y1 = y0 + sdw;
         E += y0;
         Fk = fmaf(kl, sdw, Fk);
         if (TRIG) {
-          const float al0 = talp_f[fi], al1 = talp_f[fi + 1];
+          const float4 nxt = tf4[fi + 1];
+          const float al0 = cur.y, al1 = nxt.y;
           H += al0 + al1;
           I = fmaf(al0, y0, fmaf(al1, y1, I));
-          Jz = fmaf(z + tah_f[fi], sdw, Jz);
-          z += tia_f[fi];
+          Jz = fmaf(z + cur.w, sdw, Jz);
+          z += cur.z;
+          cur = nxt;
         }
         x0 = x1;
         y0 = y1;
