@@ -187,6 +187,26 @@ def _need(t, n, dtype, name):
         raise ValueError(f"{name}: need {n} elements of {dtype}, got {t.numel()} of {t.dtype}")
 
 
+# grid size d of every context created through this binding (nx = nv = d), so that
+# output buffers can be checked against paths x d x d before the kernels write them
+_CTX_D = {}
+
+
+def _key(ctx):
+    return ctx.value if hasattr(ctx, "value") else int(ctx)
+
+
+def _dd(ctx) -> int:
+    """d * d of the context (1 for a handle this binding did not create)."""
+    d = _CTX_D.get(_key(ctx)) if ctx is not None else None
+    return d * d if d else 1
+
+
+def _need_status(st, n):
+    if st is not None and (st.numel() < n or st.element_size() != 4):
+        raise ValueError(f"status: need {n} 32-bit elements, got {st.numel()} of {st.dtype}")
+
+
 # ---- thin wrappers with the C names --------------------------------------------------
 
 def msk_create(nx: int, nv: int, ax: float, bx: float, av: float, bv: float, device: int = 0):
@@ -195,10 +215,13 @@ def msk_create(nx: int, nv: int, ax: float, bx: float, av: float, bv: float, dev
     st = load_library().msk_create(ctypes.byref(h), ctypes.byref(g), device)
     if st != MSK_OK:
         raise MskError(st, load_library().msk_last_error(None).decode())
+    _CTX_D[h.value] = nx
     return h
 
 
 def msk_destroy(ctx):
+    if ctx is not None:
+        _CTX_D.pop(_key(ctx), None)
     load_library().msk_destroy(ctx)
 
 
@@ -237,7 +260,7 @@ def msk_set_initial_gaussian(ctx, mean, cov, scale=1.0):
 
 def msk_set_initial(ctx, u0, stream=None):
     import torch
-    _need(u0, 1, torch.float64, "u0")
+    _need(u0, _dd(ctx), torch.float64, "u0")
     _check(load_library().msk_set_initial(ctx, _ptr(u0), _stream(stream)), ctx)
 
 
@@ -282,7 +305,8 @@ def msk_apply_omega(ctx, weights, paths, u, out, stream=None):
 
 
 def msk_solve_magnus(ctx, order, steps, paths, precision, u_out, status=None, stream=None):
-    _need(u_out, 1, _dtype(precision), "u_out")
+    _need(u_out, paths * _dd(ctx), _dtype(precision), "u_out")
+    _need_status(status, paths)
     _check(load_library().msk_solve_magnus(ctx, order, steps, paths, precision, _ptr(u_out), _ptr(status),
                                            _stream(stream)), ctx)
 
@@ -292,9 +316,10 @@ def msk_solve_magnus_host(ctx, order, steps, paths, precision, u0, u_out, status
     datum, copied on the stream), u_out and status page-locked CPU tensors (tensor.pin_memory()),
     into which the kernels store each finished path.  Synchronise the stream before reading."""
     import torch
-    _need(u_out, 1, _dtype(precision), "u_out")
+    _need(u_out, paths * _dd(ctx), _dtype(precision), "u_out")
+    _need_status(status, paths)
     if u0 is not None:
-        _need(u0, 1, torch.float64, "u0")
+        _need(u0, _dd(ctx), torch.float64, "u0")
     _check(load_library().msk_solve_magnus_host(ctx, order, steps, paths, precision, _host_ptr(u0),
                                                 _host_ptr(u_out), _host_ptr(status), _stream(stream)), ctx)
 
@@ -302,7 +327,8 @@ def msk_solve_magnus_host(ctx, order, steps, paths, precision, u0, u_out, status
 def msk_solve_magnus_noalloc(ctx, order, steps, paths, precision, u_out, status=None, stream=None):
     """msk_solve_magnus without device allocation: scratch comes from the library's
     16 MiB static device array (see include/msk.h for the limits and sharing rules)."""
-    _need(u_out, 1, _dtype(precision), "u_out")
+    _need(u_out, paths * _dd(ctx), _dtype(precision), "u_out")
+    _need_status(status, paths)
     _check(load_library().msk_solve_magnus_noalloc(ctx, order, steps, paths, precision, _ptr(u_out), _ptr(status),
                                                    _stream(stream)), ctx)
 
@@ -313,7 +339,8 @@ def msk_solve_magnus_times(ctx, order, steps, paths, precision, times_cells, u_o
     import torch
     cells = [int(c) for c in times_cells]
     arr = (_I64 * max(len(cells), 1))(*cells)
-    _need(u_out, paths * len(cells), _dtype(precision), "u_out")
+    _need(u_out, paths * len(cells) * _dd(ctx), _dtype(precision), "u_out")
+    _need_status(status, paths * len(cells))
     _check(load_library().msk_solve_magnus_times(ctx, order, steps, paths, precision, arr, len(cells), _ptr(u_out),
                                                  _ptr(status), _stream(stream)), ctx)
 
@@ -321,7 +348,8 @@ def msk_solve_magnus_times(ctx, order, steps, paths, precision, times_cells, u_o
 def msk_magnus_from_weights(ctx, steps, paths, precision, Wt, u_out, status=None, stream=None):
     import torch
     _need(Wt, paths * steps * MSK_NWT, torch.float64, "Wt")
-    _need(u_out, 1, _dtype(precision), "u_out")
+    _need(u_out, paths * _dd(ctx), _dtype(precision), "u_out")
+    _need_status(status, paths)
     _check(load_library().msk_magnus_from_weights(ctx, steps, paths, precision, _ptr(Wt), _ptr(u_out),
                                                   _ptr(status), _stream(stream)), ctx)
 
@@ -343,14 +371,15 @@ def msk_select_steps(ctx, tol, k_min, k_max, paths, precision, stream=None):
 
 
 def msk_solve_euler(ctx, steps, paths, precision, u_out, status=None, stream=None):
-    _need(u_out, 1, _dtype(precision), "u_out")
+    _need(u_out, paths * _dd(ctx), _dtype(precision), "u_out")
+    _need_status(status, paths)
     _check(load_library().msk_solve_euler(ctx, steps, paths, precision, _ptr(u_out), _ptr(status),
                                           _stream(stream)), ctx)
 
 
 def msk_explicit_solution(ctx, paths, u_out, stream=None):
     import torch
-    _need(u_out, 1, torch.float64, "u_out")
+    _need(u_out, paths * _dd(ctx), torch.float64, "u_out")
     _check(load_library().msk_explicit_solution(ctx, paths, _ptr(u_out), _stream(stream)), ctx)
 
 

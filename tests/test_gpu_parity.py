@@ -295,7 +295,7 @@ def test_explicit_solution_and_error_norms(w):
 def test_empty_and_invalid_calls():
     w = LANGEVIN_32.with_(paths=2)
     s = solver(w)
-    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    out = s.state(1)
     msk.msk_solve_magnus(s.ctx, 2, 1, 0, msk.MSK_F64, out)          # zero paths: no-op
     msk.msk_solve_euler(s.ctx, 10, 0, msk.MSK_F64, out)
     with pytest.raises(msk.MskError) as e:
@@ -308,6 +308,9 @@ def test_empty_and_invalid_calls():
     with pytest.raises(msk.MskError) as e:
         msk.msk_set_coefficients(s.ctx, 1, 0, float("inf"), 0, 0.5, 0)
     assert e.value.status == msk.MSK_ERR_NONFINITE
+    # the binding refuses an output buffer smaller than paths x d x d before any launch
+    with pytest.raises(ValueError):
+        msk.msk_solve_magnus(s.ctx, 2, 1, 2, msk.MSK_F64, out)
     # a single path and the context still works after rejected calls
     u = s.magnus(2, 1, paths=1)
     ref = omagnus.solve(w, 2, 1, [0])
