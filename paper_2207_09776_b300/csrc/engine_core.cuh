@@ -105,12 +105,15 @@ struct Cfg {
   // thread's own points) instead of registers: their halo-exchange code needs
   // the registers, and the register-resident sum spills there.
   static constexpr bool ACC_SMEM = C > 1;
-  static constexpr size_t OFF_CSLOT = OFF_SLOT + 4 * NW;           // 2 x 2 CTA-level norm slots
+  // 2 x C x 2 CTA-level norm slots; each pair is written by one vector store
+  // through the cluster, so the region starts on a 16-byte boundary
+  static constexpr size_t OFF_CSLOT = (OFF_SLOT + 4 * NW + 3) / 4 * 4;
   // unit-weight tables (built once per path): the twelve coefficients of the five
   // row classes for each basis operator alone, and the V1 centre of each of the six
   // D^x-class operators per local row; a step's tables are their weighted sums
   static constexpr int NDX = 6;
-  static constexpr size_t OFF_EU = OFF_CSLOT + 4;                  // MSK_NOPS x 5 x 12
+  static constexpr size_t OFF_EU = OFF_CSLOT + 4 * C;              // MSK_NOPS x 5 x 12
+  static_assert(OFF_CSLOT * sizeof(T) % 16 == 0, "cluster norm slots must be 16-byte aligned");
   static constexpr size_t OFF_BU = OFF_EU + (size_t)MSK_NOPS * 5 * MSK_NCOEF;   // NDX x RS
   static constexpr size_t OFF_END = OFF_BU + (size_t)NDX * RS;
   static constexpr size_t OFF_ACC = (OFF_END + 3) / 4 * 4;
@@ -234,6 +237,12 @@ __device__ __forceinline__ double dsmem_ld(uint32_t addr, double) {
   asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
   return v;
 }
+__device__ __forceinline__ void dsmem_st2(uint32_t addr, float a, float b) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(a), "f"(b) : "memory");
+}
+__device__ __forceinline__ void dsmem_st2(uint32_t addr, double a, double b) {
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(addr), "d"(a), "d"(b) : "memory");
+}
 __device__ __forceinline__ long long dsmem_ld_s64(uint32_t addr) {
   long long v;
   asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
@@ -348,18 +357,21 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
   };
 
   // Norms: every warp publishes its maxima; with clusters, warp 0 of each CTA
-  // folds them into one CTA-level slot (after a CTA barrier), and after the
-  // cluster barrier every warp reads the C CTA slots (one remote load per lane).
-  // The result is identical in every thread of the cluster.
-  T* cslot = sm + K::OFF_CSLOT;
+  // folds them into one CTA-level pair (after a CTA barrier) and pushes it into
+  // slot `rank` of every CTA of the cluster (lane l stores to CTA l: remote
+  // stores, off the critical path), so after the cluster barrier every warp reads
+  // the C pairs from its own shared memory.  The result is identical in every
+  // thread of the cluster.  Slots alternate by parity: a CTA already in the next
+  // term writes the other parity, and cannot reach the one after before every CTA
+  // has passed the barrier that follows these reads.
+  T* cslot = sm + K::OFF_CSLOT;   // [2][C][2]
   auto gather = [&](int par, T& gn, T& ga) {
     gn = T(0);
     ga = T(0);
     if constexpr (C > 1) {
       if (lane < C) {
-        const uint32_t q = dsmem_addr(cslot + par * 2, lane);
-        gn = dsmem_ld(q, T(0));
-        ga = dsmem_ld(q + (uint32_t)sizeof(T), T(0));
+        gn = cslot[(par * C + lane) * 2 + 0];
+        ga = cslot[(par * C + lane) * 2 + 1];
       }
     } else {
       for (int q = lane; q < NW; q += 32) {
@@ -387,10 +399,7 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
         }
         a = warp_max_nonneg(a);
         b = warp_max_nonneg(b);
-        if (lane == 0) {
-          cslot[par * 2 + 0] = a;
-          cslot[par * 2 + 1] = b;
-        }
+        if (lane < C) dsmem_st2(dsmem_addr(cslot + (par * C + rank) * 2, lane), a, b);
       }
     }
   };
