@@ -58,6 +58,7 @@ namespace {
 constexpr int kVarFields = 3;
 constexpr int kVarMaxTerms = 64;        // >= the largest Taylor degree of either theta table
 constexpr int kVarMaxThreads = 512;
+constexpr int kVarMaxCluster = 16;      // CTAs per cluster at most
 constexpr size_t kVarSmemCap = 232448;  // 227 KB per CTA
 constexpr int kVarNormBlocks = 32;      // blocks per operator in the norm kernels
 constexpr int kVarOps = 6;
@@ -117,8 +118,8 @@ __host__ __device__ inline VarLayout var_layout(int RS, int W, int NT, int nfiel
   L.off_cx = L.off_acc + RS * W;
   L.off_scale = L.off_cx + RS + 4;
   L.off_slot = L.off_scale + kVarMaxTerms + 1;
-  L.off_cslot = L.off_slot + 4 * (NT / 32);
-  L.off_q = (L.off_cslot + 4 + 1) / 2 * 2;   // the cluster's next path (8 bytes)
+  L.off_cslot = (L.off_slot + 4 * (NT / 32) + 3) / 4 * 4;   // [2][16][2], 16-byte aligned
+  L.off_q = L.off_cslot + 4 * kVarMaxCluster;               // the cluster's next path (8 bytes)
   L.total = L.off_q + 2;
   return L;
 }
@@ -136,15 +137,11 @@ __device__ __forceinline__ void cl_st(uint32_t addr, float v) {
 __device__ __forceinline__ void cl_st(uint32_t addr, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
 }
-__device__ __forceinline__ float cl_ld(uint32_t addr, float) {
-  float v;
-  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
-  return v;
+__device__ __forceinline__ void cl_st2(uint32_t addr, float a, float b) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(a), "f"(b) : "memory");
 }
-__device__ __forceinline__ double cl_ld(uint32_t addr, double) {
-  double v;
-  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
-  return v;
+__device__ __forceinline__ void cl_st2(uint32_t addr, double a, double b) {
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(addr), "d"(a), "d"(b) : "memory");
 }
 __device__ __forceinline__ long long cl_ld_s64(uint32_t addr) {
   long long v;
@@ -197,15 +194,16 @@ __device__ __forceinline__ double var_alpha_t(const CoefDev& c, double t) {
 
 // Norm reduction shared by the engines of this file: every warp publishes its
 // maxima in shared memory; with clusters warp 0 of each CTA folds them into one
-// CTA slot and every warp reads the C slots (shared::cluster loads) after the
-// cluster barrier, so all threads of a cluster take identical decisions.  Two
-// slot sets (par = 0, 1) alternate so that a publish never overwrites slots that
-// another warp may still be gathering.
+// pair and pushes it into slot `rank` of every CTA of the cluster (shared::cluster
+// stores before the cluster barrier), and every warp reads the C pairs from its
+// own shared memory after the barrier, so all threads of a cluster take identical
+// decisions.  Two slot sets (par = 0, 1) alternate so that a publish never
+// overwrites slots that another warp may still be gathering.
 template <typename T>
 struct NormSlots {
   T* slots;    // [2][NW][2]
-  T* cslot;    // [2][2]
-  int NW, C, lane, warp;
+  T* cslot;    // [2][C][2]: slot r holds CTA r's pair, pushed there by CTA r (16-byte aligned)
+  int NW, C, lane, warp, rank;
   __device__ __forceinline__ void publish(int par, T mn, T ma) const {
     mn = wmax(mn);
     ma = wmax(ma);
@@ -223,10 +221,9 @@ struct NormSlots {
         }
         x = wmax(x);
         y = wmax(y);
-        if (lane == 0) {
-          cslot[par * 2 + 0] = x;
-          cslot[par * 2 + 1] = y;
-        }
+        // push this CTA's pair into slot `rank` of every CTA (lane l -> CTA l); after
+        // the cluster barrier each warp reads the C pairs from its own shared memory
+        if (lane < C) cl_st2(cl_addr(cslot + (par * C + rank) * 2, lane), x, y);
       }
     }
   }
@@ -235,9 +232,8 @@ struct NormSlots {
     ga = T(0);
     if (C > 1) {
       if (lane < C) {
-        const uint32_t q = cl_addr(cslot + par * 2, lane);
-        gn = cl_ld(q, T(0));
-        ga = cl_ld(q + (uint32_t)sizeof(T), T(0));
+        gn = cslot[(par * C + lane) * 2 + 0];
+        ga = cslot[(par * C + lane) * 2 + 1];
       }
     } else {
       for (int q = lane; q < NW; q += 32) {
@@ -321,7 +317,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
     }
   };
 
-  const NormSlots<T> norms{slots, cslot, NW, C, lane, warp};
+  const NormSlots<T> norms{slots, cslot, NW, C, lane, warp, rank};
   auto publish = [&](int par, T mn, T ma) { norms.publish(par, mn, ma); };
   auto gather = [&](int par, T& gn, T& ga) { norms.gather(par, gn, ga); };
   // row mask: 1 for rows of the grid, 0 for the halo rows beyond its boundary
@@ -658,8 +654,8 @@ __host__ __device__ inline GenLayout gen_layout(int RS, int W, int NT) {
   L.off_acc = kGenFields * L.FS;
   L.off_scale = L.off_acc + RS * W;
   L.off_slot = L.off_scale + kVarMaxTerms + 1;
-  L.off_cslot = L.off_slot + 4 * (NT / 32);
-  L.off_q = (L.off_cslot + 4 + 1) / 2 * 2;   // the cluster's next path (8 bytes)
+  L.off_cslot = (L.off_slot + 4 * (NT / 32) + 3) / 4 * 4;   // [2][16][2], 16-byte aligned
+  L.off_q = L.off_cslot + 4 * kVarMaxCluster;               // the cluster's next path (8 bytes)
   L.total = L.off_q + 2;
   return L;
 }
@@ -728,7 +724,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
     return fma(__ldg(gA + 4 * dd + g), F[o - W], v);
   };
 
-  const NormSlots<T> norms{slots, cslot, NW, C, lane, warp};
+  const NormSlots<T> norms{slots, cslot, NW, C, lane, warp, rank};
   auto publish = [&](int par, T mn, T ma) { norms.publish(par, mn, ma); };
   auto gather = [&](int par, T& gn, T& ga) { norms.gather(par, gn, ga); };
 
