@@ -25,8 +25,10 @@
 
 namespace {
 
-__constant__ double c_theta64[MSK_THETA_MMAX_F64];
-__constant__ double c_theta32[MSK_THETA_MMAX_F32];
+// reciprocals 1 / theta_m (one multiply per candidate degree instead of a double
+// division, which is a long instruction sequence on this part's narrow double pipe)
+__constant__ double c_inv_theta64[MSK_THETA_MMAX_F64];
+__constant__ double c_inv_theta32[MSK_THETA_MMAX_F32];
 
 struct OmegaArgs {
   const double* band;
@@ -170,13 +172,13 @@ __global__ void omega_kernel(OmegaArgs a, const double* __restrict__ F, double* 
       nrm = fmax(nrm, row_abs_sum(c));
     }
   }
-  const double* th = a.precision == MSK_F32 ? c_theta32 : c_theta64;
+  const double* ith = a.precision == MSK_F32 ? c_inv_theta32 : c_inv_theta64;
   const int mmax = a.precision == MSK_F32 ? MSK_THETA_MMAX_F32 : MSK_THETA_MMAX_F64;
   double best_s = 1.0, best_m = 0.0;
   if (nrm > 0.0) {
     double best_cost = INFINITY;
     for (int m = 1; m <= mmax; ++m) {
-      const double s = fmax(1.0, ceil(nrm / th[m - 1]));
+      const double s = fmax(1.0, ceil(nrm * ith[m - 1]));
       const double cost = m * s;
       if (cost < best_cost) {
         best_cost = cost;
@@ -218,10 +220,12 @@ extern const double kMskScaleCap = 16384.0;
 // Upload the theta tables to this device's constant memory (once per device).
 msk_status msk_prepare_omega(msk_ctx* ctx) {
   if (ctx->device >= 0 && ctx->device < 64 && !g_theta_loaded[ctx->device]) {
-    msk_status st = msk_cuda(ctx, cudaMemcpyToSymbol(c_theta64, msk_theta_f64, sizeof(msk_theta_f64)),
-                             "theta64");
+    double i64[MSK_THETA_MMAX_F64], i32[MSK_THETA_MMAX_F32];
+    for (int m = 0; m < MSK_THETA_MMAX_F64; ++m) i64[m] = 1.0 / msk_theta_f64[m];
+    for (int m = 0; m < MSK_THETA_MMAX_F32; ++m) i32[m] = 1.0 / msk_theta_f32[m];
+    msk_status st = msk_cuda(ctx, cudaMemcpyToSymbol(c_inv_theta64, i64, sizeof(i64)), "theta64");
     if (st != MSK_OK) return st;
-    st = msk_cuda(ctx, cudaMemcpyToSymbol(c_theta32, msk_theta_f32, sizeof(msk_theta_f32)), "theta32");
+    st = msk_cuda(ctx, cudaMemcpyToSymbol(c_inv_theta32, i32, sizeof(i32)), "theta32");
     if (st != MSK_OK) return st;
     g_theta_loaded[ctx->device] = true;
   }
