@@ -244,6 +244,34 @@ def test_dynamic_path_queue_matches_static_assignment(d, precision, paths):
     s.close()
 
 
+@pytest.mark.parametrize("precision,tol", [(msk.MSK_F32, TOL32), (msk.MSK_F64, TOL64)])
+def test_full_bench_configuration_on_sampled_paths(precision, tol):
+    """The benchmark's own configuration at full size -- 4096 paths, d = 128, 2^14 fine
+    cells, order 3, K = 8, time-dependent coefficients -- run exactly as the bench times
+    it (functionals, weights, then the solve from the weights with the cost-ordered
+    queue), checked against the oracle on sampled paths (first, last, middle and a few
+    scattered ones) and for finiteness and clean status everywhere."""
+    w = LANGEVIN_TRIG_128
+    assert w.paths == 4096 and w.d == 128 and w.n_fine == 16384
+    s = solver(w)
+    K, P = 8, w.paths
+    F = torch.empty(P * K * msk.MSK_NF, dtype=torch.float64, device="cuda")
+    Wt = torch.empty(P * K * msk.MSK_NWT, dtype=torch.float64, device="cuda")
+    out = s.state(P, precision)
+    st = torch.full((P,), 7, dtype=torch.int32, device="cuda")
+    msk.msk_brownian_functionals_ex(s.ctx, K, P, precision, F)
+    msk.msk_omega_weights(s.ctx, 3, K, P, precision, F, Wt)
+    msk.msk_magnus_from_weights(s.ctx, K, P, precision, Wt, out, st)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(out).all())
+    assert int(st.max()) == 0
+    sample = [0, 1, 777, 2048, 3001, 4095]
+    ref = np.stack([omagnus.solve_path(w, 3, K, p) for p in sample])
+    err = rel_l2(out[sample].cpu().numpy(), ref)
+    assert err.max() <= tol, err
+    s.close()
+
+
 def test_euler_parity():
     w = LANGEVIN_32.with_(paths=6)
     s = solver(w)
