@@ -830,10 +830,11 @@ def run_batch(a):
     seq_ms = t0.elapsed_time(t1)
     msk.msk_batch_run(b, stream)
     torch.cuda.synchronize()
-    errs = {}
-    for s, w, o in zip(solvers, ws, outs):
+    errs, flagged = {}, {}
+    for s, w, o, st in zip(solvers, ws, outs, sts):
         e, m = s.error(o[:64].contiguous(), msk.MSK_F32)
         errs[f"d{w.d}"] = float(m.cpu()[0])
+        flagged[f"d{w.d}"] = int((st[: w.paths] != 0).sum())
     peaks, peak_src = measured_peaks()
     fp32_peak = 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
     achieved = matvec_pts * FLOPS_PER_POINT / (ms / 1e3) / 1e12
@@ -844,6 +845,8 @@ def run_batch(a):
                        "paths_per_gpu": [w.paths for w in ws], "order": order, "magnus_steps": K,
                        "n_fine": ws[0].n_fine, "variant": variant, "tune_ms": tune_ms,
                        "err_vs_closed_form_64_paths": errs,
+                       # order 3 with step 1/16 explodes on a few 256^2 trajectories (flag BLOWUP)
+                       "flagged_paths": flagged,
                        "parallelism": f"replicas x{world} (path ranges)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": None, "kernel": "batch_kernel (whole step)"},

@@ -9,7 +9,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 import paper_2207_09776_b300 as msk  # noqa: E402
-from oracle import magnus as omagnus  # noqa: E402
+from oracle import discretization as disc, magnus as omagnus  # noqa: E402
 from workloads import BATCH_GRIDS, LANGEVIN_32  # noqa: E402
 
 
@@ -111,5 +111,53 @@ def test_batch_edge_cases():
     with pytest.raises(msk.MskError):
         msk.msk_batch_create([(solvers[0].ctx, 2, 3, 2, outs[0], None)])   # 3 does not divide 256
     s32.close()
+    for s in solvers:
+        s.close()
+
+
+def test_full_size_batch_on_sampled_paths():
+    """The batched configuration at full size -- 9362 x 64^2, 4681 x 128^2 and 2341 x 256^2
+    paths, 2^14 fine cells, order 3, K = 16 -- in the persistent megakernel (variant 0) and
+    as per-grid launches (variant 4, the cost-ordered queue): every output finite, the two
+    variants equal to 1e-6 and flagging the same paths, the first and last path of every
+    grid against the CPU oracle.  At 256^2 the order-3 scheme with step 1/16 explodes on a
+    few trajectories (Section 3.1 reports such explosions for large steps): those paths carry
+    only the blow-up flag, stay rare, and the oracle explodes on them as well."""
+    ws = list(BATCH_GRIDS)
+    assert [w.paths for w in ws] == [9362, 4681, 2341] and ws[0].n_fine == 16384
+    solvers = [msk.Solver(w) for w in ws]
+    outs = [s.state(w.paths, msk.MSK_F32) for s, w in zip(solvers, ws)]
+    sts = [torch.full((w.paths,), 9, dtype=torch.int32, device="cuda") for w in ws]
+    items = [(s.ctx, 3, 16, w.paths, o, st) for s, w, o, st in zip(solvers, ws, outs, sts)]
+    b = msk.msk_batch_create(items)
+    got, flags = {}, {}
+    for variant in (0, 4):
+        msk.msk_batch_set_variant(b, variant)
+        for o in outs:
+            o.fill_(float("nan"))
+        msk.msk_batch_run(b)
+        torch.cuda.synchronize()
+        for o in outs:
+            assert bool(torch.isfinite(o).all())
+        got[variant] = [o.cpu().numpy() for o in outs]
+        flags[variant] = [st.cpu().numpy().astype(np.int64) for st in sts]
+    for a, c in zip(got[0], got[4]):
+        assert rel_l2(a, c).max() <= 1e-6
+    for f0, f4, w in zip(flags[0], flags[4], ws):
+        np.testing.assert_array_equal(f0, f4)
+        assert set(np.unique(f4)) <= {0, msk.MSK_PATH_BLOWUP}
+        assert (f4 != 0).sum() <= w.paths // 100
+    assert (flags[4][0] != 0).sum() == 0 and (flags[4][1] != 0).sum() == 0
+    for w, o, f in zip(ws, got[4], flags[4]):
+        sample = [0, w.paths - 1]
+        blown = [int(p) for p in np.nonzero(f)[0][:1]]
+        ref = omagnus.solve(w, 3, 16, sample + blown)
+        assert rel_l2(o[sample], ref[:2]).max() <= 1e-4
+        if blown:
+            # the oracle explodes on the same trajectory: max|u_T| > 10 max|u_0|
+            u0max = np.abs(disc.vec(disc.gaussian_initial(w))).max()
+            assert np.abs(ref[2]).max() > 10 * u0max
+            assert rel_l2(o[blown], ref[2:]).max() <= 1e-3
+    msk.msk_batch_destroy(b)
     for s in solvers:
         s.close()
