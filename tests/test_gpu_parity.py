@@ -403,6 +403,22 @@ def test_d512_sixteen_cta_clusters_match_the_oracle():
     s.close()
 
 
+def test_d512_full_size_on_a_sampled_path():
+    """The 512^2 configuration at full size as the bench runs it for sigma = 0.5 (1024 paths,
+    order 2, K = 64 from the fixed-error protocol, 2^14 fine cells, 16-CTA clusters with
+    the cost-ordered queue): every path finite and unflagged, the last path against the
+    oracle (one oracle path takes most of a minute)."""
+    w = LARGE_512[1]
+    assert w.paths == 1024 and w.d == 512 and w.s0 == 0.5
+    s = solver(w)
+    u, st = s.magnus(2, 64, precision=msk.MSK_F32, status=True)
+    assert bool(torch.isfinite(u).all())
+    assert int(st[: w.paths].max()) == 0
+    ref = _oracle_magnus(w, 2, 64, [w.paths - 1])
+    assert rel_l2(u[w.paths - 1:].cpu().numpy(), ref).max() <= TOL32
+    s.close()
+
+
 def test_d256_euler_clusters():
     w = BATCH_GRIDS[2].with_(paths=2, T=0.05, n_fine=64)
     s = solver(w)
