@@ -209,6 +209,21 @@ def test_dynamic_path_queue_matches_static_assignment(d):
     s.close()
 
 
+@pytest.mark.parametrize("d,K,paths,sample", [(100, 20, 4096, [0, 2047, 4095]), (200, 40, 1024, [1023])])
+def test_paper_grids_at_bench_size_on_sampled_paths(d, K, paths, sample):
+    """Table errorsVar grids at the path counts the bench runs (order 3, the paper's steps,
+    10^5 fine cells, float): every path finite and unflagged, sampled paths against the
+    oracle."""
+    w = PAPER_VAR[(100, 200, 300).index(d)].with_(paths=paths)
+    s = msk.Solver(w)
+    u, st = s.magnus(3, K, precision=msk.MSK_F32, status=True)
+    assert bool(torch.isfinite(u).all())
+    assert int(st[:paths].max()) == 0
+    ref = omagnus.solve(w, 3, K, sample)
+    assert rel_l2(u[sample].cpu().numpy(), ref).max() <= TOL32
+    s.close()
+
+
 def test_paper_grid_300_float_against_the_oracle():
     """d = 300 (a cluster of 7 CTAs per path in float) on a short horizon."""
     w = PAPER_VAR[2].with_(paths=1, T=0.02, n_fine=200)
