@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
       // float solves: float normals and float sums within the chunk (at most 64 cells,
       // values relative to the chunk start), folded into the double lane sums per chunk
       const float sqf = (float)sq;
-      float swf = 0.0f, sof = 0.0f, z0 = 0.0f, z1 = 0.0f;
+      float swf = 0.0f, z0 = 0.0f, z1 = 0.0f;
       int q = 0;
       if (((f0 + c0) & 1) == 0) {
         // even start: cells 2i, 2i+1 of the chunk share a Philox call; two independent
@@ -153,7 +153,6 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
           for (int e = 0; e < 4; ++e) {
             stf[(q + e) * 32 + lane] = dw[e];
             swf += dw[e];
-            if (FULL) sof = fmaf(TRIG ? tf4[fi + e].x : (float)sg0, dw[e], sof);
           }
         }
       }
@@ -163,10 +162,8 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
         const float dw = sqf * ((fi & 1) ? z1 : z0);
         stf[q * 32 + lane] = dw;
         swf += dw;
-        if (FULL) sof = fmaf(TRIG ? tf4[fi].x : (float)sg0, dw, sof);
       }
-      sw = (double)swf;
-      so = (double)sof;
+      sw = (double)swf;   // the chunk's sum of sigma dW comes out of pass 2
     } else {
       double z0 = 0.0, z1 = 0.0;
       for (int q = 0; q < cnt; ++q) {
@@ -179,12 +176,15 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
       }
     }
     const double woff = W0 + warp_excl_scan(sw, lane);
-    const double ooff = O0 + warp_excl_scan(so, lane);
     W0 += warp_sum(sw);
-    O0 += warp_sum(so);
+    double ooff = 0.0;
+    if constexpr (!NF32) {
+      ooff = O0 + warp_excl_scan(so, lane);
+      O0 += warp_sum(so);
+    }
     if (!FULL) continue;
     swT += sw;
-    soT += so;
+    if constexpr (!NF32) soT += so;
     // ---- pass 2: functionals over the staged increments -------------------------
     // Sums are kept without their constant factors (delta/2, delta/3, delta^2/6,
     // delta), applied once at the end; k is carried as a double counter.
@@ -223,6 +223,12 @@ __global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, doub
         y0 = y1;
         kl += 1.0f;
       }
+      // the chunk's sum of sigma dW (= omega~ at its end, relative to its start) gives the
+      // omega~ offsets of the chunks
+      so = (double)y0;
+      ooff = O0 + warp_excl_scan(so, lane);
+      O0 += warp_sum(so);
+      soT += so;
       const double n = (double)cnt, kc = (double)c0, xe = (double)x0;
       const double sx = 2.0 * (double)A + xe;             // sum (x0 + x1)
       Sw0 += n * woff + (double)A;
