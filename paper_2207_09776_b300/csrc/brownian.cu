@@ -88,7 +88,7 @@ __device__ __forceinline__ double warp_excl_scan(double v, int lane) {
 }
 
 template <bool FULL, bool TRIG, bool NF32>
-__global__ void __launch_bounds__(32 * kWarps) brownian_kernel(BrownArgs a, double* __restrict__ out) {
+__global__ void __launch_bounds__(32 * kWarps, 5) brownian_kernel(BrownArgs a, double* __restrict__ out) {
   // staged increments of one round (float in the float solves: half the shared
   // memory, so more warps fit on an SM)
   __shared__ typename std::conditional<NF32, float, double>::type stage[kWarps][32 * kChunk];
