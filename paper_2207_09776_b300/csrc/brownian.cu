@@ -77,14 +77,18 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ double warp_excl_scan(double v, int lane) {
+
+// exclusive prefix over the lanes and the warp total (the last lane's inclusive
+// value, one shuffle instead of a second reduction)
+__device__ __forceinline__ void warp_scan_total(double v, int lane, double& excl, double& total) {
   double x = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const double y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
-  return x - v;
+  excl = x - v;
+  total = __shfl_sync(0xffffffffu, x, 31);
 }
 
 template <bool FULL, bool TRIG, bool NF32>
@@ -175,12 +179,16 @@ __global__ void __launch_bounds__(32 * kWarps, 5) brownian_kernel(BrownArgs a, d
         if (FULL) so += (TRIG ? tsig[fi] : sg0) * dw;
       }
     }
-    const double woff = W0 + warp_excl_scan(sw, lane);
-    W0 += warp_sum(sw);
+    double woff, wtot;
+    warp_scan_total(sw, lane, woff, wtot);
+    woff += W0;
+    W0 += wtot;
     double ooff = 0.0;
     if constexpr (!NF32) {
-      ooff = O0 + warp_excl_scan(so, lane);
-      O0 += warp_sum(so);
+      double otot;
+      warp_scan_total(so, lane, ooff, otot);
+      ooff += O0;
+      O0 += otot;
     }
     if (!FULL) continue;
     swT += sw;
@@ -226,8 +234,10 @@ __global__ void __launch_bounds__(32 * kWarps, 5) brownian_kernel(BrownArgs a, d
       // the chunk's sum of sigma dW (= omega~ at its end, relative to its start) gives the
       // omega~ offsets of the chunks
       so = (double)y0;
-      ooff = O0 + warp_excl_scan(so, lane);
-      O0 += warp_sum(so);
+      double otot;
+      warp_scan_total(so, lane, ooff, otot);
+      ooff += O0;
+      O0 += otot;
       soT += so;
       const double n = (double)cnt, kc = (double)c0, xe = (double)x0;
       const double sx = 2.0 * (double)A + xe;             // sum (x0 + x1)
