@@ -78,6 +78,32 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Warp sums of eight per-lane values at once, by a transposed butterfly: in each of
+// the first three rounds a lane keeps half of its values (chosen by one bit of its
+// index) and adds its partner's copy of that half, then two plain rounds finish;
+// 9 double additions instead of 40.  Every lane gets all eight totals back.
+__device__ __forceinline__ void warp_sum8(double (&v)[8], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  double h[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const double keep = b4 ? v[4 + j] : v[j], send = b4 ? v[j] : v[4 + j];
+    h[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  double q[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const double keep = b3 ? h[2 + j] : h[j], send = b3 ? h[j] : h[2 + j];
+    q[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  double x = (b2 ? q[1] : q[0]) + __shfl_xor_sync(0xffffffffu, b2 ? q[0] : q[1], 4);
+  x += __shfl_xor_sync(0xffffffffu, x, 2);
+  x += __shfl_xor_sync(0xffffffffu, x, 1);
+  // value k is now held by the lanes whose bits 4, 3, 2 spell k
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = __shfl_sync(0xffffffffu, x, ((k & 4) << 2) | ((k & 2) << 2) | ((k & 1) << 2));
+}
+
 // exclusive prefix over the lanes and the warp total (the last lane's inclusive
 // value, one shuffle instead of a second reduction)
 __device__ __forceinline__ void warp_scan_total(double v, int lane, double& excl, double& total) {
@@ -282,14 +308,16 @@ __global__ void __launch_bounds__(32 * kWarps, 5) brownian_kernel(BrownArgs a, d
     const double S3 = 3.0 * (Skw + Sw0) + 2.0 * swT;          // sum (3k (w0 + w1) + w0 + 2 w1)
     const double J1 = 2.0 * So0 + soT;                       // sum (om0 + om1)
     const double J2 = Sks + 0.5 * soT;                       // sum (k + 1/2) sigma dW
-    const double I1 = 0.5 * delta * warp_sum(S1);
-    const double I2 = delta / 3.0 * warp_sum(S2);
-    const double I3 = delta * delta / 6.0 * warp_sum(S3);
-    const double jom = 0.5 * delta * warp_sum(J1);
-    const double ssdw = delta * warp_sum(J2);
+    double t[8] = {S1, S2, S3, J1, J2, TRIG ? J3 : 0.0, TRIG ? J4 : 0.0, 0.0};
+    warp_sum8(t, lane);
+    const double I1 = 0.5 * delta * t[0];
+    const double I2 = delta / 3.0 * t[1];
+    const double I3 = delta * delta / 6.0 * t[2];
+    const double jom = 0.5 * delta * t[3];
+    const double ssdw = delta * t[4];
     // constant coefficients: alpha_bar(s) = alpha s and alpha0 = alpha1 = alpha
-    const double jaom = TRIG ? 0.5 * delta * warp_sum(J3) : al0 * jom;
-    const double abdw = TRIG ? warp_sum(J4) : al0 * ssdw;
+    const double jaom = TRIG ? 0.5 * delta * t[5] : al0 * jom;
+    const double abdw = TRIG ? t[6] : al0 * ssdw;
     if (lane == 0) {
       double* o = out + idx * MSK_NF;
       o[MSK_F_DW] = W0;
