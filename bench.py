@@ -62,6 +62,8 @@ def parse():
                         "surrogate of the 128^2 workload served 65536 paths per step with a 1%% Magnus audit; "
                         "large512: the 512^2 constant-coefficient grids, sigma = 0.25 / 0.5 / 1, 1024 paths, m2")
     p.add_argument("--no-surrogate", action="store_true", help="skip the surrogate summary of the default line")
+    p.add_argument("--clock-csv-dir", default=None,
+                   help="directory for the clock samples taken during the timed region (default: a temporary one)")
     p.add_argument("--surrogate-profile-case", type=int, default=0, metavar="PATHS",
                    help="serve PATHS paths twice with an untrained surrogate of the 128^2 workload (random "
                         "weights, random orthonormal POD basis; features, network, decode; no audit) -- a "
@@ -126,12 +128,16 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
+    csv_dir = None            # --clock-csv-dir; None: a temporary directory
+
     def __init__(self, index):
+        import tempfile
         self.index = index
         self.proc = None
         self.thread = None
         self.rows = []
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+        out_dir = ClockSampler.csv_dir or tempfile.mkdtemp(prefix="msk_clocks_")
+        self.path = os.path.join(out_dir, f"clocks_gpu{index}.csv")
 
     def _nvml_index(self):
         vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
@@ -1379,6 +1385,7 @@ def run_profile_case(a):
 
 def main():
     a = parse()
+    ClockSampler.csv_dir = a.clock_csv_dir
     if a.profile_case:
         run_profile_case(a)
         return

@@ -300,7 +300,10 @@ msk_status msk_solve_magnus_times(msk_ctx* ctx, int order, int steps, int64_t pa
  * on a device looks up the array's address (once per device); make it before
  * any stream capture.  All calls share the array and it keeps the last call's
  * contents (nothing in it needs to start at zero); calls whose work overlaps
- * on the GPU race on it and must be serialised by the caller.  Arguments and
+ * on the GPU race on it and must be serialised by the caller.  With an x
+ * profile or general coefficients the operator table those engines read is
+ * allocated by msk_set_x_profile / msk_set_general_coefficients, never by a
+ * solve, so this call stays allocation-free there too.  Arguments and
  * outputs as for msk_solve_magnus. */
 msk_status msk_solve_magnus_noalloc(msk_ctx* ctx, int order, int steps, int64_t paths,
                                     int precision, void* u_out_dev,

@@ -1265,16 +1265,21 @@ int var_table_ops(const msk_ctx* ctx) {
   return (!ctx->gen && ctx->xprof && ctx->coef.kind == MSK_COEF_TRIG) ? MSK_NOPS : kVarOps;
 }
 
+// The operator table (traces, shifted norms and their per-block partials) is
+// allocated by the calls that switch a context to variable or general
+// coefficients, never by a solve: the solves only rebuild its contents.
+static msk_status alloc_var_tab(msk_ctx* ctx) {
+  if (ctx->var_tab) return MSK_OK;
+  return msk_cuda(ctx, cudaMalloc(&ctx->var_tab, (2 * MSK_NOPS + 2 * MSK_NOPS * kVarNormBlocks) * sizeof(double)),
+                  "operator table allocation");
+}
+
 msk_status ensure_var_tables(msk_ctx* ctx, cudaStream_t stream) {
   if (!ctx->xprof && !ctx->gen) return MSK_OK;
   const int ops = var_table_ops(ctx);
   if (!ctx->var_dirty && ctx->var_ops_built == ops) return MSK_OK;
   constexpr int NB = kVarNormBlocks;
-  if (!ctx->var_tab) {
-    msk_status st = msk_cuda(ctx, cudaMalloc(&ctx->var_tab, (2 * MSK_NOPS + 2 * MSK_NOPS * NB) * sizeof(double)),
-                             "operator table allocation");
-    if (st != MSK_OK) return st;
-  }
+  if (!ctx->var_tab) return msk_fail(ctx, MSK_ERR_ARG, "operator table missing (profile or coefficients not set)");
   VarOpsDev o;
   o.d = ctx->d;
   o.kx = (double)ctx->coef.drift_sign * (0.5 / ctx->dx);
@@ -1378,6 +1383,8 @@ extern "C" msk_status msk_set_x_profile(msk_ctx* ctx, int kind, double c, const 
     st = msk_cuda(ctx, cudaMalloc(&ctx->psi, (size_t)ctx->d * sizeof(double)), "profile allocation");
     if (st != MSK_OK) return st;
   }
+  st = alloc_var_tab(ctx);
+  if (st != MSK_OK) return st;
   if (kind == MSK_XPROF_RATIONAL) st = launch_psi_rational(ctx, c, 0);
   else st = msk_cuda(ctx, cudaMemcpy(ctx->psi, psi_host, (size_t)ctx->d * sizeof(double), cudaMemcpyHostToDevice),
                      "copy profile");
@@ -1406,6 +1413,8 @@ extern "C" msk_status msk_set_general_coefficients(msk_ctx* ctx, const double* c
     if (st == MSK_OK) st = msk_cuda(ctx, cudaMalloc(&ctx->gen32, 14 * dd * sizeof(float)), "stencil field allocation");
     if (st != MSK_OK) return st;
   }
+  st = alloc_var_tab(ctx);
+  if (st != MSK_OK) return st;
   double* tmp = nullptr;
   st = msk_cuda(ctx, cudaMalloc(&tmp, 9 * dd * sizeof(double)), "coefficient upload");
   if (st != MSK_OK) return st;

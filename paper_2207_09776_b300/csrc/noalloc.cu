@@ -24,8 +24,10 @@
 //    before reading it, on the caller's stream).  Calls whose work overlaps on
 //    the GPU (different streams, or different contexts on the same device)
 //    race on the array and must be serialised by the caller.
-//  - Inputs live in the context (set up beforehand, which does allocate), the
-//    outputs are the caller's buffers, as for msk_solve_magnus.
+//  - Inputs live in the context (set up beforehand, which does allocate: also
+//    the operator table of the x-profile and general-coefficient engines, which
+//    msk_set_x_profile / msk_set_general_coefficients allocate), the outputs
+//    are the caller's buffers, as for msk_solve_magnus.
 #include <mutex>
 
 #include "msk_internal.cuh"
@@ -73,13 +75,20 @@ extern "C" msk_status msk_solve_magnus_noalloc(msk_ctx* ctx, int order, int step
   if (paths == 0) return MSK_OK;
   if (!u_out_dev) return msk_fail(ctx, MSK_ERR_ARG, "null output");
   const bool trig = ctx->coef.kind == MSK_COEF_TRIG;
-  const size_t nF = (size_t)paths * steps * MSK_NF, nW = (size_t)paths * steps * MSK_NWT;
-  const size_t nT = trig ? 6 * (size_t)(ctx->n_fine + 1) : 0;
-  if (nF + nW + nT > kNoAllocScratchDoubles)
+  // Bound check by division, so that no product of the caller's sizes can wrap
+  // around: the cell table first (n_fine is at most the array size here), then
+  // the per-path share (steps <= n_fine, so steps * 28 cannot overflow).
+  const size_t per_path = (size_t)steps * (MSK_NF + MSK_NWT);
+  const bool table_fits = (uint64_t)ctx->n_fine < kNoAllocScratchDoubles / 6;
+  const size_t nT = trig && table_fits ? 6 * (size_t)(ctx->n_fine + 1) : 0;
+  if ((trig && (!table_fits || nT > kNoAllocScratchDoubles)) ||
+      (uint64_t)paths > (kNoAllocScratchDoubles - nT) / per_path)
     return msk_fail(ctx, MSK_ERR_ARG,
-                    "request needs " + std::to_string(nF + nW + nT) + " doubles of scratch; the static scratch of "
-                    "msk_solve_magnus_noalloc holds " + std::to_string(kNoAllocScratchDoubles) +
-                    " (paths * steps * " + std::to_string(MSK_NF + MSK_NWT) + " + 6 (n_fine + 1) if time-dependent)");
+                    "request of " + std::to_string(paths) + " paths x " + std::to_string(steps) +
+                    " steps does not fit the static scratch of msk_solve_magnus_noalloc, which holds " +
+                    std::to_string(kNoAllocScratchDoubles) + " doubles (paths * steps * " +
+                    std::to_string(MSK_NF + MSK_NWT) + " + 6 (n_fine + 1) if time-dependent)");
+  const size_t nF = (size_t)paths * steps * MSK_NF, nW = (size_t)paths * steps * MSK_NWT;
   cudaStream_t s = (cudaStream_t)stream;
   msk_status st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
   if (st != MSK_OK) return st;
