@@ -74,9 +74,17 @@ enum {
 };
 
 /* Per (path, step) record written by msk_omega_weights (doubles):
- * [0, MSK_NOPS) operator weights, then shift mu, norm bound, scaling s, degree m. */
+ * [0, MSK_NOPS) operator weights, then
+ *   MSK_WT_ALPHA  the bound alpha that chose (s, m): an upper bound of the minimum of
+ *                 Al-Mohy & Higham's alpha_p(Omega - mu I) over the p with
+ *                 p (p - 1) <= m + 1 (<= MSK_WT_NORM); alpha / s <= theta_m
+ *   MSK_WT_WORK   expected stencil applications of the step (path ordering), 0 if unused
+ *   MSK_WT_MU     shift mu = trace(Omega) / n
+ *   MSK_WT_NORM   ||Omega - mu I||_inf (exact for the Langevin operators; a bound
+ *                 over the operators with an x profile or general coefficients)
+ *   MSK_WT_S, MSK_WT_M  Taylor scaling count s and degree cap m (alpha / s <= theta_m). */
 #define MSK_NWT 20
-enum { MSK_WT_MU = 16, MSK_WT_NORM = 17, MSK_WT_S = 18, MSK_WT_M = 19 };
+enum { MSK_WT_ALPHA = 13, MSK_WT_WORK = 14, MSK_WT_MU = 16, MSK_WT_NORM = 17, MSK_WT_S = 18, MSK_WT_M = 19 };
 
 /* Interior grid n_x x n_v on [ax,bx] x [av,bv]; Delta = (b - a)/(n + 1)
  * (Eq. xGrid, vGrid).  This build requires nx == nv. */
@@ -122,6 +130,32 @@ msk_status msk_create(msk_ctx** out, const msk_grid* grid, int device);
  * device) and is not possible while a stream of the device is being captured
  * into a graph: size it with one uncaptured call first. */
 void msk_destroy(msk_ctx* ctx);
+
+/* Multiply-add throughput of the CUDA cores of `device` in TFLOP/s (2 flop per
+ * fused multiply-add), MSK_F32 or MSK_F64, measured on `stream` by a kernel of
+ * independent FMA chains over every SM (a few milliseconds; synchronises the
+ * stream).  No counterpart in the paper: the denominator of the roofline
+ * fraction of the engines, whose state stays on chip.  Bad precision or null
+ * output -> MSK_ERR_ARG. */
+msk_status msk_fma_throughput(int device, int precision, double* tflops_out, void* stream);
+
+/* Engine of the Magnus solves of the Langevin operators (constant or
+ * time-dependent coefficients):
+ *   MSK_ENGINE_AUTO      the resident engine where one is built for (d, precision),
+ *                        else the streamed one (default)
+ *   MSK_ENGINE_RESIDENT  each path's state in shared memory (a cluster of up to 16
+ *                        CTAs; d = 32 .. 512 in float, 32 .. 256 in double)
+ *   MSK_ENGINE_STREAMED  each path's state in HBM, swept by one CTA per path with
+ *                        several Taylor terms per sweep (d = 256, 512; float and
+ *                        double); needs two d x d grids of library scratch per CTA,
+ *                        so msk_solve_magnus_noalloc refuses it
+ * Euler-Maruyama, output times, x profiles and general coefficients always use the
+ * resident engines.  Both engines give the same solution within the Taylor
+ * tolerance.  Bad mode -> MSK_ERR_ARG. */
+#define MSK_ENGINE_AUTO 0
+#define MSK_ENGINE_RESIDENT 1
+#define MSK_ENGINE_STREAMED 2
+msk_status msk_set_engine(msk_ctx* ctx, int mode);
 
 /* Last error message of the context ("" if none).  For ctx NULL: the message
  * of the last msk_create that failed after validating its arguments on this
@@ -220,6 +254,20 @@ msk_status msk_brownian_increments(msk_ctx* ctx, int steps, int64_t paths, doubl
 msk_status msk_omega_weights(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
                              const double* F_dev, double* Wt_dev, void* stream);
 
+/* S5a: infinity norms of the powers of the deterministic part of Omega, the
+ * input of the (s, m) selection of msk_omega_weights (Section 2, `expmvtay2`,
+ * after Al-Mohy & Higham (2011), who bound the scaling by
+ * alpha_p = max(||A^p||^(1/p), ||A^(p+1)||^(1/(p+1))) instead of ||A||).
+ * X_n = Omega_n - mu_n I with every Brownian functional set to zero (the terms
+ * h Bx + alpha_bar Bvv - (int sigma^2)/2 A0^2 - G3/2 [Bx,Bvv] of step n, shared by
+ * all paths): out_dev[r * 9 + q - 1] = ||X_r^q||_inf, q = 1 .. 9, computed in
+ * float by propagating unit rows.  *rows_out = 1 for MSK_COEF_CONST (X is the
+ * same every step), steps for MSK_COEF_TRIG, 0 with an x profile or general
+ * coefficients (those engines bound the norm over their operators; nothing is
+ * written).  out_dev: caller-owned float[*rows_out * 9], or NULL to query
+ * *rows_out only. */
+msk_status msk_power_norms(msk_ctx* ctx, int order, int steps, float* out_dev, int* rows_out, void* stream);
+
 /* One application out = Omega u of Omega = sum_k w_k Op_k, weights_dev
  * [paths][MSK_NOPS] (double), u_dev/out_dev [paths][v][x] double.  Exposes the
  * widened-stencil operator tables for parity checks. */
@@ -296,7 +344,10 @@ msk_status msk_solve_magnus_times(msk_ctx* ctx, int order, int steps, int64_t pa
  * the library holds until exit.  No cudaMalloc, cudaFree or allocating
  * library routine is called.  Requests needing more than the array
  * (paths * steps * (MSK_NF + MSK_NWT) doubles, plus 6 (n_fine + 1) for
- * MSK_COEF_TRIG) fail with MSK_ERR_ARG before any device work.  The first call
+ * MSK_COEF_TRIG, plus ceil(9 r / 2) for the power norms of the Taylor
+ * selection, r = steps for MSK_COEF_TRIG and 1 otherwise, 0 with an x profile
+ * or general coefficients) fail with MSK_ERR_ARG before any device work.  The
+ * power norms are recomputed by every call (no cache).  The first call
  * on a device looks up the array's address (once per device); make it before
  * any stream capture.  All calls share the array and it keeps the last call's
  * contents (nothing in it needs to start at zero); calls whose work overlaps

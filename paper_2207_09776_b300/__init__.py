@@ -26,6 +26,7 @@ MSK_REF_EXPLICIT, MSK_REF_BUFFER = 0, 1
 MSK_PATH_NONFINITE, MSK_PATH_SCALE_CAP, MSK_PATH_BLOWUP = 1, 2, 4
 MSK_NF, MSK_NOPS, MSK_NWT = 8, 13, 20
 MSK_F_DW, MSK_F_I1, MSK_F_I2, MSK_F_I3, MSK_F_OM, MSK_F_JOM, MSK_F_G1, MSK_F_G2 = range(8)
+MSK_WT_ALPHA, MSK_WT_WORK = 13, 14
 MSK_WT_MU, MSK_WT_NORM, MSK_WT_S, MSK_WT_M = 16, 17, 18, 19
 OP_NAMES = ("Bx", "Bvv", "A0", "A0A0", "[Bx,A0]", "[Bvv,A0]", "[Bx,Bvv]", "[[Bx,A0],A0]",
             "[[Bvv,A0],A0]", "[[Bx,A0],Bx]", "[[Bx,A0],Bvv]", "[[Bvv,A0],Bx]", "[[Bvv,A0],Bvv]")
@@ -81,6 +82,9 @@ SIGNATURES = {
     "msk_brownian_functionals_ex": (_INT, [_P, _INT, _I64, _INT, _P, _P]),
     "msk_brownian_increments": (_INT, [_P, _INT, _I64, _P, _P]),
     "msk_omega_weights": (_INT, [_P, _INT, _INT, _I64, _INT, _P, _P, _P]),
+    "msk_power_norms": (_INT, [_P, _INT, _INT, _P, ctypes.POINTER(_INT), _P]),
+    "msk_fma_throughput": (_INT, [_INT, _INT, ctypes.POINTER(_DBL), _P]),
+    "msk_set_engine": (_INT, [_P, _INT]),
     "msk_apply_omega": (_INT, [_P, _P, _I64, _P, _P, _P]),
     "msk_solve_magnus": (_INT, [_P, _INT, _INT, _I64, _INT, _P, _P, _P]),
     "msk_solve_magnus_host": (_INT, [_P, _INT, _INT, _I64, _INT, _P, _P, _P, _P]),
@@ -298,6 +302,37 @@ def msk_omega_weights(ctx, order, steps, paths, precision, F, Wt, stream=None):
     _need(Wt, paths * steps * MSK_NWT, torch.float64, "Wt")
     _check(load_library().msk_omega_weights(ctx, order, steps, paths, precision, _ptr(F), _ptr(Wt),
                                             _stream(stream)), ctx)
+
+
+def msk_power_norms(ctx, order, steps, stream=None):
+    """||X_n^q||_inf (q = 1..9) of the deterministic part of each step's Omega: a float
+    tensor of shape (rows, 9), rows = 1 (constant coefficients), steps (time-dependent)
+    or 0 (x profile / general coefficients)."""
+    import torch
+    lib = load_library()
+    rows = ctypes.c_int(0)
+    _check(lib.msk_power_norms(ctx, order, steps, None, ctypes.byref(rows), _stream(stream)), ctx)
+    out = torch.empty(max(rows.value, 1) * 9, dtype=torch.float32, device="cuda")
+    if rows.value:
+        _check(lib.msk_power_norms(ctx, order, steps, _ptr(out), ctypes.byref(rows), _stream(stream)), ctx)
+    return out[: rows.value * 9].view(rows.value, 9)
+
+
+MSK_ENGINE_AUTO, MSK_ENGINE_RESIDENT, MSK_ENGINE_STREAMED = 0, 1, 2
+
+
+def msk_set_engine(ctx, mode):
+    """Engine of the Magnus solves: MSK_ENGINE_AUTO / _RESIDENT / _STREAMED."""
+    _check(load_library().msk_set_engine(ctx, mode), ctx)
+
+
+def msk_fma_throughput(device=0, precision=MSK_F32, stream=None):
+    """Measured multiply-add throughput (TFLOP/s) of the CUDA cores."""
+    v = ctypes.c_double(0.0)
+    st = load_library().msk_fma_throughput(device, precision, ctypes.byref(v), _stream(stream))
+    if st != MSK_OK:
+        raise MskError(st, "msk_fma_throughput failed")
+    return v.value
 
 
 def msk_apply_omega(ctx, weights, paths, u, out, stream=None):

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmsk.so")
 SOURCES = ["ctx.cu", "operators.cu", "brownian.cu", "omega.cu", "engine.cu", "errors.cu", "noalloc.cu", "batch.cu",
-           "surrogate.cu", "stepsel.cu", "engine_var.cu", "times.cu", "path_order.cu"]
+           "surrogate.cu", "stepsel.cu", "engine_var.cu", "times.cu", "path_order.cu", "peaks.cu", "engine_stream.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

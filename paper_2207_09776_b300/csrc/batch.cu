@@ -114,6 +114,7 @@ struct msk_batch {
   std::vector<msk_batch_item> items;
   std::vector<EngineArgs> args;
   std::vector<size_t> f_off, w_off, o_off;   // functionals, weights, path order + queue counter
+  std::vector<size_t> p_off;                 // power-norm table of the (s, m) selection (floats)
   double* scratch = nullptr;
   EngineArgs* d_args = nullptr;
   BatchUnit* d_units = nullptr;
@@ -213,8 +214,12 @@ msk_status enqueue(msk_batch* b, cudaStream_t s) {
     if (it.paths == 0) continue;
     double* F = b->scratch + b->f_off[k];
     double* Wt = b->scratch + b->w_off[k];
+    float* P = reinterpret_cast<float*>(b->scratch + b->p_off[k]);
     st = launch_brownian(it.ctx, it.steps, it.paths, F, false, s, true);   // float solves: float normals
-    if (st == MSK_OK) st = launch_omega(it.ctx, it.order, it.steps, it.paths, MSK_F32, F, Wt, s);
+    // the power norms are recomputed into the batch's own scratch on every run (a few
+    // microseconds): the graph then depends on no state of the contexts' caches
+    if (st == MSK_OK) st = launch_power_norms(it.ctx, it.order, it.steps, P, s);
+    if (st == MSK_OK) st = launch_omega_tab(it.ctx, it.order, it.steps, it.paths, MSK_F32, F, Wt, P, s);
     if (st != MSK_OK) b->err = it.ctx->err;
   }
   if (st != MSK_OK || b->n_units == 0) return st;
@@ -319,6 +324,8 @@ extern "C" msk_status msk_batch_create(msk_batch** out, const msk_batch_item* it
     total += (size_t)items[k].paths * items[k].steps * MSK_NWT;
     b->o_off.push_back(total);
     total += (size_t)items[k].paths + 1;
+    b->p_off.push_back(total);
+    total += ((size_t)power_norm_rows(items[k].ctx, items[k].steps) * MSK_POW_J + 1) / 2;
   }
   if (st == MSK_OK) st = bcuda(b, cudaMalloc(&b->scratch, std::max<size_t>(total, 1) * sizeof(double)), "scratch");
   if (st == MSK_OK) st = bcuda(b, cudaMalloc(&b->d_counter, sizeof(unsigned int)), "counter");

@@ -55,6 +55,8 @@ extern "C" void msk_destroy(msk_ctx* ctx) {
   if (ctx->tab) cudaFree(ctx->tab);
   if (ctx->psi) cudaFree(ctx->psi);
   if (ctx->var_tab) cudaFree(ctx->var_tab);
+  if (ctx->pow_tab) cudaFree(ctx->pow_tab);
+  if (ctx->stream_scratch) cudaFree(ctx->stream_scratch);
   if (ctx->gen64) cudaFree(ctx->gen64);
   if (ctx->gen32) cudaFree(ctx->gen32);
   delete ctx;
@@ -112,7 +114,16 @@ extern "C" msk_status msk_set_coefficients(msk_ctx* ctx, const msk_coeffs* c) {
   const bool rebuild = c->drift_sign != ctx->coef.drift_sign;
   if (rebuild || c->a0 != ctx->coef.a0 || c->kind != ctx->coef.kind) ctx->var_dirty = true;
   ctx->coef = *c;
+  ++ctx->setup_gen;
   if (rebuild) return launch_band_tables(ctx, 0);
+  return MSK_OK;
+}
+
+extern "C" msk_status msk_set_engine(msk_ctx* ctx, int mode) {
+  if (!ctx) return MSK_ERR_ARG;
+  if (mode != MSK_ENGINE_AUTO && mode != MSK_ENGINE_RESIDENT && mode != MSK_ENGINE_STREAMED)
+    return msk_fail(ctx, MSK_ERR_ARG, "bad engine mode");
+  ctx->engine_mode = mode;
   return MSK_OK;
 }
 
@@ -147,6 +158,7 @@ extern "C" msk_status msk_set_seed(msk_ctx* ctx, uint64_t seed, uint64_t path_of
   ctx->path_offset = path_offset;
   ctx->n_fine = n_fine;
   ctx->T = T;
+  ++ctx->setup_gen;
   return MSK_OK;
 }
 

@@ -153,6 +153,18 @@ msk_status launch_em_table(msk_ctx* ctx, int steps, double* em_d, float* em_f, c
   return msk_cuda(ctx, cudaGetLastError(), "euler table");
 }
 
+bool resident_engine_available(int d, int precision) {
+  if (precision == MSK_F32) return d == 32 || d == 64 || d == 128 || d == 256 || d == 512;
+  return d == 32 || d == 64 || d == 128 || d == 256;
+}
+
+bool engine_is_streamed(const msk_ctx* ctx, int precision) {
+  if (ctx->xprof || ctx->gen) return false;
+  if (ctx->engine_mode == MSK_ENGINE_STREAMED) return true;
+  if (ctx->engine_mode == MSK_ENGINE_RESIDENT) return false;
+  return !resident_engine_available(ctx->d, precision) && stream_engine_available(ctx->d, precision);
+}
+
 msk_status launch_engine(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
                          const double* Wt, const double* dW, void* out, uint32_t* status,
                          cudaStream_t stream) {
@@ -165,6 +177,11 @@ msk_status launch_engine_ex(msk_ctx* ctx, bool euler, int steps, int64_t paths, 
   if (paths == 0) return MSK_OK;
   if (ctx->xprof || ctx->gen)
     return launch_engine_var(ctx, euler, steps, paths, precision, Wt, dW, out, status, stream, x);
+  if (!euler && engine_is_streamed(ctx, precision)) {
+    if (x.snap || x.u0_self)
+      return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "output times are not built on the streamed engine");
+    return launch_engine_stream(ctx, steps, paths, precision, Wt, out, status, stream, x.order, x.queue);
+  }
   EngineArgs a{};
   a.snap = x.snap;
   a.snap_first = x.snap_first;

@@ -47,7 +47,7 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int kMaxTerms = 64;   // >= the largest Taylor degree of either theta table
+constexpr int kMaxTerms = 128;  // >= the largest Taylor degree of either theta table
 
 struct EngineArgs {
   const double* band;
@@ -498,7 +498,7 @@ __device__ __forceinline__ void solve_path(const EngineArgs& a, int64_t path, T*
         else if (lane == MSK_OP_A0) wl = em[2 * n + 1] * (T)a.dW[path * a.steps + n];   // sigma(t_n) dW_n
         else if (lane == MSK_NOPS) wl = T(1);                                           // I + ...
       } else {
-        // lanes 14, 15 carry s and m (exact in float: s <= 2^14, m <= 64)
+        // lanes 14, 15 carry s and m (exact in float: s <= 2^14, m <= 128)
         const double* rec = a.Wt + ((size_t)path * a.steps + n) * MSK_NWT;
         if (lane < MSK_NOPS) wl = (T)rec[lane];
         else if (lane == MSK_NOPS) wl = (T)(-rec[MSK_WT_MU]);

@@ -56,7 +56,7 @@ extern const double kMskScaleCap;
 namespace {
 
 constexpr int kVarFields = 3;
-constexpr int kVarMaxTerms = 64;        // >= the largest Taylor degree of either theta table
+constexpr int kVarMaxTerms = 128;       // >= the largest Taylor degree of either theta table
 constexpr int kVarMaxThreads = 512;
 constexpr int kVarMaxCluster = 16;      // CTAs per cluster at most
 constexpr size_t kVarSmemCap = 232448;  // 227 KB per CTA
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
         const T wBA = w[MSK_OP_BX_A0], wBAA = w[MSK_OP_BXA0_A0], wBAB = w[MSK_OP_BXA0_BX];
         const T muT = __shfl_sync(0xffffffffu, rl, MSK_NOPS);
         const T sT = __shfl_sync(0xffffffffu, rl, MSK_NOPS + 1), mT = __shfl_sync(0xffffffffu, rl, MSK_NOPS + 2);
-        const int s_steps = max(1, (int)sT);               // exact: s <= 2^14, m <= 64
+        const int s_steps = max(1, (int)sT);               // exact: s <= 2^14, m <= 128
         const int m_terms = min((int)mT, kVarMaxTerms);
         if (sT >= (T)a.s_cap) scale_cap = true;
         T te;
@@ -1393,6 +1393,7 @@ extern "C" msk_status msk_set_x_profile(msk_ctx* ctx, int kind, double c, const 
   ctx->xprof = kind;
   ctx->gen = 0;
   ctx->var_dirty = true;
+  ++ctx->setup_gen;
   return MSK_OK;
 }
 
@@ -1429,5 +1430,6 @@ extern "C" msk_status msk_set_general_coefficients(msk_ctx* ctx, const double* c
   ctx->gen = 1;
   ctx->xprof = 0;
   ctx->var_dirty = true;
+  ++ctx->setup_gen;
   return MSK_OK;
 }

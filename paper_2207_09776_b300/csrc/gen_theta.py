@@ -67,7 +67,7 @@ TOL64_EXP, TOL32_EXP = 53, 20
 
 
 def main():
-    mmax64, mmax32 = 55, 55
+    mmax64, mmax32 = 120, 120
     t64 = [theta(m, mp.mpf(2) ** -TOL64_EXP) for m in range(1, mmax64 + 1)]
     t32 = [theta(m, mp.mpf(2) ** -TOL32_EXP) for m in range(1, mmax32 + 1)]
     print(f"/* Generated by gen_theta.py: theta_m for tolerances 2^-{TOL64_EXP} (double) and "

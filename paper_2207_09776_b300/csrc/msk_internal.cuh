@@ -44,6 +44,18 @@ struct msk_ctx {
   int var_ops_built = 0;      // operators var_tab holds: 6 (constant coefficients) or 13 (time-dependent)
   // general coefficients of Eq. generalSPDE (msk_set_general_coefficients)
   int gen = 0;
+  // bumped by every call that changes the operators, coefficients or time grid
+  unsigned long long setup_gen = 1;
+  // cached infinity norms of the powers of each step's deterministic Omega part
+  // (launch_power_norms), for the (steps, order >= 2) of the last solve
+  float* pow_tab = nullptr;
+  // engine choice (msk_set_engine) and the streamed engine's per-CTA term grids
+  int engine_mode = MSK_ENGINE_AUTO;
+  void* stream_scratch = nullptr;
+  size_t stream_bytes = 0;
+  int64_t pow_cap = 0;        // floats allocated
+  int pow_steps = 0, pow_o2 = -1;
+  unsigned long long pow_gen = 0;
   double* gen64 = nullptr;    // [14][d][d] stencil fields: B (9), A (5)
   float* gen32 = nullptr;
   std::string err;
@@ -83,6 +95,18 @@ msk_status launch_brownian_strided(msk_ctx* ctx, int steps, int64_t paths, doubl
                                    uint64_t stride, cudaStream_t stream, bool nf32 = false);
 msk_status launch_omega(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
                         const double* F, double* Wt, cudaStream_t stream);
+// Powers of the deterministic part of Omega (Langevin operators with constant or
+// time-dependent coefficients): pow_tab[n * MSK_POW_J + q - 1] >= ||X_n^q||_inf for
+// q = 1 .. MSK_POW_J, X_n = Omega_n - mu_n I with every Brownian functional set to
+// zero (one row when X_n does not depend on n).  The (s, m) selection bounds
+// ||(Omega - mu I)^p||^(1/p) with them (Al-Mohy & Higham's alpha_p).
+#define MSK_POW_J 9
+int power_norm_rows(const msk_ctx* ctx, int steps);   // rows of the table (0: not used for this context)
+msk_status launch_power_norms(msk_ctx* ctx, int order, int steps, float* pow_tab, cudaStream_t stream);
+// launch_omega with an explicit power-norm table (null: the plain norm bound);
+// launch_omega itself uses the context's cached table (allocated on demand).
+msk_status launch_omega_tab(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
+                            const double* F, double* Wt, const float* pow_tab, cudaStream_t stream);
 msk_status launch_engine(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
                          const double* Wt, const double* dW, void* out, uint32_t* status,
                          cudaStream_t stream);
@@ -125,6 +149,16 @@ msk_status launch_brownian_jobs(msk_ctx* ctx, const int64_t* jobs_dev, int64_t n
                                 cudaStream_t stream, bool nf32);
 msk_status launch_omega_jobs(msk_ctx* ctx, int order, int64_t njobs, int precision, const double* F,
                              const double* job_th_dev, double* Wt, cudaStream_t stream);
+// Streamed engine (engine_stream.cu): the Magnus solve with every path's state in
+// HBM (its output slot and two per-CTA term grids of library scratch), for grids
+// whose state does not stay on chip.
+bool stream_engine_available(int d, int precision);
+msk_status launch_engine_stream(msk_ctx* ctx, int steps, int64_t paths, int precision, const double* Wt, void* out,
+                                uint32_t* status, cudaStream_t stream, const long long* order,
+                                unsigned long long* queue);
+bool resident_engine_available(int d, int precision);
+// whether the Magnus solves of this context run the streamed engine (msk_set_engine)
+bool engine_is_streamed(const msk_ctx* ctx, int precision);
 // Variable-coefficient path (engine_var.cu): the engine, and the traces and
 // norms of its six operators for the (s, m) selection (rebuilt when dirty).
 msk_status launch_engine_var(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,

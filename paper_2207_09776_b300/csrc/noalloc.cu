@@ -14,8 +14,10 @@
 //    loads this library holds it from the moment the library's device code is
 //    loaded there until the process exits.
 //  - A request needs paths * steps * (MSK_NF + MSK_NWT) doubles, plus
-//    6 * (n_fine + 1) for time-dependent coefficients; larger requests are
-//    rejected with MSK_ERR_ARG before any device work.
+//    6 * (n_fine + 1) for time-dependent coefficients and MSK_POW_J / 2 per
+//    step for the power norms of the Taylor selection (recomputed by every
+//    call, a few microseconds); larger requests are rejected with MSK_ERR_ARG
+//    before any device work.
 //  - The first call on a device looks up the array's device address (set-up,
 //    once per device, with that device current); make that first call before
 //    any stream capture.
@@ -74,6 +76,9 @@ extern "C" msk_status msk_solve_magnus_noalloc(msk_ctx* ctx, int order, int step
   if (paths < 0) return msk_fail(ctx, MSK_ERR_ARG, "paths < 0");
   if (paths == 0) return MSK_OK;
   if (!u_out_dev) return msk_fail(ctx, MSK_ERR_ARG, "null output");
+  if (engine_is_streamed(ctx, precision))
+    return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "the streamed engine needs library scratch; msk_solve_magnus_noalloc "
+                                              "runs the resident engines only");
   const bool trig = ctx->coef.kind == MSK_COEF_TRIG;
   // Bound check by division, so that no product of the caller's sizes can wrap
   // around: the cell table first (n_fine is at most the array size here), then
@@ -81,13 +86,16 @@ extern "C" msk_status msk_solve_magnus_noalloc(msk_ctx* ctx, int order, int step
   const size_t per_path = (size_t)steps * (MSK_NF + MSK_NWT);
   const bool table_fits = (uint64_t)ctx->n_fine < kNoAllocScratchDoubles / 6;
   const size_t nT = trig && table_fits ? 6 * (size_t)(ctx->n_fine + 1) : 0;
-  if ((trig && (!table_fits || nT > kNoAllocScratchDoubles)) ||
-      (uint64_t)paths > (kNoAllocScratchDoubles - nT) / per_path)
+  // power-norm table of the (s, m) selection: rows <= steps <= n_fine floats x MSK_POW_J
+  const size_t nP = ((size_t)power_norm_rows(ctx, steps) * MSK_POW_J + 1) / 2;
+  if ((trig && (!table_fits || nT > kNoAllocScratchDoubles)) || nP > kNoAllocScratchDoubles - nT ||
+      (uint64_t)paths > (kNoAllocScratchDoubles - nT - nP) / per_path)
     return msk_fail(ctx, MSK_ERR_ARG,
                     "request of " + std::to_string(paths) + " paths x " + std::to_string(steps) +
                     " steps does not fit the static scratch of msk_solve_magnus_noalloc, which holds " +
                     std::to_string(kNoAllocScratchDoubles) + " doubles (paths * steps * " +
-                    std::to_string(MSK_NF + MSK_NWT) + " + 6 (n_fine + 1) if time-dependent)");
+                    std::to_string(MSK_NF + MSK_NWT) + " + 6 (n_fine + 1) if time-dependent + " +
+                    std::to_string(MSK_POW_J) + " / 2 per step of the Taylor selection)");
   const size_t nF = (size_t)paths * steps * MSK_NF, nW = (size_t)paths * steps * MSK_NWT;
   cudaStream_t s = (cudaStream_t)stream;
   msk_status st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
@@ -98,9 +106,11 @@ extern "C" msk_status msk_solve_magnus_noalloc(msk_ctx* ctx, int order, int step
   double* F = base;
   double* Wt = F + nF;
   double* tab = Wt + nW;
+  float* pow_tab = reinterpret_cast<float*>(tab + nT);
   if (trig) st = launch_cell_table_into(ctx, tab, s);
   if (st == MSK_OK) st = launch_brownian_with_table(ctx, steps, paths, F, tab, s, precision == MSK_F32);
-  if (st == MSK_OK) st = launch_omega(ctx, order, steps, paths, precision, F, Wt, s);
+  if (st == MSK_OK) st = launch_power_norms(ctx, order, steps, pow_tab, s);
+  if (st == MSK_OK) st = launch_omega_tab(ctx, order, steps, paths, precision, F, Wt, pow_tab, s);
   if (st == MSK_OK) st = launch_engine(ctx, false, steps, paths, precision, Wt, nullptr, u_out_dev, path_status_dev, s);
   return st;
 }

@@ -13,11 +13,22 @@
 //        + G1/2 [Bx,A0] + G2/2 [Bvv,A0] - G3/2 [Bx,Bvv],
 // plus the two third-order terms with B, A frozen at the step midpoint.
 //
-// The exponential action uses a scaled truncated Taylor series; (s, m) follow
-// Al-Mohy & Higham (2011): for ||Omega - mu I|| <= nrm, choose m minimising
-// m ceil(nrm / theta_m) with theta_m the backward-error radius at the unit
-// roundoff of the arithmetic, mu = trace(Omega)/n.  The norm is the exact
-// infinity norm bound of the folded stencil (maximum absolute row sum).
+// The exponential action uses a scaled truncated Taylor series (T_m(A/s))^s with
+// the backward-error radii theta_m of Al-Mohy & Higham (2011) at the unit
+// roundoff of the arithmetic, A = Omega - mu I, mu = trace(Omega)/n.  Their
+// Theorem 4.2 allows any p with p(p-1) <= m + 1 and
+//   alpha_p(A) = max(||A^p||^(1/p), ||A^(p+1)||^(1/(p+1))) <= s theta_m,
+// which is sharper than ||A|| <= s theta_m for these non-normal stencils.  Here
+//   - ||A||_inf is exact (maximum absolute row sum of the folded stencil);
+//   - A = X + E, X the deterministic part (every functional set to zero, shared
+//     by all paths of a step) and E the Brownian part; ||X^q||_inf, q <= 9, are
+//     computed exactly once per step by propagating unit rows (power_norm_kernel),
+//     ||E||_inf per path, and expanding (X + E)^q into its 2^q words bounds
+//     ||A^q|| <= T_q, T_0 = 1, T_q = ||X^q|| + ||E|| sum_{j<q} ||X^j|| T_{q-1-j};
+//   - s is the smallest scaling count admissible for some p (the series stops
+//     early once two consecutive terms are below the tolerance, so its cost is
+//     about the number of terms until convergence, which grows with s), then m the
+//     smallest degree admissible at that s; m <= 120.
 #include <math.h>
 
 #include "stencil.cuh"
@@ -36,6 +47,8 @@ struct OmegaArgs {
   const double* var;   // x profile / general coefficients: traces [0, ops) and shifted norms [ops, 2 ops); else null
   int var_ops;         // 6: the six operators of constant coefficients; 13: the MSK_OP_* basis
   const double* job_th;   // interval mode: (t0, h) per record; else null (step n: t0 = n h, h = T / steps)
+  const float* pow_tab;   // ||X_n^q||, q = 1 .. MSK_POW_J, per step (pow_rows rows); null: plain norm bound
+  int pow_rows;           // 1: X does not depend on the step
   int D, order, steps, precision;
   int64_t paths;
   double T, dx;
@@ -114,6 +127,107 @@ __device__ void magnus_weights(const OmegaArgs& a, double tn, double h, const do
   }
 }
 
+// ---- infinity norms of the powers of the deterministic part X_n ---------------
+//
+// X_n = V0 (x) I + V1 (x) D^x with the v-bands V0 (offsets -2..2, the shift -mu
+// on the centre) and V1 (offsets -1..1) of the zero-functional weights of step n
+// (no (D^x)^2 operator carries a deterministic weight).  Row (i0, j0) of X^q is
+// e^T X^q, propagated as r <- r X in a window of v-rows j0 - 2q .. j0 + 2q and
+// columns i0 - q .. i0 + q (zero outside the grid):
+//   (r X)(i, j) = sum_o r(i, j-o) V0[j-o][o] + sum_o (r(i-1, j-o) - r(i+1, j-o)) V1[j-o][o] / (2 dx).
+// Rows whose column lies J or more from both x edges never reach an edge within
+// J products, so they share their row sums: one representative column per
+// v-row suffices besides the J columns next to each edge.
+constexpr int kPowJ = MSK_POW_J;
+constexpr int kPowWV = 4 * kPowJ + 5;      // window v-rows: +-2J and a 2-row halo
+constexpr int kPowWX = 2 * kPowJ + 3;      // window columns: +-J and a 1-column halo
+constexpr int kPowThreads = 256;
+
+struct PowArgs {
+  OmegaArgs o;     // band, trace, D, order, steps, T, dx, c
+  int nxc;         // column classes per v-row
+  float* out;      // [rows][kPowJ], zeroed; maxima by atomicMax on the bit patterns
+};
+
+__device__ __forceinline__ int pow_class_col(int xc, int D) {
+  if (D <= 2 * kPowJ + 1) return xc;           // every column its own class
+  if (xc <= kPowJ) return xc;                  // J edge columns, then the representative column J
+  return D - 1 - (xc - kPowJ - 1);
+}
+
+__global__ void __launch_bounds__(kPowThreads) power_norm_kernel(PowArgs pa) {
+  const OmegaArgs& a = pa.o;
+  const int D = a.D;
+  const int j0 = blockIdx.x / pa.nxc, i0 = pow_class_col(blockIdx.x % pa.nxc, D);
+  const int n = blockIdx.y;
+  __shared__ float buf[2][kPowWV * kPowWX];
+  __shared__ float V0[kPowWV][5], V1[kPowWV][3];
+  __shared__ float red[kPowThreads / 32];
+  const int tid = threadIdx.x;
+  // zero-functional weights and shift of step n
+  const double h = a.T / a.steps, tn = n * h;
+  double w[MSK_NOPS], f0[MSK_NF];
+  for (int k = 0; k < MSK_NF; ++k) f0[k] = 0.0;
+  magnus_weights(a, tn, h, f0, w);
+  double tr = 0.0;
+  for (int k = 0; k < MSK_NOPS; ++k) tr += w[k] * a.trace[k];
+  const double mu = tr / ((double)D * D), inv2dx = 0.5 / a.dx;
+  // window row jw <-> grid row j0 - 2J - 2 + jw, window column iw <-> i0 - J - 1 + iw
+  for (int jw = tid; jw < kPowWV; jw += kPowThreads) {
+    const int j = j0 - 2 * kPowJ - 2 + jw;
+    double v0[5] = {0, 0, 0, 0, 0}, v1[3] = {0, 0, 0};
+    if (j >= 0 && j < D) {
+      for (int k = 0; k < MSK_NOPS; ++k) {
+        if (w[k] == 0.0) continue;
+        const double* b = a.band + ((size_t)k * D + j) * MSK_BAND;
+        if (c_op_xclass[k] == XC_I)
+          for (int o = 0; o < 5; ++o) v0[o] += w[k] * b[o];
+        else if (c_op_xclass[k] == XC_DX)
+          for (int o = 0; o < 3; ++o) v1[o] += w[k] * b[o + 1];
+      }
+      v0[2] -= mu;
+    }
+    for (int o = 0; o < 5; ++o) V0[jw][o] = (float)v0[o];
+    for (int o = 0; o < 3; ++o) V1[jw][o] = (float)(v1[o] * inv2dx);
+  }
+  for (int e = tid; e < 2 * kPowWV * kPowWX; e += kPowThreads) (&buf[0][0])[e] = 0.0f;
+  __syncthreads();
+  const int cj = 2 * kPowJ + 2, ci = kPowJ + 1;   // window position of (i0, j0)
+  if (tid == 0) buf[0][cj * kPowWX + ci] = 1.0f;
+  __syncthreads();
+  int cur = 0;
+  for (int q = 1; q <= kPowJ; ++q) {
+    const int hv = 2 * q, hx = q, nv = 2 * hv + 1, nx = 2 * hx + 1;
+    const float* src = buf[cur];
+    float* dst = buf[cur ^ 1];
+    float part = 0.0f;
+    for (int e = tid; e < nv * nx; e += kPowThreads) {
+      const int jw = cj - hv + e / nx, iw = ci - hx + e % nx;
+      const int j = j0 - 2 * kPowJ - 2 + jw, i = i0 - kPowJ - 1 + iw;
+      float v = 0.0f;
+      if (j >= 0 && j < D && i >= 0 && i < D) {
+#pragma unroll
+        for (int o = -2; o <= 2; ++o) v = fmaf(src[(jw - o) * kPowWX + iw], V0[jw - o][o + 2], v);
+#pragma unroll
+        for (int o = -1; o <= 1; ++o)
+          v = fmaf(src[(jw - o) * kPowWX + iw - 1] - src[(jw - o) * kPowWX + iw + 1], V1[jw - o][o + 1], v);
+      }
+      dst[jw * kPowWX + iw] = v;
+      part += fabsf(v);
+    }
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    if (tid == 0) {
+      float t = 0.0f;
+      for (int k = 0; k < kPowThreads / 32; ++k) t += red[k];
+      atomicMax(reinterpret_cast<unsigned int*>(pa.out) + (size_t)n * kPowJ + q - 1, __float_as_uint(t));
+    }
+    cur ^= 1;
+    __syncthreads();
+  }
+}
+
 __device__ double row_abs_sum(const double c[MSK_NCOEF]) {
   // interior-column sum; edge columns lose neighbours but may carry Ae instead of A[+-1]
   double s = fabs(c[CF_A + 0]) + fmax(fabs(c[CF_A + 1]), fabs(c[CF_AE + 0])) + fabs(c[CF_A + 2]) +
@@ -174,23 +288,79 @@ __global__ void omega_kernel(OmegaArgs a, const double* __restrict__ F, double* 
   }
   const double* ith = a.precision == MSK_F32 ? c_inv_theta32 : c_inv_theta64;
   const int mmax = a.precision == MSK_F32 ? MSK_THETA_MMAX_F32 : MSK_THETA_MMAX_F64;
-  double best_s = 1.0, best_m = 0.0;
+  // d[q] >= ||(Omega - mu I)^q||^(1/q): d[1] the exact norm, d[2..J] from the
+  // deterministic power norms (when available) and the norm of the Brownian part
+  double dq[MSK_POW_J + 1];
+  for (int q = 0; q <= MSK_POW_J; ++q) dq[q] = nrm;
+  if (a.pow_tab && nrm > 0.0) {
+    const int row = a.pow_rows == 1 ? 0 : (int)(idx % a.steps);
+    const float* g = a.pow_tab + (size_t)row * MSK_POW_J;
+    // Brownian part E = Omega - mu I - X: weights minus the zero-functional weights
+    double wd[MSK_NOPS], f0[MSK_NF];
+    for (int k = 0; k < MSK_NF; ++k) f0[k] = 0.0;
+    magnus_weights(a, tn, h, f0, wd);
+    double trd = 0.0;
+    for (int k = 0; k < MSK_NOPS; ++k) {
+      trd += wd[k] * a.trace[k];
+      wd[k] = w[k] - wd[k];
+    }
+    const double dmu = mu - trd / ((double)D * D);
+    double eps = 0.0;
+    const int rows[6] = {0, 1, 2, D - 3, D - 2, D - 1};
+    for (int r = 0; r < 6; ++r) {
+      double c[MSK_NCOEF];
+      fold_row(a.band, D, rows[r], wd, -dmu, 0.5 / a.dx, 0.25 / (a.dx * a.dx), c);
+      eps = fmax(eps, row_abs_sum(c));
+    }
+    // the float table carries relative rounding far below 1e-4 (unit rows, at most
+    // nine stencil products): inflate it by 2^-10 so it stays an upper bound
+    double gx[MSK_POW_J + 1], Tq[MSK_POW_J + 1];
+    gx[0] = 1.0;
+    Tq[0] = 1.0;
+    for (int q = 1; q <= MSK_POW_J; ++q) {
+      gx[q] = (double)g[q - 1] * (1.0 + 0x1p-10);
+      double t = gx[q];
+      for (int j = 0; j < q; ++j) t += eps * gx[j] * Tq[q - 1 - j];
+      Tq[q] = t;
+      if (q >= 2) dq[q] = fmin(nrm, exp(log(t) / q));
+    }
+  }
+  double best_s = 1.0, best_m = 0.0, amin = nrm, used = nrm;
   if (nrm > 0.0) {
-    double best_cost = INFINITY;
-    for (int m = 1; m <= mmax; ++m) {
-      const double s = fmax(1.0, ceil(nrm * ith[m - 1]));
-      const double cost = m * s;
-      if (cost < best_cost) {
-        best_cost = cost;
-        best_s = s;
-        best_m = m;
+    // alpha_p for p = 2 .. J - 1, usable at degree m when p (p - 1) <= m + 1
+    double alpha[MSK_POW_J];
+    alpha[1] = nrm;
+    for (int p = 2; p < MSK_POW_J; ++p) alpha[p] = fmax(dq[p], dq[p + 1]);
+    for (int p = 2; p < MSK_POW_J; ++p)
+      if (p * (p - 1) <= mmax + 1) amin = fmin(amin, alpha[p]);
+    best_s = fmax(1.0, ceil(amin * ith[mmax - 1]));
+    if (!(best_s <= a.s_cap)) {   // also catches a non-finite norm
+      best_s = a.s_cap;
+      best_m = mmax;
+      used = amin;
+    } else {
+      best_m = mmax;
+      for (int m = 1; m <= mmax; ++m) {
+        double am = nrm;
+        for (int p = 2; p < MSK_POW_J && p * (p - 1) <= m + 1; ++p) am = fmin(am, alpha[p]);
+        if (am * ith[m - 1] <= best_s) {
+          best_m = m;
+          used = am;
+          break;
+        }
       }
     }
-    if (!(best_s <= a.s_cap)) best_s = a.s_cap;   // also catches a non-finite norm
   }
   double* o = Wt + idx * MSK_NWT;
   for (int k = 0; k < MSK_NOPS; ++k) o[k] = w[k];
   for (int k = MSK_NOPS; k < MSK_WT_MU; ++k) o[k] = 0.0;
+  o[MSK_WT_ALPHA] = used;
+  // expected Taylor terms: per sub-step about x + sqrt(2 x ln(1/tol)) with x = alpha / s
+  // (the terms x^k / k! fall below the tolerance), capped by the degree
+  if (nrm > 0.0) {
+    const double x = used / best_s, L = a.precision == MSK_F32 ? 13.9 : 36.7;
+    o[MSK_WT_WORK] = best_s * fmin(best_m, ceil(x + sqrt(2.0 * x * L)) + 1.0);
+  }
   o[MSK_WT_MU] = mu;
   o[MSK_WT_NORM] = nrm;
   o[MSK_WT_S] = best_s;
@@ -232,8 +402,57 @@ msk_status msk_prepare_omega(msk_ctx* ctx) {
   return MSK_OK;
 }
 
-msk_status launch_omega(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
-                        const double* F, double* Wt, cudaStream_t stream) {
+int power_norm_rows(const msk_ctx* ctx, int steps) {
+  if (ctx->xprof || ctx->gen) return 0;      // those engines bound the norm over their operators
+  return ctx->coef.kind == MSK_COEF_CONST ? 1 : steps;
+}
+
+msk_status launch_power_norms(msk_ctx* ctx, int order, int steps, float* pow_tab, cudaStream_t stream) {
+  const int rows = power_norm_rows(ctx, steps);
+  if (rows == 0) return MSK_OK;
+  msk_status st = msk_cuda(ctx, cudaMemsetAsync(pow_tab, 0, (size_t)rows * MSK_POW_J * sizeof(float), stream),
+                           "power norm reset");
+  if (st != MSK_OK) return st;
+  PowArgs pa{};
+  pa.o = OmegaArgs{ctx->band, ctx->aux, nullptr, 0, nullptr, nullptr, 0, ctx->d, order, steps, MSK_F64, 0,
+                   ctx->T, ctx->dx, omega_coef(ctx), kMskScaleCap};
+  pa.nxc = ctx->d <= 2 * kPowJ + 1 ? ctx->d : 2 * kPowJ + 1;
+  pa.out = pow_tab;
+  power_norm_kernel<<<dim3((unsigned)(ctx->d * pa.nxc), (unsigned)rows), kPowThreads, 0, stream>>>(pa);
+  return msk_cuda(ctx, cudaGetLastError(), "power norm kernel");
+}
+
+// The context's cached table for (steps, order >= 2); recomputed when the
+// operators, coefficients or time grid changed since it was built.
+static msk_status ensure_power_norms(msk_ctx* ctx, int order, int steps, cudaStream_t stream, const float** out) {
+  *out = nullptr;
+  const int rows = power_norm_rows(ctx, steps);
+  if (rows == 0) return MSK_OK;
+  const int o2 = order >= 2;
+  if (ctx->pow_tab && ctx->pow_gen == ctx->setup_gen && ctx->pow_steps == steps && ctx->pow_o2 == o2) {
+    *out = ctx->pow_tab;
+    return MSK_OK;
+  }
+  const int64_t need = (int64_t)rows * MSK_POW_J;
+  if (need > ctx->pow_cap) {
+    if (ctx->pow_tab) cudaFree(ctx->pow_tab);   // waits for work that may still read it
+    ctx->pow_tab = nullptr;
+    ctx->pow_cap = 0;
+    msk_status st = msk_cuda(ctx, cudaMalloc(&ctx->pow_tab, need * sizeof(float)), "power norm table");
+    if (st != MSK_OK) return st;
+    ctx->pow_cap = need;
+  }
+  msk_status st = launch_power_norms(ctx, order, steps, ctx->pow_tab, stream);
+  if (st != MSK_OK) return st;
+  ctx->pow_gen = ctx->setup_gen;
+  ctx->pow_steps = steps;
+  ctx->pow_o2 = o2;
+  *out = ctx->pow_tab;
+  return MSK_OK;
+}
+
+msk_status launch_omega_tab(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
+                            const double* F, double* Wt, const float* pow_tab, cudaStream_t stream) {
   msk_status st0 = msk_prepare_omega(ctx);
   if (st0 != MSK_OK) return st0;
   const int64_t n = paths * steps;
@@ -242,10 +461,21 @@ msk_status launch_omega(msk_ctx* ctx, int order, int steps, int64_t paths, int p
     st0 = ensure_var_tables(ctx, stream);
     if (st0 != MSK_OK) return st0;
   }
+  const int rows = power_norm_rows(ctx, steps);
   OmegaArgs a{ctx->band, ctx->aux, (ctx->xprof || ctx->gen) ? ctx->var_tab : nullptr, var_table_ops(ctx), nullptr,
-              ctx->d, order, steps, precision, paths, ctx->T, ctx->dx, omega_coef(ctx), kMskScaleCap};
+              rows ? pow_tab : nullptr, rows, ctx->d, order, steps, precision, paths, ctx->T, ctx->dx,
+              omega_coef(ctx), kMskScaleCap};
   omega_kernel<<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(a, F, Wt);
   return msk_cuda(ctx, cudaGetLastError(), "omega kernel");
+}
+
+msk_status launch_omega(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
+                        const double* F, double* Wt, cudaStream_t stream) {
+  if (paths * steps == 0) return MSK_OK;
+  const float* tab = nullptr;
+  msk_status st = ensure_power_norms(ctx, order, steps, stream, &tab);
+  if (st != MSK_OK) return st;
+  return launch_omega_tab(ctx, order, steps, paths, precision, F, Wt, tab, stream);
 }
 
 // Weight records of arbitrary intervals: job_th_dev[2 i], [2 i + 1] = (t0, h) of
@@ -260,7 +490,8 @@ msk_status launch_omega_jobs(msk_ctx* ctx, int order, int64_t njobs, int precisi
     if (st0 != MSK_OK) return st0;
   }
   OmegaArgs a{ctx->band, ctx->aux, (ctx->xprof || ctx->gen) ? ctx->var_tab : nullptr, var_table_ops(ctx),
-              job_th_dev, ctx->d, order, 1, precision, njobs, ctx->T, ctx->dx, omega_coef(ctx), kMskScaleCap};
+              job_th_dev, nullptr, 0, ctx->d, order, 1, precision, njobs, ctx->T, ctx->dx, omega_coef(ctx),
+              kMskScaleCap};
   omega_kernel<<<(unsigned)((njobs + 127) / 128), 128, 0, stream>>>(a, F, Wt);
   return msk_cuda(ctx, cudaGetLastError(), "omega kernel (intervals)");
 }
@@ -278,4 +509,17 @@ extern "C" msk_status msk_omega_weights(msk_ctx* ctx, int order, int steps, int6
   msk_status st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
   if (st != MSK_OK) return st;
   return launch_omega(ctx, order, steps, paths, precision, F_dev, Wt_dev, (cudaStream_t)stream);
+}
+
+extern "C" msk_status msk_power_norms(msk_ctx* ctx, int order, int steps, float* out_dev, int* rows_out,
+                                      void* stream) {
+  if (!ctx || !rows_out) return MSK_ERR_ARG;
+  if (order < 1 || order > 3) return msk_fail(ctx, MSK_ERR_ARG, "order must be 1, 2 or 3");
+  if (steps < 1 || ctx->n_fine % steps != 0)
+    return msk_fail(ctx, MSK_ERR_ARG, "steps must be >= 1 and divide n_fine");
+  *rows_out = power_norm_rows(ctx, steps);
+  if (*rows_out == 0 || !out_dev) return MSK_OK;   // null output: the row count only
+  msk_status st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
+  if (st != MSK_OK) return st;
+  return launch_power_norms(ctx, order, steps, out_dev, (cudaStream_t)stream);
 }

@@ -1,13 +1,14 @@
 // Longest-processing-time-first path order for the engines' dynamic queue:
-// a path's Taylor work is estimated by sum_n s_n m_n from its step records
-// (the scaling count and degree chosen per step), the paths are counting-sorted
+// a path's Taylor work is estimated from its step records (the expected number
+// of Taylor terms of each step, or s_n m_n where none was estimated), the paths
+// are counting-sorted
 // by decreasing estimate, and the engine's CTAs take them in that order from an
 // atomic counter, so the last paths handed out are the cheapest.
 #include "msk_internal.cuh"
 
 namespace {
 
-// Counting sort of the paths by decreasing estimated cost sum_n s_n m_n, in one
+// Counting sort of the paths by decreasing estimated cost, in one
 // block: histogram of the (capped) costs in shared memory, a block-wide
 // exclusive scan, then a scatter.  Paths of equal cost keep no particular order
 // (the solution of a path does not depend on which CTA solves it).
@@ -20,7 +21,8 @@ __device__ __forceinline__ int order_bucket(const double* Wt, int steps, int64_t
 #pragma unroll 4
   for (int n = 0; n < steps; ++n) {
     const double* o = Wt + ((size_t)p * steps + n) * MSK_NWT;
-    c += o[MSK_WT_S] * o[MSK_WT_M];
+    // expected stencil applications when the weight kernel estimated them, else s m
+    c += o[MSK_WT_WORK] > 0.0 ? o[MSK_WT_WORK] : o[MSK_WT_S] * o[MSK_WT_M];
   }
   const int ci = c < (double)(kOrderBuckets - 1) ? (int)c : kOrderBuckets - 1;   // NaN -> cap
   return kOrderBuckets - 1 - ci;   // costliest first

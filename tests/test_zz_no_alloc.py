@@ -112,6 +112,11 @@ def test_noalloc_refuses_requests_beyond_the_static_scratch():
         st = lib.msk_solve_magnus_noalloc(s.ctx, 2, steps, paths, msk.MSK_F64, out.data_ptr(), None, stream)
         assert st == msk.MSK_ERR_ARG
         assert "static scratch" in msk.msk_last_error(s.ctx)
+    # the streamed engine needs library scratch: refused, before any device work
+    msk.msk_set_engine(s.ctx, msk.MSK_ENGINE_STREAMED)
+    st = lib.msk_solve_magnus_noalloc(s.ctx, 2, 1, 3, msk.MSK_F64, out.data_ptr(), None, stream)
+    assert st == msk.MSK_ERR_UNSUPPORTED
+    msk.msk_set_engine(s.ctx, msk.MSK_ENGINE_AUTO)
     # the context is still usable after the refusals
     u = s.state(3)
     msk.msk_solve_magnus_noalloc(s.ctx, 2, 1, 3, msk.MSK_F64, u)
