@@ -75,6 +75,10 @@ def parse():
     p.add_argument("--profile-grid", type=int, default=128, choices=(128, 512, 100, 200, 300),
                    help="grid of --profile-case: 128 (the bench workload, m3, K = 8) or 512 "
                         "(sigma = 0.5, m2, K = 64)")
+    p.add_argument("--profile-engine", default="auto", choices=("auto", "resident", "streamed"),
+                   help="engine of the --profile-case solves")
+    p.add_argument("--profile-precision", default="f32", choices=("f32", "f64"),
+                   help="precision of the --profile-case solves")
     p.add_argument("--profile-case", type=int, default=0, metavar="PATHS",
                    help="run two plain solves of the benchmark workload with PATHS paths at K = 8 "
                         "(a small case for ncu captures) and exit")
@@ -1057,7 +1061,10 @@ def run_large512(a):
     """512^2 grids (262144 unknowns) on [-8, 8]^2, a = 1, sigma in {0.25, 0.5, 1}: order-2
     float Magnus on 1024 paths each at the cheapest K in {8, 16, 32, 64} whose Err against the
     closed-form solution is <= 1e-3 with no path flagged (non-finite / blow-up) on a 128-path
-    subset; sigma = 1 (a = sigma^2, degenerate) is reported at K = 64 without a gate."""
+    subset; sigma = 1 (a = sigma^2, degenerate) is reported at K = 64 without a gate.  Each
+    solve is timed on both engines (resident 16-CTA clusters, streamed one CTA per path); the
+    step runs the faster.  The double-precision solution of all 1024 paths (streamed engine)
+    gives the float form's relative L2 error per path and its own speed."""
     import torch
 
     import paper_2207_09776_b300 as msk
@@ -1073,13 +1080,28 @@ def run_large512(a):
     msk.load_library()
     stream = torch.cuda.current_stream()
     order, sub = 2, 128
-    peaks, peak_src = measured_peaks()
-    fp32_peak = 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    peaks, _ = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    fp32_peak = fma_peak(msk, local, stream, msk.MSK_F32)
+    fp64_peak = fma_peak(msk, local, stream, msk.MSK_F64)
     per_sigma = {}
-    total_ms, total_paths, total_flops = 0.0, 0, 0.0
+    tot = {"ms": 0.0, "paths": 0, "pts": 0.0}
+    eng_tot = {m: {"ms": 0.0, "pts": 0.0} for m in ("resident", "streamed")}
     clocks = ClockSampler(local)
     started = False
     reps = max(1, a.steps // 3)
+    modes = {"resident": msk.MSK_ENGINE_RESIDENT, "streamed": msk.MSK_ENGINE_STREAMED}
+
+    def timed(s, K, P, prec, out, st):
+        msk.msk_work_counter(s.ctx, reset=True, stream=stream)
+        e0, e1 = _events(torch, stream)
+        e0.record(stream)
+        for _ in range(reps):
+            msk.msk_solve_magnus(s.ctx, order, K, P, prec, out, st, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, msk.msk_work_counter(s.ctx, reset=True, stream=stream) / reps
+
     for w0 in LARGE_512:
         w = w0.with_(path_offset=rank * w0.paths)
         s = msk.Solver(w, device=local)
@@ -1102,50 +1124,88 @@ def run_large512(a):
             if not bool((st != 0).any()) or K >= K_CANDIDATES[-1] or w.s0 >= 1.0:
                 break
             K = K_CANDIDATES[K_CANDIDATES.index(K) + 1]
-        msk.msk_work_counter(s.ctx, reset=True, stream=stream)
         if not started:
             clocks.start()
             started = True
-        e0, e1 = _events(torch, stream)
-        e0.record(stream)
-        for _ in range(reps):
-            msk.msk_solve_magnus(s.ctx, order, K, P, msk.MSK_F32, out, st, stream)
-        e1.record(stream)
+        eng = {}
+        for name, mode in modes.items():
+            msk.msk_set_engine(s.ctx, mode)
+            msk.msk_solve_magnus(s.ctx, order, K, P, msk.MSK_F32, out, st, stream)   # warm (scratch)
+            ms, mv = timed(s, K, P, msk.MSK_F32, out, st)
+            eng[name] = {"ms": ms, "paths_per_s": P / (ms / 1e3), "matvecs_per_path": mv / P,
+                         "tflops": mv * w.d * w.d * FLOPS_PER_POINT / (ms / 1e3) / 1e12,
+                         "hbm_equivalent_gbs": mv * w.d * w.d * 8 / (ms / 1e3) / 1e9}
+            eng_tot[name]["ms"] += ms
+            eng_tot[name]["pts"] += mv * w.d * w.d
+        best = min(eng, key=lambda k: eng[k]["ms"])
+        msk.msk_set_engine(s.ctx, modes[best])
+        msk.msk_solve_magnus(s.ctx, order, K, P, msk.MSK_F32, out, st, stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        mv = msk.msk_work_counter(s.ctx, reset=True, stream=stream) / reps
         errs, _ = s.error(out, msk.MSK_F32)
         errs = errs.cpu()
         ok = torch.isfinite(errs)
+        # double precision (streamed engine) for every path: its speed, and the float error per path
+        msk.msk_set_engine(s.ctx, msk.MSK_ENGINE_AUTO)
+        out64 = s.state(P, msk.MSK_F64)
+        st64 = torch.zeros(P, dtype=torch.int32, device="cuda")
+        msk.msk_work_counter(s.ctx, reset=True, stream=stream)
+        e0, e1 = _events(torch, stream)
+        e0.record(stream)
+        msk.msk_solve_magnus(s.ctx, order, K, P, msk.MSK_F64, out64, st64, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        mv64 = msk.msk_work_counter(s.ctx, reset=True, stream=stream)
+        okb = ((st == 0) & (st64 == 0)).cpu()
+        d32 = (out.double() - out64).reshape(P, -1).norm(dim=1) / out64.reshape(P, -1).norm(dim=1)
+        d32 = d32.cpu()[okb]
         per_sigma[f"sigma{w.s0}"] = {
-            "K": K, "gated": w.s0 < 1.0 and chosen is not None, "paths_per_s": P / (ms / 1e3), "ms": ms,
+            "K": K, "gated": w.s0 < 1.0 and chosen is not None, "engine": best,
+            "paths_per_s": P / (eng[best]["ms"] / 1e3), "ms": eng[best]["ms"],
             "err_vs_closed_form_mean_finite": float(errs[ok].mean()) if bool(ok.any()) else None,
-            "flagged_paths": int((st != 0).sum()), "matvecs_per_path": mv / P,
-            "tflops": mv * w.d * w.d * FLOPS_PER_POINT / (ms / 1e3) / 1e12, f"sweep_{sub}_paths": sweep}
-        total_ms += ms
-        total_paths += P
-        total_flops += mv * w.d * w.d * FLOPS_PER_POINT
+            "flagged_paths": int((st != 0).sum()), "engines": eng,
+            "double": {"paths_per_s": P / (ms64 / 1e3), "ms": ms64, "matvecs_per_path": mv64 / P,
+                       "tflops": mv64 * w.d * w.d * FLOPS_PER_POINT / (ms64 / 1e3) / 1e12,
+                       "frac_of_fp64_fma_peak": mv64 * w.d * w.d * FLOPS_PER_POINT / (ms64 / 1e3) / 1e12 / fp64_peak,
+                       "flagged_paths": int((st64 != 0).sum())},
+            "float_vs_double_rel_l2": {"paths": int(okb.sum()), "mean": float(d32.mean()) if len(d32) else None,
+                                       "max": float(d32.max()) if len(d32) else None},
+            f"sweep_{sub}_paths": sweep}
+        tot["ms"] += eng[best]["ms"]
+        tot["paths"] += P
+        tot["pts"] += eng[best]["matvecs_per_path"] * P * w.d * w.d
         s.close()
     clk = clocks.stop()
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
+        t = torch.tensor([tot["ms"]], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    achieved = total_flops / (total_ms / 1e3) / 1e12
-    line = {"metric": METRIC, "value": world * total_paths / (total_ms / 1e3), "unit": "paths/s", "n_gpus": world,
-            "steps": reps, "warmup": max(a.warmup, 1), "ms_per_step": total_ms,
+        tot["ms"] = float(t.item())
+    streamed = eng_tot["streamed"]
+    st_gbs = streamed["pts"] * 8 / (streamed["ms"] / 1e3) / 1e9
+    achieved = tot["pts"] * FLOPS_PER_POINT / (tot["ms"] / 1e3) / 1e12
+    line = {"metric": METRIC, "value": world * tot["paths"] / (tot["ms"] / 1e3), "unit": "paths/s", "n_gpus": world,
+            "steps": reps, "warmup": max(a.warmup, 1), "ms_per_step": tot["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "langevin_const_d512_sigma_0.25_0.5_1", "d": 512, "paths_per_gpu": total_paths,
+            "config": {"workload": "langevin_const_d512_sigma_0.25_0.5_1", "d": 512, "paths_per_gpu": tot["paths"],
                        "order": order, "n_fine": LARGE_512[0].n_fine,
-                       "step": "one float solve of 1024 paths for each of the three sigma, at each one's K",
+                       "step": "one float solve of 1024 paths for each of the three sigma, at each one's K, "
+                               "on the faster engine",
                        "err_target": "1e-3 vs the closed form, no flagged path (sigma = 1 not gated)",
-                       "double_precision": "not built at 512^2 (two double slabs exceed 16 CTAs' shared memory)",
                        "parallelism": f"replicas x{world} (path ranges)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": None,
-                         "kernel": "engine_kernel<float,512,16,512> (16-CTA clusters, DSMEM halos)",
-                         "hbm_equivalent": hbm_equivalent(total_flops / FLOPS_PER_POINT, total_ms / 1e3)},
+                         "kernel": "the faster engine per sigma (per_sigma.engine)",
+                         "peak_note": "measured FMA-chain throughput (msk_fma_throughput)"},
+            "streamed_engine": {"bound": "hbm", "achieved": st_gbs, "peak": hbm_peak, "unit": "GB/s",
+                                "frac": st_gbs / hbm_peak,
+                                "note": "algorithmic bytes: 8 per grid point per stencil application (read + "
+                                        "write of the float state); the engine moves 16 bytes per point per "
+                                        "sweep of 4 applications, so its DRAM traffic is about half of these",
+                                "tflops": streamed["pts"] * FLOPS_PER_POINT / (streamed["ms"] / 1e3) / 1e12,
+                                "frac_of_fp32_fma_peak": streamed["pts"] * FLOPS_PER_POINT / (streamed["ms"] / 1e3)
+                                / 1e12 / fp32_peak},
+            "fp64_fma_peak_tflops": fp64_peak,
             "per_sigma": per_sigma, "clocks": clk, "gpu_launches": 3 * (3 + queued(P)) * reps}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -1399,13 +1459,16 @@ def run_profile_case(a):
     else:
         w, K, order = LANGEVIN_TRIG_128.with_(paths=P), K_CANDIDATES[0], ORDER
     s = msk.Solver(w)
+    msk.msk_set_engine(s.ctx, {"auto": msk.MSK_ENGINE_AUTO, "resident": msk.MSK_ENGINE_RESIDENT,
+                               "streamed": msk.MSK_ENGINE_STREAMED}[a.profile_engine])
+    prec = msk.MSK_F32 if a.profile_precision == "f32" else msk.MSK_F64
     F = torch.empty(P * K * msk.MSK_NF, dtype=torch.float64, device="cuda")
     Wt = torch.empty(P * K * msk.MSK_NWT, dtype=torch.float64, device="cuda")
-    out = torch.empty(P * w.d * w.d, dtype=torch.float32, device="cuda")
+    out = torch.empty(P * w.d * w.d, dtype=torch.float32 if prec == msk.MSK_F32 else torch.float64, device="cuda")
     for _ in range(2):
-        msk.msk_brownian_functionals_ex(s.ctx, K, P, msk.MSK_F32, F)
-        msk.msk_omega_weights(s.ctx, order, K, P, msk.MSK_F32, F, Wt)
-        msk.msk_magnus_from_weights(s.ctx, K, P, msk.MSK_F32, Wt, out)
+        msk.msk_brownian_functionals_ex(s.ctx, K, P, prec, F)
+        msk.msk_omega_weights(s.ctx, order, K, P, prec, F, Wt)
+        msk.msk_magnus_from_weights(s.ctx, K, P, prec, Wt, out)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": P, "matvecs": msk.msk_work_counter(s.ctx)}))
     s.close()

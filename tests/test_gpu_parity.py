@@ -465,12 +465,12 @@ def test_d256_cluster_slabs_match_the_oracle(precision, tol):
 def test_d512_sixteen_cta_clusters_match_the_oracle():
     w = LARGE_512[1].with_(paths=1, T=0.05, n_fine=64)
     s = solver(w)
+    msk.msk_set_engine(s.ctx, msk.MSK_ENGINE_RESIDENT)   # the automatic choice streams 512^2
     u = s.magnus(2, 1, precision=msk.MSK_F32)
     ref = _oracle_magnus(w, 2, 1, [0])
     assert rel_l2(u.cpu().numpy(), ref).max() <= TOL32
     # double at 512^2 does not fit a cluster's shared memory: the resident engine
     # refuses it (the automatic choice runs the streamed engine, tests/test_gpu_stream.py)
-    msk.msk_set_engine(s.ctx, msk.MSK_ENGINE_RESIDENT)
     with pytest.raises(msk.MskError) as e:
         s.magnus(2, 1, precision=msk.MSK_F64)
     assert e.value.status == msk.MSK_ERR_UNSUPPORTED
@@ -485,6 +485,7 @@ def test_d512_full_size_on_a_sampled_path():
     w = LARGE_512[1]
     assert w.paths == 1024 and w.d == 512 and w.s0 == 0.5
     s = solver(w)
+    msk.msk_set_engine(s.ctx, msk.MSK_ENGINE_RESIDENT)
     u, st = s.magnus(2, 64, precision=msk.MSK_F32, status=True)
     assert bool(torch.isfinite(u).all())
     assert int(st[: w.paths].max()) == 0
