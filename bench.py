@@ -60,12 +60,13 @@ def parse():
     p.add_argument("--no-comparators", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=0, help="paths in the CPU-oracle sample (0 = auto)")
     p.add_argument("--workload", default="trig128", choices=("trig128", "batch", "surrogate", "large512",
-                                                              "paper_var"),
+                                                              "paper_var", "small32", "step_sweep"),
                    help="trig128: the time-dependent 128^2 workload (default); batch: grids 64/128/256 "
                         "in ratio 4:2:1 of 16384 paths in one persistent launch; surrogate: the learned "
                         "surrogate of the 128^2 workload served 65536 paths per step with a 1%% Magnus audit; "
                         "large512: the 512^2 constant-coefficient grids, sigma = 0.25 / 0.5 / 1, 1024 paths, m2")
     p.add_argument("--no-surrogate", action="store_true", help="skip the surrogate summary of the default line")
+    p.add_argument("--no-fp64", action="store_true", help="skip the timed double-precision sub-line")
     p.add_argument("--clock-csv-dir", default=None,
                    help="directory for the clock samples taken during the timed region (default: a temporary one)")
     p.add_argument("--surrogate-profile-case", type=int, default=0, metavar="PATHS",
@@ -531,6 +532,106 @@ def surrogate_serve(msk, torch, solver, s, steps, warmup, stream):
             "audit_tflops": aud_matvecs * n * FLOPS_PER_POINT / (t_aud / 1e3) / 1e12}, U
 
 
+# ------------------------------------------------------------------ double precision and Euler comparators
+
+def time_fp64(a, msk, torch, solver, ref, P, stream, dev):
+    """The plain double-precision Magnus form of the same step (double normals, functionals,
+    weights and Taylor action), K by the same fixed-error protocol, timed over the same
+    warm-up and step counts as the headline; its roofline is the measured double FMA rate."""
+    ctx, w = solver.ctx, solver.w
+    K64, sweep64 = None, {}
+    for Kc in K_CANDIDATES:
+        u = solver.magnus(ORDER, Kc, paths=REF_PATHS, precision=msk.MSK_F64)
+        _, em = solver.error(u, msk.MSK_F64, ref=ref, ref_precision=msk.MSK_F64)
+        sweep64[f"K{Kc}"] = float(em.cpu()[0])
+        if K64 is None and sweep64[f"K{Kc}"] <= ERR_TARGET:
+            K64 = Kc
+    K64 = K64 or K_CANDIDATES[-1]
+    F = torch.empty(P * K64 * msk.MSK_NF, dtype=torch.float64, device=dev)
+    Wt = torch.empty(P * K64 * msk.MSK_NWT, dtype=torch.float64, device=dev)
+    out = torch.empty(P * w.d * w.d, dtype=torch.float64, device=dev)
+    st = torch.zeros(P, dtype=torch.int32, device=dev)
+    ev = [_events(torch, stream) for _ in range(a.steps)]
+
+    def step(i=None):
+        msk.msk_brownian_functionals_ex(ctx, K64, P, msk.MSK_F64, F, stream)
+        msk.msk_omega_weights(ctx, ORDER, K64, P, msk.MSK_F64, F, Wt, stream)
+        if i is not None:
+            ev[i][0].record(stream)
+        msk.msk_magnus_from_weights(ctx, K64, P, msk.MSK_F64, Wt, out, st, stream)
+        if i is not None:
+            ev[i][1].record(stream)
+
+    for _ in range(max(a.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    msk.msk_work_counter(ctx, reset=True, stream=stream)
+    t0, t1 = _events(torch, stream)
+    t0.record(stream)
+    for i in range(a.steps):
+        step(i)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / a.steps
+    engine_ms = sum(x.elapsed_time(y) for x, y in ev) / a.steps
+    pts = msk.msk_work_counter(ctx, reset=True, stream=stream) / a.steps * w.d * w.d
+    roof = engine_roofline(msk, torch.cuda.current_device(), stream, pts, engine_ms,
+                           "engine_kernel<double,128,2,256> (2-CTA clusters)", precision=msk.MSK_F64)
+    return {"value": P / (ms / 1e3), "unit": "paths/s", "ms_per_step": ms, "steps": a.steps,
+            "warmup": a.warmup, "K": K64, "err": sweep64[f"K{K64}"], "err_sweep": sweep64,
+            "dtype": "f64", "engine_ms": engine_ms, "roofline": roof,
+            "path_status_max": int(st.max().item())}
+
+
+EQ_NFINE = 65536          # fine Brownian cells of the equal-error comparison (Euler needs up to 65536 steps)
+EQ_MAGNUS_K = (4, 8, 16)
+EQ_EULER_N = (4096, 16384, 32768, 65536)
+
+
+def equal_error_vs_euler(msk, torch, solver, Pc, stream):
+    """Magnus (float, order 3) against Euler-Maruyama (float) at the same fixed error: both on
+    the same Philox paths refined to 2^16 fine cells, so that Euler can take up to 65536
+    steps; error against the double-precision order-3 Magnus solution with 1024 steps on
+    128 paths; each method at the cheapest setting with Err <= 1e-3, timed on the same
+    path count.  The context's Brownian grid is restored afterwards."""
+    ctx, w = solver.ctx, solver.w
+    msk.msk_set_seed(ctx, w.seed, w.path_offset, EQ_NFINE, w.T)
+    try:
+        ref = solver.magnus(ORDER, REF_K, paths=REF_PATHS, precision=msk.MSK_F64)
+        n = ref.shape[0]
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            s0, s1 = _events(torch, stream)
+            s0.record(stream)
+            r = fn()
+            s1.record(stream)
+            torch.cuda.synchronize()
+            return r, s0.elapsed_time(s1)
+        res = {"n_fine": EQ_NFINE, "paths_timed": Pc, "err_paths": n, "target": ERR_TARGET,
+               "magnus_fp32": {}, "euler_fp32": {}}
+        for Kc in EQ_MAGNUS_K:
+            u, ms = timed(lambda: solver.magnus(ORDER, Kc, paths=Pc, precision=msk.MSK_F32))
+            _, e = solver.error(u[:n].contiguous(), msk.MSK_F32, ref=ref, ref_precision=msk.MSK_F64)
+            res["magnus_fp32"][f"K{Kc}"] = {"paths_per_s": Pc / (ms / 1e3), "err": float(e.cpu()[0])}
+        for ne in EQ_EULER_N:
+            u, ms = timed(lambda: solver.euler(ne, paths=Pc, precision=msk.MSK_F32))
+            _, e = solver.error(u[:n].contiguous(), msk.MSK_F32, ref=ref, ref_precision=msk.MSK_F64)
+            res["euler_fp32"][f"N{ne}"] = {"paths_per_s": Pc / (ms / 1e3), "err": float(e.cpu()[0])}
+
+        def cheapest(tab):
+            ok = [(v["paths_per_s"], k) for k, v in tab.items() if v["err"] <= ERR_TARGET]
+            return max(ok)[1] if ok else None
+        km, ke = cheapest(res["magnus_fp32"]), cheapest(res["euler_fp32"])
+        res["magnus_choice"], res["euler_choice"] = km, ke
+        res["speedup_magnus_over_euler"] = (res["magnus_fp32"][km]["paths_per_s"] /
+                                            res["euler_fp32"][ke]["paths_per_s"]) if km and ke else None
+        return res
+    finally:
+        msk.msk_set_seed(ctx, w.seed, w.path_offset, w.n_fine, w.T)
+
+
 # ------------------------------------------------------------------ our implementation
 
 def run_ours(a):
@@ -665,6 +766,11 @@ def run_ours(a):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
+    # ---- the plain double-precision form, timed like the headline -----------------------
+    fp64 = None
+    if not a.no_fp64:
+        fp64 = time_fp64(a, msk, torch, solver, ref, P, stream, dev)
+
     # ---- comparators (untimed by the main loop; events) --------------------------------
     comparators = {}
     if not a.no_comparators:
@@ -692,6 +798,7 @@ def run_ours(a):
             comparators.setdefault("euler_fp32", {})[f"N{ne}"] = {
                 "paths_per_s": Pc / (msem / 1e3), "err": float(eem.cpu()[0])}
         comparators["magnus_fp32_sweep_err"] = {f"K{k}": v for k, v in sweep.items()}
+        comparators["equal_error_vs_euler"] = equal_error_vs_euler(msk, torch, solver, Pc, stream)
         comparators["step_control"] = step_control
         for Kc in K_CANDIDATES:   # order 2 on the same paths and reference
             u2, ms2 = timed(lambda: solver.magnus(2, Kc, paths=Pc, precision=msk.MSK_F32))
@@ -763,6 +870,7 @@ def run_ours(a):
         "clocks": clk,
         "gpu_launches": (3 + queued(P)) * a.steps,   # functionals, weights, [path order,] engine
         "path_status_max": status_bits,
+        "fp64": fp64,
         "comparators": comparators,
     }
     solver.close()
@@ -1211,6 +1319,174 @@ def run_large512(a):
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ small grid, one Magnus step (configuration 1)
+
+SMALL_REPS = 200
+
+
+def run_small32(a):
+    """du = (1/2 u_vv + v u_x) dt + 1/2 u_v dW on a 32 x 32 grid over [-5, 5]^2, standard
+    Gaussian u0, 100 Philox paths, T = 1: double-precision Magnus orders 1 and 2 with one
+    step against Euler-Maruyama with 1000 steps, all against the closed-form solution.
+    The target error is Euler's own (Err of Euler 1000); each method is timed on the 100
+    paths, SMALL_REPS solves per timed step."""
+    import torch
+
+    import paper_2207_09776_b300 as msk
+    from paper_2207_09776_b300 import build as mbuild
+    from workloads import LANGEVIN_32
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    mbuild.build()
+    msk.load_library()
+    stream = torch.cuda.current_stream()
+    w = LANGEVIN_32.with_(path_offset=rank * LANGEVIN_32.paths)
+    s = msk.Solver(w, device=local)
+    P = w.paths
+    out = s.state(P, msk.MSK_F64)
+    st = torch.zeros(P, dtype=torch.int32, device="cuda")
+    methods = {"magnus_m1_K1": lambda: msk.msk_solve_magnus(s.ctx, 1, 1, P, msk.MSK_F64, out, st, stream),
+               "magnus_m2_K1": lambda: msk.msk_solve_magnus(s.ctx, 2, 1, P, msk.MSK_F64, out, st, stream),
+               "euler_N1000": lambda: msk.msk_solve_euler(s.ctx, 1000, P, msk.MSK_F64, out, st, stream)}
+    res = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    for name, fn in methods.items():
+        fn()
+        torch.cuda.synchronize()
+        errs, em = s.error(out, msk.MSK_F64)
+        e = float(em.cpu()[0])
+        for _ in range(max(a.warmup, 1)):
+            fn()
+        t0, t1 = _events(torch, stream)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for _ in range(a.steps * SMALL_REPS):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / (a.steps * SMALL_REPS)
+        res[name] = {"err_vs_closed_form": e, "err_max_path": float(errs.max().cpu()),
+                     "paths_per_s": P / (ms / 1e3), "ms_per_solve": ms}
+    clk = clocks.stop()
+    target = res["euler_N1000"]["err_vs_closed_form"]
+    for v in res.values():
+        v["meets_target"] = v["err_vs_closed_form"] <= target * (1 + 1e-12)
+    best = "magnus_m2_K1"
+    line = {"metric": METRIC, "value": world * res[best]["paths_per_s"], "unit": "paths/s", "n_gpus": world,
+            "steps": a.steps, "warmup": max(a.warmup, 1), "ms_per_step": res[best]["ms_per_solve"] * SMALL_REPS,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "langevin_const_d32", "d": 32, "paths_per_gpu": P, "T": w.T,
+                       "n_fine": w.n_fine, "reference": "closed-form solution (Gaussian)",
+                       "err_target": "Err of Euler-Maruyama with 1000 steps",
+                       "step": f"{SMALL_REPS} solves of the 100 paths",
+                       "parallelism": f"replicas x{world} (path ranges)"},
+            "methods": res, "err_target": target,
+            "speedup_m2_over_euler": res[best]["paths_per_s"] / res["euler_N1000"]["paths_per_s"],
+            "note": "order 1 carries no Ito correction (Stratonovich-consistent), so its error does not "
+                    "shrink with the step", "clocks": clk, "gpu_launches": 4 * a.steps * SMALL_REPS}
+    s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ step-size experiments (Section 3.1 / 3.2)
+
+# Magnus steps per unit time of the sweeps: the constant-coefficient sweep resolves the
+# paper's thresholds (m2: fluctuations above 0.065, explosion near 0.085; m3: above 0.1 and
+# 0.33) on a fine Brownian grid divisible by every K; the variable-coefficient sweep keeps
+# that workload's 10^5 fine cells (K must divide them; the Euler reference takes 10^4 steps)
+SWEEP_K_CONST = (100, 50, 25, 20, 16, 15, 14, 13, 12, 11, 10, 8, 6, 5, 4, 3, 2)
+SWEEP_NFINE_CONST = 1_201_200          # lcm of SWEEP_K_CONST
+SWEEP_K_VAR = (100, 80, 50, 40, 32, 25, 20, 16, 10, 8, 5, 4, 2)
+SWEEP_EULER_REF = 10_000               # Euler step 1e-4 (the reference of Fig. StepTestVar)
+
+
+def run_step_sweep(a):
+    """Fig. StepTest (Section 3.1) and Fig. StepTestVar (Section 3.2): d = 200, 100 paths,
+    the paper's constant coefficients (a = 1.1, sigma = 1/sqrt(10), -v d_x, [-4, 4]^2,
+    phi = exp(-(x^2 + v^2)/2)) and then the x profile psi = 1 + 1/(1 + x^2); Magnus orders 2
+    and 3 over a range of step sizes.  Per step size: time per path, mean relative error on
+    the central 1/16 of the grid (kappa = 4, the paper's measure) and on the central quarter
+    (kappa = 1), and the number of exploding paths (MSK_PATH_BLOWUP or non-finite).
+    References: the closed-form solution (constant coefficients), Euler-Maruyama with step
+    1e-4 in double precision (x profile).  Float Taylor arithmetic on the variable-
+    coefficient engine (d = 200 is not a multiple of 32; psi = 1 for the constant case)."""
+    import torch
+
+    import paper_2207_09776_b300 as msk
+    from paper_2207_09776_b300 import build as mbuild
+    from workloads import PAPER_CONST, PAPER_VAR
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    mbuild.build()
+    msk.load_library()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+
+    def sweep(s, ref, Ks, P):
+        res = {}
+        for order in (2, 3):
+            rows = {}
+            for K in Ks:
+                out = s.state(P, msk.MSK_F32)
+                st = torch.zeros(P, dtype=torch.int32, device="cuda")
+                msk.msk_solve_magnus(s.ctx, order, K, P, msk.MSK_F32, out, st, stream)   # warm
+                t0, t1 = _events(torch, stream)
+                t0.record(stream)
+                msk.msk_solve_magnus(s.ctx, order, K, P, msk.MSK_F32, out, st, stream)
+                t1.record(stream)
+                torch.cuda.synchronize()
+                ms = t0.elapsed_time(t1)
+                bad = (st != 0).cpu()
+                row = {"dt": 1.0 / K, "ms_per_path": ms / P, "exploded": int(bad.sum())}
+                for kappa in (4, 1):
+                    e, _ = s.error(out, msk.MSK_F32, ref=ref, ref_precision=msk.MSK_F64, kappa=kappa)
+                    e = e.cpu()
+                    good = ~bad & torch.isfinite(e)
+                    row[f"err_k{kappa}"] = float(e.mean())
+                    row[f"err_k{kappa}_unexploded"] = float(e[good].mean()) if bool(good.any()) else None
+                rows[f"K{K}"] = row
+            res[f"m{order}"] = rows
+        return res
+
+    out_line = {}
+    # ---- constant coefficients, closed-form reference ---------------------------------
+    wc = PAPER_CONST.with_(d=200, n_fine=SWEEP_NFINE_CONST, paths=100)
+    sref = msk.Solver(wc, device=local)
+    ref_c = sref.explicit()
+    s = msk.Solver(wc, device=local)
+    msk.msk_set_x_profile(s.ctx, msk.MSK_XPROF_VALUES, psi=[1.0] * wc.d)
+    out_line["constant"] = sweep(s, ref_c, SWEEP_K_CONST, wc.paths)
+    s.close()
+    sref.close()
+    # ---- x profile, Euler 1e-4 reference (double) ---------------------------------------
+    wv = PAPER_VAR[1].with_(paths=100)
+    s = msk.Solver(wv, device=local)
+    ref_v = s.euler(SWEEP_EULER_REF, precision=msk.MSK_F64)
+    out_line["x_profile"] = sweep(s, ref_v, SWEEP_K_VAR, wv.paths)
+    s.close()
+    clk = clocks.stop()
+
+    m3 = out_line["constant"]["m3"]["K10"]
+    line = {"metric": METRIC, "value": 1e3 / m3["ms_per_path"], "unit": "paths/s", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": m3["ms_per_path"] * 100, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "paper_step_sweep_d200", "d": 200, "paths_per_gpu": 100,
+                       "value_is": "order 3, step 0.1, constant coefficients",
+                       "n_fine_constant": SWEEP_NFINE_CONST, "n_fine_x_profile": PAPER_VAR[1].n_fine,
+                       "reference": {"constant": "closed form", "x_profile": "Euler-Maruyama, step 1e-4, double"}},
+            "sweeps": out_line, "clocks": clk, "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ variable coefficients (Table errorsVar)
 
 VAR_STEPS = {100: 20, 200: 40, 300: 100}       # the paper's Magnus step sizes 0.05, 0.025, 0.01
@@ -1493,6 +1769,10 @@ def main():
         run_large512(a)
     elif a.workload == "paper_var":
         run_paper_var(a)
+    elif a.workload == "small32":
+        run_small32(a)
+    elif a.workload == "step_sweep":
+        run_step_sweep(a)
     else:
         run_ours(a)
 

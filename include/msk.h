@@ -529,6 +529,17 @@ msk_status msk_surrogate_infer(msk_surrogate* s, int64_t path0, int64_t paths, f
                                uint32_t* flags_dev, int64_t audit_every, double tol,
                                double max_fail_frac, double* report_host, void* stream);
 
+/* Test hook of the failure path (no counterpart in the paper): with on != 0 every
+ * tensor-core GEMM of this surrogate makes its epilogue warps first wait on an
+ * mbarrier that no thread ever arrives at, for a bounded number of polls.  The
+ * wait runs out on a healthy pipeline: the warps skip their tiles (still
+ * releasing each accumulator), the producer waits for its issued TMA loads and the
+ * MMA issuer for its issued MMAs, TMEM is freed, and the next
+ * msk_surrogate_sync_status returns MSK_ERR_TIMEOUT (the error word stays set for
+ * this surrogate).  The outputs of those calls are undefined.  The GPU context
+ * stays usable.  on = 0 restores normal operation (the word is not cleared). */
+msk_status msk_surrogate_set_wait_test(msk_surrogate* s, int on);
+
 /* Synchronise `stream` and report the surrogate's device status: MSK_ERR_TIMEOUT
  * if a tensor-core pipeline wait of any earlier call ran out (the affected
  * outputs are invalid), else MSK_OK. */

@@ -120,6 +120,7 @@ SIGNATURES = {
     "msk_surrogate_train": (_INT, [_P, _P, _P, _I64, _INT, ctypes.c_float, _P, _P]),
     "msk_surrogate_infer": (_INT, [_P, _I64, _I64, _P, _P, _I64, _DBL, _DBL, ctypes.POINTER(_DBL), _P]),
     "msk_surrogate_sync_status": (_INT, [_P, _P]),
+    "msk_surrogate_set_wait_test": (_INT, [_P, _INT]),
     "msk_select_steps": (_INT, [_P, _DBL, _INT, _INT, _I64, _INT, ctypes.POINTER(_INT), ctypes.POINTER(_DBL),
                                 ctypes.POINTER(_INT), _P]),
     "msk_explicit_solution": (_INT, [_P, _I64, _P, _P]),
@@ -589,6 +590,12 @@ def msk_surrogate_infer(s, path0, paths, U, flags=None, audit_every=0, tol=1e-2,
     _scheck(load_library().msk_surrogate_infer(s, path0, paths, _ptr(U), _ptr(flags), audit_every, tol,
                                                max_fail_frac, rep, _stream(stream)), s)
     return list(rep)
+
+
+def msk_surrogate_set_wait_test(s, on):
+    """Test hook: the GEMM epilogues wait on a barrier nothing arrives at (bounded), so the
+    next msk_surrogate_sync_status raises MSK_ERR_TIMEOUT."""
+    _scheck(load_library().msk_surrogate_set_wait_test(s, int(bool(on))), s)
 
 
 def msk_surrogate_sync_status(s, stream=None):

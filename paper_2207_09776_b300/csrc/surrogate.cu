@@ -68,6 +68,7 @@ struct msk_surrogate {
   double* aerr = nullptr;
   size_t aerr_bytes = 0;
   uint32_t* dev_err = nullptr;        // set by kernels whose bounded waits ran out
+  int wait_test = 0;                  // msk_surrogate_set_wait_test
   cudaStream_t aud = nullptr;         // audit stream (higher priority), overlaps the serve kernels
   cudaEvent_t ev_in = nullptr, ev_aud = nullptr;
   std::map<std::tuple<uintptr_t, int, int, int, int>, CUtensorMap> maps;   // TMA descriptors
@@ -273,6 +274,7 @@ msk_status gemm(msk_surrogate* s, const bf16* A, int lda, int M, const bf16* B, 
   g.aux = o.aux;
   g.ldaux = o.ldaux;
   g.err = s->dev_err;
+  g.wait_test = s->wait_test;
   if (splits > 1) {
     g.C = s->ws;
     g.ldc = N;
@@ -1088,6 +1090,12 @@ extern "C" msk_status msk_surrogate_infer(msk_surrogate* s, int64_t path0, int64
     report_host[4] = whole ? 1.0 : 0.0;
   }
   return st;
+}
+
+extern "C" msk_status msk_surrogate_set_wait_test(msk_surrogate* s, int on) {
+  if (!s) return MSK_ERR_ARG;
+  s->wait_test = on ? 1 : 0;
+  return MSK_OK;
 }
 
 extern "C" msk_status msk_surrogate_sync_status(msk_surrogate* s, void* stream) {

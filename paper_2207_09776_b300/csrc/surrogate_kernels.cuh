@@ -115,10 +115,12 @@ struct TcArgs {
   const float* aux;      // EPI_GELU_BWD: pre-activation z [M][ldaux]
   int ldaux;
   uint32_t* err;         // bit 0 set if a pipeline wait ran out
+  int wait_test;         // test hook: the epilogue first waits on a barrier nothing arrives at
 };
 
 constexpr int TC_BM = 128, TC_BK = 64;
 constexpr uint32_t kTcWaitLimit = 1u << 24;   // polls of one mbarrier before giving up
+constexpr uint32_t kTcTestPolls = 1u << 10;    // polls of the test hook's wait (it never completes)
 
 // EPI_ADD_MEAN stages each epilogue warp's 32 x 32 float chunks in two 4 KB
 // buffers (128-byte swizzle) for TMA stores.
@@ -257,7 +259,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 //           (tmem_empty[b], eight arrivals), so the next tile's MMAs overlap
 //           this tile's epilogue.
 // Every mbarrier wait is bounded (kTcWaitLimit polls); on expiry the thread sets
-// g.err and the pipeline drains without further waits.
+// g.err, an epilogue warp skips its remaining tiles (releasing each accumulator),
+// the producer waits for its issued loads and the MMA issuer for its issued MMAs,
+// so no CTA leaves with a bulk copy or an MMA in flight.
 constexpr int TC_THREADS = 320;
 
 template <int BN, int EPI, int TC_STAGES>
@@ -277,7 +281,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(const __grid_con
   uint64_t* empty = full + TC_STAGES;
   uint64_t* tfull = empty + TC_STAGES;     // [2]
   uint64_t* tempty = tfull + 2;            // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* never = tempty + 2;            // test hook: no thread ever arrives here
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   uint8_t* stage_out = sB + TC_STAGES * B_BYTES + 1024;   // EPI_ADD_MEAN: [8 warps][2][32 rows x 128 B]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per_split = tiles_m * tiles_n, ntiles = per_split * splits;
@@ -294,6 +299,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(const __grid_con
       umma::mbar_init(tfull + b, 1);
       umma::mbar_init(tempty + b, 8);
     }
+    umma::mbar_init(never, 1);
     umma::fence_barrier_init();
   }
   if (warp == 1) umma::tmem_alloc(tmem_slot, 2 * BN);
@@ -339,6 +345,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(const __grid_con
       // ---- MMA issuer
       constexpr uint32_t idesc = umma::idesc_bf16_f32(TC_BM, BN);
       uint32_t it = 0, i = 0;
+      int last0 = -1, last1 = -1;   // tile of the last commit on accumulators 0 and 1
       for (int t = blockIdx.x; t < ntiles && !fail; t += gridDim.x, ++i) {
         const int z = t / per_split;
         int kbeg, nk;
@@ -365,7 +372,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(const __grid_con
           umma::mma_commit(empty + s);
         }
         umma::mma_commit(tfull + ab);   // arrives when this tile's MMAs are complete
+        if (ab) last1 = (int)i;
+        else last0 = (int)i;
       }
+      // every MMA issued has completed before TMEM can be freed, also when the epilogue
+      // gave up on a tile and no longer waits for it (bounded like every wait)
+      if (last0 >= 0 && !umma::mbar_wait(tfull + 0, ((uint32_t)last0 >> 1) & 1, kTcWaitLimit)) fail = true;
+      if (last1 >= 0 && !umma::mbar_wait(tfull + 1, ((uint32_t)last1 >> 1) & 1, kTcWaitLimit)) fail = true;
     }
   } else {
     // ---- epilogue warps
@@ -377,15 +390,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) gemm_tc_kernel(const __grid_con
       const int z = t / per_split, rem = t % per_split;
       const int m0 = (rem / tiles_n) * TC_BM, n0 = (rem % tiles_n) * BN;
       const uint32_t ab = i & 1;
-      const bool ready = __all_sync(0xffffffffu, umma::mbar_wait(tfull + ab, (i >> 1) & 1, kTcWaitLimit));
+      // after a wait has run out the warp waits no more: it skips its tiles but still
+      // releases each accumulator, so the MMA issuer and the TMA producer run to the end
+      bool ok = !fail;
+      if (ok && g.wait_test) ok = umma::mbar_wait(never, 0, kTcTestPolls);
+      if (ok) ok = umma::mbar_wait(tfull + ab, (i >> 1) & 1, kTcWaitLimit);
+      const bool ready = __all_sync(0xffffffffu, ok);
       umma::tc_fence_after();
-      if (!ready) {
-        fail = true;
-        break;
-      }
+      if (!ready) fail = true;
       const int m = m0 + quarter * 32 + lane;
 #pragma unroll 1
-      for (int c = half * CH; c < (half + 1) * CH; ++c) {
+      for (int c = half * CH; ready && c < (half + 1) * CH; ++c) {
         const int nb = n0 + c * 32;
         if (nb >= g.N) break;                                 // same for the whole warp
         uint32_t r[32];
