@@ -79,12 +79,16 @@ enum {
  *                 Al-Mohy & Higham's alpha_p(Omega - mu I) over the p with
  *                 p (p - 1) <= m + 1 (<= MSK_WT_NORM); alpha / s <= theta_m
  *   MSK_WT_WORK   expected stencil applications of the step (path ordering), 0 if unused
+ *   MSK_WT_EPS    ||E||_inf (a bound with an x profile or general coefficients) of the
+ *                 Brownian part E of Omega - mu I (the terms whose weights vanish with the
+ *                 functionals); s >= ||E|| / theta_E, theta_E = 14 (float), 24 (double)
  *   MSK_WT_MU     shift mu = trace(Omega) / n
  *   MSK_WT_NORM   ||Omega - mu I||_inf (exact for the Langevin operators; a bound
  *                 over the operators with an x profile or general coefficients)
  *   MSK_WT_S, MSK_WT_M  Taylor scaling count s and degree cap m (alpha / s <= theta_m). */
 #define MSK_NWT 20
-enum { MSK_WT_ALPHA = 13, MSK_WT_WORK = 14, MSK_WT_MU = 16, MSK_WT_NORM = 17, MSK_WT_S = 18, MSK_WT_M = 19 };
+enum { MSK_WT_ALPHA = 13, MSK_WT_WORK = 14, MSK_WT_EPS = 15, MSK_WT_MU = 16, MSK_WT_NORM = 17, MSK_WT_S = 18,
+       MSK_WT_M = 19 };
 
 /* Interior grid n_x x n_v on [ax,bx] x [av,bv]; Delta = (b - a)/(n + 1)
  * (Eq. xGrid, vGrid).  This build requires nx == nv. */

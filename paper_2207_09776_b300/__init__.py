@@ -26,7 +26,7 @@ MSK_REF_EXPLICIT, MSK_REF_BUFFER = 0, 1
 MSK_PATH_NONFINITE, MSK_PATH_SCALE_CAP, MSK_PATH_BLOWUP = 1, 2, 4
 MSK_NF, MSK_NOPS, MSK_NWT = 8, 13, 20
 MSK_F_DW, MSK_F_I1, MSK_F_I2, MSK_F_I3, MSK_F_OM, MSK_F_JOM, MSK_F_G1, MSK_F_G2 = range(8)
-MSK_WT_ALPHA, MSK_WT_WORK = 13, 14
+MSK_WT_ALPHA, MSK_WT_WORK, MSK_WT_EPS = 13, 14, 15
 MSK_WT_MU, MSK_WT_NORM, MSK_WT_S, MSK_WT_M = 16, 17, 18, 19
 OP_NAMES = ("Bx", "Bvv", "A0", "A0A0", "[Bx,A0]", "[Bvv,A0]", "[Bx,Bvv]", "[[Bx,A0],A0]",
             "[[Bvv,A0],A0]", "[[Bx,A0],Bx]", "[[Bx,A0],Bvv]", "[[Bvv,A0],Bx]", "[[Bvv,A0],Bvv]")

@@ -34,6 +34,22 @@
 #include "stencil.cuh"
 #include "theta_tables.h"
 
+// Largest norm of the Brownian part E of Omega - mu I per Taylor sub-step.  The
+// deterministic part is dissipative and centred by the trace shift, so its terms
+// grow only where the partial sum grows; E (Delta W A, the commutator terms) has
+// oscillatory spectrum, and its terms can grow like e^{||E|| / s} while the sum
+// stays bounded, so the rounding of the working precision is amplified by up to
+// that factor.  s is at least ||E|| / MSK_THETA_E.  In float, 14 (about theta_55
+// at the float tolerance) is where the large-step order-3 solves of the d = 200
+// step-size experiment explode on exactly the paths the double solves explode on
+// (without the bound, on up to 95 of 100 more); in double 24 changes no result.
+#ifndef MSK_THETA_E_F32
+#define MSK_THETA_E_F32 14.0
+#endif
+#ifndef MSK_THETA_E_F64
+#define MSK_THETA_E_F64 24.0
+#endif
+
 namespace {
 
 // reciprocals 1 / theta_m (one multiply per candidate degree instead of a double
@@ -286,32 +302,43 @@ __global__ void omega_kernel(OmegaArgs a, const double* __restrict__ F, double* 
       nrm = fmax(nrm, row_abs_sum(c));
     }
   }
+  // norm (or bound) of the Brownian part E of Omega - mu I: the operators whose weights
+  // vanish when every functional is zero
+  double wd[MSK_NOPS], f0[MSK_NF];
+  for (int k = 0; k < MSK_NF; ++k) f0[k] = 0.0;
+  magnus_weights(a, tn, h, f0, wd);
+  double eps = 0.0;
+  if (a.var && a.var_ops == MSK_NOPS) {
+    for (int k = 0; k < MSK_NOPS; ++k) eps += fabs(w[k] - wd[k]) * a.var[MSK_NOPS + k];
+  } else if (a.var) {
+    const int map6[6] = {MSK_OP_BX, MSK_OP_A0, MSK_OP_A0A0, MSK_OP_BX_A0, MSK_OP_BXA0_A0, MSK_OP_BXA0_BX};
+    for (int k = 0; k < 6; ++k) eps += fabs(w[map6[k]] - wd[map6[k]]) * a.var[6 + k];
+  }
   const double* ith = a.precision == MSK_F32 ? c_inv_theta32 : c_inv_theta64;
   const int mmax = a.precision == MSK_F32 ? MSK_THETA_MMAX_F32 : MSK_THETA_MMAX_F64;
   // d[q] >= ||(Omega - mu I)^q||^(1/q): d[1] the exact norm, d[2..J] from the
   // deterministic power norms (when available) and the norm of the Brownian part
   double dq[MSK_POW_J + 1];
   for (int q = 0; q <= MSK_POW_J; ++q) dq[q] = nrm;
-  if (a.pow_tab && nrm > 0.0) {
-    const int row = a.pow_rows == 1 ? 0 : (int)(idx % a.steps);
-    const float* g = a.pow_tab + (size_t)row * MSK_POW_J;
-    // Brownian part E = Omega - mu I - X: weights minus the zero-functional weights
-    double wd[MSK_NOPS], f0[MSK_NF];
-    for (int k = 0; k < MSK_NF; ++k) f0[k] = 0.0;
-    magnus_weights(a, tn, h, f0, wd);
-    double trd = 0.0;
+  if (!a.var) {
+    // Langevin operators: E = Omega - mu I - X exactly, X the zero-functional part with its
+    // own shift (the infinity norm of its folded stencil)
+    double we[MSK_NOPS], trd = 0.0;
     for (int k = 0; k < MSK_NOPS; ++k) {
       trd += wd[k] * a.trace[k];
-      wd[k] = w[k] - wd[k];
+      we[k] = w[k] - wd[k];
     }
     const double dmu = mu - trd / ((double)D * D);
-    double eps = 0.0;
     const int rows[6] = {0, 1, 2, D - 3, D - 2, D - 1};
     for (int r = 0; r < 6; ++r) {
       double c[MSK_NCOEF];
-      fold_row(a.band, D, rows[r], wd, -dmu, 0.5 / a.dx, 0.25 / (a.dx * a.dx), c);
+      fold_row(a.band, D, rows[r], we, -dmu, 0.5 / a.dx, 0.25 / (a.dx * a.dx), c);
       eps = fmax(eps, row_abs_sum(c));
     }
+  }
+  if (a.pow_tab && nrm > 0.0) {
+    const int row = a.pow_rows == 1 ? 0 : (int)(idx % a.steps);
+    const float* g = a.pow_tab + (size_t)row * MSK_POW_J;
     // the float table carries relative rounding far below 1e-4 (unit rows, at most
     // nine stencil products): inflate it by 2^-10 so it stays an upper bound
     double gx[MSK_POW_J + 1], Tq[MSK_POW_J + 1];
@@ -334,6 +361,7 @@ __global__ void omega_kernel(OmegaArgs a, const double* __restrict__ F, double* 
     for (int p = 2; p < MSK_POW_J; ++p)
       if (p * (p - 1) <= mmax + 1) amin = fmin(amin, alpha[p]);
     best_s = fmax(1.0, ceil(amin * ith[mmax - 1]));
+    best_s = fmax(best_s, ceil(eps / (a.precision == MSK_F32 ? MSK_THETA_E_F32 : MSK_THETA_E_F64)));
     if (!(best_s <= a.s_cap)) {   // also catches a non-finite norm
       best_s = a.s_cap;
       best_m = mmax;
@@ -355,6 +383,7 @@ __global__ void omega_kernel(OmegaArgs a, const double* __restrict__ F, double* 
   for (int k = 0; k < MSK_NOPS; ++k) o[k] = w[k];
   for (int k = MSK_NOPS; k < MSK_WT_MU; ++k) o[k] = 0.0;
   o[MSK_WT_ALPHA] = used;
+  o[MSK_WT_EPS] = eps;
   // expected Taylor terms: per sub-step about x + sqrt(2 x ln(1/tol)) with x = alpha / s
   // (the terms x^k / k! fall below the tolerance), capped by the degree
   if (nrm > 0.0) {

@@ -192,7 +192,9 @@ def test_taylor_parameters_are_admissible():
                 assert min([dq[0]] + alpha_p) <= al * (1 + rt) and al <= nrm * (1 + 1e-12)
                 assert 1 <= mv <= 120 and sv >= 1 and sv == int(sv) and mv == int(mv)
                 assert al / sv <= th[int(mv) - 1] * (1 + 1e-12)
-                assert sv == 1 or al > (sv - 1) * th[119]
+                eps, theta_e = rec[msk.MSK_WT_EPS], (14.0 if prec == msk.MSK_F32 else 24.0)
+                assert eps / sv <= theta_e * (1 + 1e-12)            # the Brownian part per sub-step
+                assert sv == 1 or al > (sv - 1) * th[119] or eps > (sv - 1) * theta_e
                 assert rec[msk.MSK_WT_WORK] > 0
                 gain.append(al / nrm)
         assert np.mean(gain) < 0.97          # the power bounds are sharper than the norm
