@@ -433,6 +433,15 @@ msk_status msk_prepare_omega(msk_ctx* ctx) {
 
 int power_norm_rows(const msk_ctx* ctx, int steps) {
   if (ctx->xprof || ctx->gen) return 0;      // those engines bound the norm over their operators
+  // Steps so short that the plain norm already allows one sub-step gain nothing from the
+  // power norms (the degree only caps an early-terminating series): an upper estimate
+  // of ||h B|| + ||A^2 term|| against half of the smaller theta_120 (double) skips them.
+  const double h = ctx->T / steps;
+  const double vmax = fmax(fabs(ctx->av), fabs(ctx->bv));
+  const double amax = fabs(ctx->coef.a0) + fabs(ctx->coef.kind == MSK_COEF_TRIG ? ctx->coef.a1 : 0.0);
+  const double smax = fabs(ctx->coef.s0) * (1.0 + fabs(ctx->coef.kind == MSK_COEF_TRIG ? ctx->coef.s1 : 0.0));
+  const double est = h * (vmax / ctx->dx + (amax + smax * smax) * 2.0 / (ctx->dv * ctx->dv));
+  if (est < 0.5 * msk_theta_f64[MSK_THETA_MMAX_F64 - 1]) return 0;
   return ctx->coef.kind == MSK_COEF_CONST ? 1 : steps;
 }
 
