@@ -324,8 +324,8 @@ extern "C" msk_status msk_batch_create(msk_batch** out, const msk_batch_item* it
     total += (size_t)items[k].paths * items[k].steps * MSK_NWT;
     b->o_off.push_back(total);
     total += (size_t)items[k].paths + 1;
-    b->p_off.push_back(total);
-    total += ((size_t)power_norm_rows(items[k].ctx, items[k].steps) * MSK_POW_J + 1) / 2;
+    b->p_off.push_back(total);   // room for one row per step: the most any coefficient set needs
+    total += ((size_t)items[k].steps * MSK_POW_J + 1) / 2;
   }
   if (st == MSK_OK) st = bcuda(b, cudaMalloc(&b->scratch, std::max<size_t>(total, 1) * sizeof(double)), "scratch");
   if (st == MSK_OK) st = bcuda(b, cudaMalloc(&b->d_counter, sizeof(unsigned int)), "counter");
