@@ -1005,6 +1005,16 @@ def run_batch(a):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     total = sum(w.paths for w in ws)
+    # kernels per batch run: functionals, [power norms,] weights per grid; then each grid's
+    # [path order and] engine (per-grid variant) or each grid's path order, the megakernel
+    # and, when the smaller grids run as tasks (variants 0 and 2), the task kernel
+    pn = sum(1 for s in solvers if msk.msk_power_norms(s.ctx, order, K, stream=stream).shape[0] > 0)
+    if variant == 4:
+        batch_launches = 2 * len(ws) + pn + sum(1 + queued(w.paths) for w in ws)
+    else:
+        small = any(w.d < 256 for w in ws)
+        batch_launches = 3 * len(ws) + pn + (1 if (any(w.d == 256 for w in ws) or variant & 1) else 0) + \
+            (1 if small and not variant & 1 else 0)
     # per-grid launches one after another, for comparison
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for s, w, o in zip(solvers, ws, outs):
@@ -1038,10 +1048,7 @@ def run_batch(a):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": None, "kernel": "batch_kernel (whole step)"},
             "clocks": clk,
-            # per batch run: functionals and weights per grid, then the megakernel or, for the
-            # per-grid variant, each grid's [path order and] engine launch
-            "gpu_launches": a.steps * (2 * len(ws) + (sum(1 + queued(w.paths) for w in ws)
-                                                      if variant == 4 else 1)),
+            "gpu_launches": a.steps * batch_launches,
             "comparators": {"per_grid_launches_ms": seq_ms,
                             "per_grid_paths_per_s": total / (seq_ms / 1e3)}}
     msk.msk_batch_destroy(b)

@@ -3,25 +3,29 @@
 // a CUDA graph, with the work layout chosen by a small autotuner.
 //
 // The megakernel runs thread-block clusters of four 512-thread CTAs, one CTA
-// per SM.  Each cluster repeatedly takes the next work unit from a queue (one
-// atomic counter) and runs it with the engine's per-path solver
-// (engine_core.cuh):
-//   D256   one 256^2 path, split into four 64-row slabs (the cluster's CTAs)
-//   D128   up to four 128^2 paths, one per CTA
-//   D64x2  up to eight 64^2 paths, two per CTA (two 256-thread halves, each
-//          synchronised by its own named barrier)
-//   D64x1  up to four 64^2 paths, one per CTA (512 threads, two rows each)
-// Every unit keeps one SM busy per CTA for about the same number of grid
-// points (16384), so units differ in length only by their Taylor work, which
+// per SM, and each item's paths in decreasing order of estimated Taylor cost
+// (path_order.cu).  Work comes in two kinds, each from its own atomic counter,
+// and is run with the engine's per-path solver (engine_core.cuh):
+//   units, taken by a whole cluster:
+//     D256   one 256^2 path, split into four 64-row slabs (the cluster's CTAs)
+//     D128   up to four 128^2 paths, one per CTA
+//     D64x2  up to eight 64^2 paths, two per CTA (two 256-thread halves, each
+//            synchronised by its own named barrier)
+//     D64x1  up to four 64^2 paths, one per CTA (512 threads, two rows each)
+//   tasks, taken by one CTA once the units are gone: one 128^2 path, two 64^2
+//     paths (one per half) or one 64^2 path, so that no CTA waits for the
+//     slowest path of a unit
+// Every CTA holds about the same number of grid points (16384) whatever it
+// runs, so the work items differ in length only by their Taylor work, which
 // grows with the grid (the operator norm scales like 1/Delta^2).
 //
-// Tuned choices (the "variant"): for 0..3, bit 0 orders the queue by
-// decreasing unit length (largest grids first) or interleaves the items, and
-// bit 1 packs 64^2 paths two per CTA or one per CTA; variant 4 replaces the
-// megakernel by each item's own engine launch (its best per-grid
-// configuration) inside the same graph.  msk_batch_tune times all five on the
-// batch itself and keeps the fastest; the result can be cached in a text file
-// keyed by device name and batch shape.
+// Tuned choices (the "variant"): for 0..3, bit 0 puts every path in units with
+// the items interleaved, or (clear) the 256^2 paths in units and the smaller
+// grids' paths in tasks, largest grids first; bit 1 packs 64^2 paths two per CTA
+// or one per CTA; variant 4 replaces the megakernel by each item's own engine
+// launch (its best per-grid configuration) inside the same graph.
+// msk_batch_tune times all five on the batch itself and keeps the fastest; the
+// result can be cached in a text file keyed by device name and batch shape.
 #include <stdio.h>
 
 #include <new>
@@ -53,9 +57,44 @@ using K64h = Cfg<float, 64, 1, kNT / 2>;
 using K64 = Cfg<float, 64, 1, kNT>;
 constexpr size_t kHalf64 = (K64h::SMEM + 255) / 256 * 256;   // byte offset of the second half-slab
 constexpr size_t kSlabBytes = std::max(std::max(K256::SMEM, K128::SMEM), std::max(2 * kHalf64, K64::SMEM));
-constexpr size_t kBatchSmem = kSlabBytes + 16;                 // + the unit index slot
+constexpr size_t kBatchSmem = kSlabBytes + 16;                 // + the unit and task index slots
 static_assert(kBatchSmem <= 232448, "batch slab does not fit shared memory");
 
+// Position pos of an item's cost order -> path index (identity without an order).
+__device__ __forceinline__ int64_t path_at(const EngineArgs& a, int64_t pos) { return a.order ? a.order[pos] : pos; }
+
+// The paths of a unit of small grids that fall to CTA `sub` of the cluster, or
+// of a task (sub = 0): one 128^2 path, two 64^2 paths (one per 256-thread half)
+// or one 64^2 path.
+__device__ __forceinline__ void run_small(const BatchUnit& un, const EngineArgs& a, int sub, unsigned char* smem_raw,
+                                          int tid) {
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  switch (un.type) {
+    case UNIT_D128: {
+      const CtaSync s;
+      slab_init<float, 128, 1, kNT>(sm, tid, 0, s);
+      if (sub < un.count) solve_path<float, 128, 1, kNT, false>(a, path_at(a, un.first + sub), sm, tid, 0, s);
+      break;
+    }
+    case UNIT_D64X2: {
+      const int g = tid / (kNT / 2), t = tid % (kNT / 2);
+      const NamedSync s{1 + g, kNT / 2};
+      float* half = reinterpret_cast<float*>(smem_raw + g * kHalf64);
+      slab_init<float, 64, 1, kNT / 2>(half, t, 0, s);
+      const int idx = 2 * sub + g;
+      if (idx < un.count) solve_path<float, 64, 1, kNT / 2, false>(a, path_at(a, un.first + idx), half, t, 0, s);
+      break;
+    }
+    default: {
+      const CtaSync s;
+      slab_init<float, 64, 1, kNT>(sm, tid, 0, s);
+      if (sub < un.count) solve_path<float, 64, 1, kNT, false>(a, path_at(a, un.first + sub), sm, tid, 0, s);
+      break;
+    }
+  }
+}
+
+// The units, each taken by a whole cluster from counter[0].
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kNT, 1)
     batch_kernel(const EngineArgs* __restrict__ items, const BatchUnit* __restrict__ units, int n_units,
                  unsigned int* __restrict__ counter) {
@@ -65,6 +104,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kNT, 1)
   const int tid = threadIdx.x;
   const int rank = (int)cg::this_cluster().block_rank();
   const ClusterSync csync;
+  // every CTA of this grid is resident (one wave of clusters): the task kernel,
+  // launched as this kernel's programmatic dependent, may start on the SMs that
+  // no cluster of four can use
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   for (;;) {
     // The previous unit is finished by every CTA once all have reached this
     // barrier; rank 0 then publishes the next unit index in its shared memory.
@@ -77,33 +120,31 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kNT, 1)
     if (u >= n_units) break;                        // same value in every thread of the cluster
     const BatchUnit un = units[u];
     const EngineArgs a = items[un.item];
-    switch (un.type) {
-      case UNIT_D256:
-        slab_init<float, 256, 4, kNT>(sm, tid, rank, csync);
-        solve_path<float, 256, 4, kNT, false>(a, un.first, sm, tid, rank, csync);
-        break;
-      case UNIT_D128: {
-        const CtaSync s;
-        slab_init<float, 128, 1, kNT>(sm, tid, 0, s);
-        if (rank < un.count) solve_path<float, 128, 1, kNT, false>(a, un.first + rank, sm, tid, 0, s);
-        break;
-      }
-      case UNIT_D64X2: {
-        const int g = tid / (kNT / 2), t = tid % (kNT / 2);
-        const NamedSync s{1 + g, kNT / 2};
-        float* half = reinterpret_cast<float*>(smem_raw + g * kHalf64);
-        slab_init<float, 64, 1, kNT / 2>(half, t, 0, s);
-        const int idx = 2 * rank + g;
-        if (idx < un.count) solve_path<float, 64, 1, kNT / 2, false>(a, un.first + idx, half, t, 0, s);
-        break;
-      }
-      default: {
-        const CtaSync s;
-        slab_init<float, 64, 1, kNT>(sm, tid, 0, s);
-        if (rank < un.count) solve_path<float, 64, 1, kNT, false>(a, un.first + rank, sm, tid, 0, s);
-        break;
-      }
+    if (un.type == UNIT_D256) {
+      slab_init<float, 256, 4, kNT>(sm, tid, rank, csync);
+      solve_path<float, 256, 4, kNT, false>(a, path_at(a, un.first), sm, tid, rank, csync);
+    } else {
+      run_small(un, a, rank, smem_raw, tid);
     }
+  }
+}
+
+// The tasks, each taken by one CTA from counter[1] (no clusters: every SM, and
+// a register allocation of its own).  It reads nothing the megakernel writes.
+__global__ void __launch_bounds__(kNT, 1)
+    batch_task_kernel(const EngineArgs* __restrict__ items, const BatchUnit* __restrict__ tasks, int n_tasks,
+                      unsigned int* __restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int* s_task = reinterpret_cast<int*>(smem_raw + kSlabBytes);
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) *s_task = (int)atomicAdd(counter + 1, 1u);
+    __syncthreads();
+    const int q = *s_task;
+    __syncthreads();   // read by every thread before thread 0 takes the next one
+    if (q >= n_tasks) break;
+    const BatchUnit un = tasks[q];
+    run_small(un, items[un.item], 0, smem_raw, tid);
   }
 }
 
@@ -117,9 +158,9 @@ struct msk_batch {
   std::vector<size_t> p_off;                 // power-norm table of the (s, m) selection (floats)
   double* scratch = nullptr;
   EngineArgs* d_args = nullptr;
-  BatchUnit* d_units = nullptr;
-  unsigned int* d_counter = nullptr;
-  int n_units = 0, units_cap = 0;
+  BatchUnit* d_units = nullptr;   // units, then tasks (units_cap entries)
+  unsigned int* d_counter = nullptr;   // [0] unit queue, [1] task queue
+  int n_units = 0, n_tasks = 0, units_cap = 0;
   int variant = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -145,36 +186,45 @@ msk_status bcuda(msk_batch* b, cudaError_t e, const char* what) {
 constexpr int kPerGridVariant = 4;
 constexpr int kVariants = 5;
 
-std::vector<BatchUnit> build_units(const msk_batch* b, int variant) {
+// The work of a megakernel variant: units, each run by a whole cluster, and
+// tasks, each run by one CTA.  Positions count along each item's cost order.
+//   interleaved (bit 0): every path in units (one 256^2 path, four 128^2 paths,
+//     eight or four 64^2 paths), the items' units taken in turn; no tasks
+//   longest first: the 256^2 paths as units; the 128^2 paths, then the 64^2
+//     ones, as tasks of one path (or two 64^2 paths on the two halves of a CTA),
+//     so a CTA waits for no other CTA's path once the 256^2 units are gone
+void build_units(const msk_batch* b, int variant, std::vector<BatchUnit>* units, std::vector<BatchUnit>* tasks) {
   const bool interleave = variant & 1, one64 = variant & 2;
   std::vector<std::vector<BatchUnit>> per(b->items.size());
   for (size_t k = 0; k < b->items.size(); ++k) {
     const msk_batch_item& it = b->items[k];
     const int d = it.ctx->d;
     const int type = d == 256 ? UNIT_D256 : d == 128 ? UNIT_D128 : one64 ? UNIT_D64X1 : UNIT_D64X2;
-    const int per_unit = type == UNIT_D256 ? 1 : type == UNIT_D64X2 ? 8 : 4;
+    const int per_cta = type == UNIT_D64X2 ? 2 : 1;
+    const int per_unit = type == UNIT_D256 || !interleave ? per_cta : 4 * per_cta;
     for (int64_t p = 0; p < it.paths; p += per_unit)
       per[k].push_back({type, (int32_t)k, p, (int32_t)std::min<int64_t>(per_unit, it.paths - p), 0});
   }
-  std::vector<BatchUnit> out;
+  units->clear();
+  tasks->clear();
   if (interleave) {
     for (size_t r = 0;; ++r) {
       bool any = false;
       for (auto& v : per)
         if (r < v.size()) {
-          out.push_back(v[r]);
+          units->push_back(v[r]);
           any = true;
         }
       if (!any) break;
     }
   } else {
-    for (auto& v : per) out.insert(out.end(), v.begin(), v.end());
-    // longest units first: larger grids carry more Taylor work per grid point
-    std::stable_sort(out.begin(), out.end(), [&](const BatchUnit& x, const BatchUnit& y) {
+    for (auto& v : per)
+      for (const BatchUnit& u : v) (u.type == UNIT_D256 ? units : tasks)->push_back(u);
+    // larger grids first: they carry more Taylor work per grid point
+    std::stable_sort(tasks->begin(), tasks->end(), [&](const BatchUnit& x, const BatchUnit& y) {
       return b->items[x.item].ctx->d > b->items[y.item].ctx->d;
     });
   }
-  return out;
 }
 
 void drop_graph(msk_batch* b) {
@@ -185,30 +235,34 @@ void drop_graph(msk_batch* b) {
 }
 
 msk_status set_variant(msk_batch* b, int variant) {
-  const std::vector<BatchUnit> units = build_units(b, variant);
-  if ((int)units.size() > b->units_cap) {
+  std::vector<BatchUnit> units, tasks;
+  build_units(b, variant, &units, &tasks);
+  const size_t n = units.size() + tasks.size();
+  if ((int)n > b->units_cap) {
     if (b->d_units) cudaFree(b->d_units);
     b->d_units = nullptr;
-    msk_status st = bcuda(b, cudaMalloc(&b->d_units, std::max<size_t>(1, units.size()) * sizeof(BatchUnit)),
+    msk_status st = bcuda(b, cudaMalloc(&b->d_units, std::max<size_t>(1, n) * sizeof(BatchUnit)),
                           "unit list allocation");
     if (st != MSK_OK) return st;
-    b->units_cap = (int)units.size();
+    b->units_cap = (int)n;
   }
-  if (!units.empty()) {
-    msk_status st = bcuda(b, cudaMemcpy(b->d_units, units.data(), units.size() * sizeof(BatchUnit),
-                                        cudaMemcpyHostToDevice), "unit list upload");
+  units.insert(units.end(), tasks.begin(), tasks.end());
+  if (n > 0) {
+    msk_status st = bcuda(b, cudaMemcpy(b->d_units, units.data(), n * sizeof(BatchUnit), cudaMemcpyHostToDevice),
+                          "unit list upload");
     if (st != MSK_OK) return st;
   }
-  b->n_units = (int)units.size();
+  b->n_units = (int)(n - tasks.size());
+  b->n_tasks = (int)tasks.size();
   b->variant = variant;
   drop_graph(b);
   return MSK_OK;
 }
 
-// Enqueue the whole batch on `s`: counter reset, per-item Brownian functionals
-// and weights, then the persistent megakernel.
+// Enqueue the whole batch on `s`: counter reset, per-item Brownian functionals,
+// weights and path cost order, then the persistent megakernel.
 msk_status enqueue(msk_batch* b, cudaStream_t s) {
-  msk_status st = bcuda(b, cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), s), "counter reset");
+  msk_status st = bcuda(b, cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(unsigned int), s), "counter reset");
   for (size_t k = 0; k < b->items.size() && st == MSK_OK; ++k) {
     const msk_batch_item& it = b->items[k];
     if (it.paths == 0) continue;
@@ -220,9 +274,14 @@ msk_status enqueue(msk_batch* b, cudaStream_t s) {
     // microseconds): the graph then depends on no state of the contexts' caches
     if (st == MSK_OK) st = launch_power_norms(it.ctx, it.order, it.steps, P, s);
     if (st == MSK_OK) st = launch_omega_tab(it.ctx, it.order, it.steps, it.paths, MSK_F32, F, Wt, P, s);
+    // the megakernel takes each item's paths costliest first (the item table points at this order)
+    long long* order_buf = reinterpret_cast<long long*>(b->scratch + b->o_off[k]);
+    if (st == MSK_OK && b->variant != kPerGridVariant)
+      st = launch_path_order(it.ctx, Wt, it.steps, it.paths, order_buf,
+                             reinterpret_cast<unsigned long long*>(order_buf + it.paths), s);
     if (st != MSK_OK) b->err = it.ctx->err;
   }
-  if (st != MSK_OK || b->n_units == 0) return st;
+  if (st != MSK_OK || b->n_units + b->n_tasks == 0) return st;
   if (b->variant == kPerGridVariant) {   // each item's own engine launch, one after another
     for (size_t k = 0; k < b->items.size() && st == MSK_OK; ++k) {
       const msk_batch_item& it = b->items[k];
@@ -235,19 +294,42 @@ msk_status enqueue(msk_batch* b, cudaStream_t s) {
     }
     return st;
   }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(148 * 4, 1, 1);
-  cfg.blockDim = dim3(kNT, 1, 1);
-  cfg.dynamicSmemBytes = kBatchSmem;
-  cfg.stream = s;
-  int nc = 0;
-  st = bcuda(b, cudaOccupancyMaxActiveClusters(&nc, batch_kernel, &cfg), "occupancy clusters");
-  if (st != MSK_OK) return st;
-  if (nc < 1) return bfail(b, MSK_ERR_UNSUPPORTED, "batch cluster configuration cannot be scheduled");
-  cfg.gridDim = dim3((unsigned)(std::min(nc, b->n_units) * 4), 1, 1);
-  return bcuda(b, cudaLaunchKernelEx(&cfg, batch_kernel, (const EngineArgs*)b->d_args,
-                                     (const BatchUnit*)b->d_units, b->n_units, b->d_counter),
+  const BatchUnit* units = b->d_units;
+  if (b->n_units > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(148 * 4, 1, 1);
+    cfg.blockDim = dim3(kNT, 1, 1);
+    cfg.dynamicSmemBytes = kBatchSmem;
+    cfg.stream = s;
+    int nc = 0;
+    st = bcuda(b, cudaOccupancyMaxActiveClusters(&nc, batch_kernel, &cfg), "occupancy clusters");
+    if (st != MSK_OK) return st;
+    if (nc < 1) return bfail(b, MSK_ERR_UNSUPPORTED, "batch cluster configuration cannot be scheduled");
+    cfg.gridDim = dim3((unsigned)(std::min(nc, b->n_units) * 4), 1, 1);
+    st = bcuda(b, cudaLaunchKernelEx(&cfg, batch_kernel, (const EngineArgs*)b->d_args, units, b->n_units,
+                                     b->d_counter),
                "batch launch");
+    if (st != MSK_OK) return st;
+  }
+  if (b->n_tasks > 0) {
+    // a programmatic dependent of the megakernel: it may start once every
+    // megakernel CTA is resident, on the SMs the clusters leave free, and takes
+    // the rest as the megakernel's CTAs exit
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3((unsigned)std::min<int64_t>(b->items[0].ctx->num_sms, b->n_tasks), 1, 1);
+    cfg.blockDim = dim3(kNT, 1, 1);
+    cfg.dynamicSmemBytes = kBatchSmem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = b->n_units > 0 ? 1 : 0;
+    st = bcuda(b, cudaLaunchKernelEx(&cfg, batch_task_kernel, (const EngineArgs*)b->d_args, units + b->n_units,
+                                     b->n_tasks, b->d_counter),
+               "batch task launch");
+  }
+  return st;
 }
 
 msk_status capture(msk_batch* b, cudaStream_t s) {
@@ -328,7 +410,7 @@ extern "C" msk_status msk_batch_create(msk_batch** out, const msk_batch_item* it
     total += ((size_t)items[k].steps * MSK_POW_J + 1) / 2;
   }
   if (st == MSK_OK) st = bcuda(b, cudaMalloc(&b->scratch, std::max<size_t>(total, 1) * sizeof(double)), "scratch");
-  if (st == MSK_OK) st = bcuda(b, cudaMalloc(&b->d_counter, sizeof(unsigned int)), "counter");
+  if (st == MSK_OK) st = bcuda(b, cudaMalloc(&b->d_counter, 2 * sizeof(unsigned int)), "counters");
   if (st == MSK_OK) st = bcuda(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "capture stream");
   if (st == MSK_OK) st = bcuda(b, cudaMalloc(&b->d_args, n_items * sizeof(EngineArgs)), "item table");
   for (int k = 0; k < n_items && st == MSK_OK; ++k) {
@@ -350,6 +432,8 @@ extern "C" msk_status msk_batch_create(msk_batch** out, const msk_batch_item* it
     a.tol32 = 0x1p-20f;   // float Taylor tolerance (see gen_theta.py)
     a.tol64 = 0x1p-53;
     a.c = coef_dev(c->coef);
+    // the megakernel's path order (written on every run before the megakernel)
+    a.order = reinterpret_cast<const long long*>(b->scratch + b->o_off[k]);
     b->args.push_back(a);
     st = msk_prepare_brownian(c, 0);
     if (st == MSK_OK) st = msk_prepare_omega(c);
@@ -360,6 +444,10 @@ extern "C" msk_status msk_batch_create(msk_batch** out, const msk_batch_item* it
                "item table upload");
   if (st == MSK_OK)
     st = bcuda(b, cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem),
+               "smem attribute");
+  if (st == MSK_OK)
+    st = bcuda(b, cudaFuncSetAttribute(batch_task_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kBatchSmem),
                "smem attribute");
   if (st == MSK_OK) st = bcuda(b, cudaDeviceSynchronize(), "prepare");
   if (st == MSK_OK) {
