@@ -84,7 +84,7 @@ struct VarArgs {
   const long long* order;
   unsigned long long* queue;
   int64_t paths;
-  int steps, d, C, RS, ng, R;
+  int steps, d, C, RS, ns;   // ns: threads that hold grid points (see strip_of)
   int pitch;   // shared-memory row pitch of the fields and the partial sum (var_pitch)
   double dx, dv, av, kappa, T, s_cap;
   float tol32;
@@ -92,20 +92,54 @@ struct VarArgs {
   CoefDev c;
 };
 
-// Row pitch W >= d + pad of the shared fields and partial sum.  Threads take
-// (row group, column) pairs in group-major order, so a warp can span the end of
-// group g and the start of group g + 1, whose rows lie R rows apart; with
-// R W = d (mod 32) the two parts of such a warp fall on distinct banks (every
-// lane's word is its thread index modulo 32 away from a common base).
-__host__ __device__ inline int var_pitch(int d, int R, int ng, int pad) {
-  if (ng > 1)
-    for (int W = d + pad; W < d + pad + 32; ++W)
-      if ((R * W - d) % 32 == 0) return W;
-  return d + pad;
+// Thread -> (strip, column): the first ns threads take the CTA's points in
+// strip-major order, column c being cut into ns / d + (c < ns % d) strips of
+// near-equal length (rows [p0, p0 + nrows) of the rs rows held).  With ns a
+// multiple of 32 every warp carries points, so the four schedulers of an SM get
+// equal numbers of working warps (whose loads differ by at most one strip).
+__host__ __device__ inline void strip_of(int t, int d, int ns, int rs, int& col, int& p0, int& nrows) {
+  if (t >= ns) {
+    col = 0;
+    p0 = 0;
+    nrows = 0;
+    return;
+  }
+  col = t % d;
+  const int g = t / d, n = ns / d + (col < ns % d ? 1 : 0);
+  p0 = g * rs / n;
+  nrows = (g + 1) * rs / n - p0;
+}
+
+// Row pitch W >= d + pad of the shared fields and partial sum: each loop step of
+// a strip touches word (p0 + r) W + col of every lane, so lanes whose strips
+// start on different rows (a warp spanning two strips of a column, or columns
+// cut into different strip counts) may share banks.  Of d + pad .. d + pad + 31
+// the pitch with the fewest shared-memory wavefronts over all warps wins (the
+// smallest on ties).
+inline int var_pitch(int d, int RS, int ns, int pad) {
+  int best_w = d + pad, best = 1 << 30;
+  for (int W = d + pad; W < d + pad + 32; ++W) {
+    int cost = 0;
+    for (int w0 = 0; w0 < ns; w0 += 32) {
+      int cnt[32] = {0}, worst = 0;
+      for (int t = w0; t < w0 + 32 && t < ns; ++t) {
+        int c, p0, nr;
+        strip_of(t, d, ns, RS, c, p0, nr);
+        const int b = (p0 * W + c) % 32;
+        worst = std::max(worst, ++cnt[b]);
+      }
+      cost += worst;
+    }
+    if (cost < best) {
+      best = cost;
+      best_w = W;
+    }
+  }
+  return best_w;
 }
 
 // Shared memory of one CTA in elements of T: three fields of (RS + 4) x W
-// (W = var_pitch(d, R, ng, 4)), the partial sum [RS][W], the per-row Bx
+// (W = var_pitch(d, RS, ns, 4)), the partial sum [RS][W], the per-row Bx
 // coefficient of the rows -2 .. RS+1, 1/(s k), and the norm slots.  (All
 // offsets fit 32 bits: the layout is capped at 227 KB.)
 struct VarLayout {
@@ -270,13 +304,11 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
 
   const int r0 = rank * RS;          // first global v-row of this CTA
   const int rs = min(RS, d - r0);    // rows held by this CTA
-  // thread -> (row group, column): the CTA's points as the group-major sequence
-  // of (group, column) pairs, one per thread, so no lane idles when d is not a
-  // multiple of 32 (a warp may span two groups; nothing is exchanged by lanes)
-  const bool act = tid < a.ng * d;
-  const int col = act ? tid % d : 0, grp = act ? tid / d : 0;
-  const int p0 = grp * a.R;
-  const int nrows = act ? max(0, min(a.R, rs - p0)) : 0;
+  // thread -> strip of rows [p0, p0 + nrows) of column col (strip_of; nothing is
+  // exchanged by lanes, so a warp may span two strips)
+  const bool act = tid < a.ns;
+  int col, p0, nrows;
+  strip_of(tid, d, a.ns, rs, col, p0, nrows);
 
   // zero the fields once: grid-boundary halos and pad columns are never written again
   for (int e = tid; e < NF * FS; e += NT) sm[e] = T(0);
@@ -686,10 +718,9 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
 
   const int r0 = rank * RS;
   const int rs = min(RS, d - r0);
-  const bool act = tid < a.ng * d;   // group-major (row group, column) per thread
-  const int col = act ? tid % d : 0, grp = act ? tid / d : 0;
-  const int p0 = grp * a.R;
-  const int nrows = act ? max(0, min(a.R, rs - p0)) : 0;
+  const bool act = tid < a.ns;   // strip of rows [p0, p0 + nrows) of column col (strip_of)
+  int col, p0, nrows;
+  strip_of(tid, d, a.ns, rs, col, p0, nrows);
 
   for (int e = tid; e < kGenFields * FS; e += NT) sm[e] = T(0);
   sync_all();
@@ -1119,7 +1150,7 @@ __global__ void psi_rational_kernel(int d, double ax, double dx, double c, doubl
 
 // ------------------------------------------------------------------ launch planning
 struct VarPlan {
-  int C = 0, RS = 0, ng = 0, R = 0, NT = 0, pitch = 0, clusters = 0;
+  int C = 0, RS = 0, ns = 0, NT = 0, pitch = 0, clusters = 0;
   size_t smem = 0;
 };
 
@@ -1161,17 +1192,16 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
   for (int C = 1; C <= 16; ++C) {
     const int RS = (d + C - 1) / C;
     if ((C - 1) * RS >= d || RS < 2) continue;
-    // row groups: as many as 512 threads hold, at least two rows per strip
-    const int ng = std::max(1, std::min(kVarMaxThreads / d, RS / 2));
-    const int R = (RS + ng - 1) / ng;
-    const int NT = 32 * ((ng * d + 31) / 32);
+    // strips: as many as 512 threads hold, at least two rows each
+    const int ns = std::min(kVarMaxThreads, d * std::max(1, RS / 2));
+    const int NT = 32 * ((ns + 31) / 32);
     // the bank-aligned pitch where it fits, else the plain one (same cluster size)
     const int pad = MODE == kModeGen ? 2 : 4;
     auto total_of = [&](int W) {
       return MODE == kModeGen ? gen_layout(RS, W, NT).total
                               : var_layout(RS, W, NT, MODE == kModeSplit ? kVarFields + 1 : kVarFields).total;
     };
-    int W = var_pitch(d, R, ng, pad);
+    int W = var_pitch(d, RS, ns, pad);
     if ((size_t)total_of(W) * sizeof(T) > kVarSmemCap) W = d + pad;
     const size_t smem = (size_t)total_of(W) * sizeof(T);
     if (smem > kVarSmemCap) continue;
@@ -1204,8 +1234,7 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
     VarPlan p;
     p.C = C;
     p.RS = RS;
-    p.ng = ng;
-    p.R = R;
+    p.ns = ns;
     p.NT = NT;
     p.pitch = W;
     p.clusters = clusters;
@@ -1233,8 +1262,7 @@ msk_status launch_var_typed(msk_ctx* ctx, VarArgs a, int64_t paths, cudaStream_t
   if (st != MSK_OK) return st;
   a.C = pl.C;
   a.RS = pl.RS;
-  a.ng = pl.ng;
-  a.R = pl.R;
+  a.ns = pl.ns;
   a.pitch = pl.pitch;
   const int64_t clusters = std::min<int64_t>(pl.clusters, paths);
   cudaLaunchConfig_t cfg = {};
