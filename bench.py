@@ -67,6 +67,8 @@ def parse():
                         "large512: the 512^2 constant-coefficient grids, sigma = 0.25 / 0.5 / 1, 1024 paths, m2")
     p.add_argument("--no-surrogate", action="store_true", help="skip the surrogate summary of the default line")
     p.add_argument("--no-fp64", action="store_true", help="skip the timed double-precision sub-line")
+    p.add_argument("--no-other-workloads", action="store_true",
+                   help="skip the compact timings of the batch, 512^2 and variable-coefficient configurations")
     p.add_argument("--clock-csv-dir", default=None,
                    help="directory for the clock samples taken during the timed region (default: a temporary one)")
     p.add_argument("--surrogate-profile-case", type=int, default=0, metavar="PATHS",
@@ -880,6 +882,11 @@ def run_ours(a):
         except Exception as exc:   # the Magnus line stands on its own
             comparators["surrogate"] = {"error": f"{type(exc).__name__}: {exc}"}
 
+    # ---- the other configurations, compactly (after every timed region of the headline) -----
+    others = None
+    if not a.no_other_workloads and world == 1:
+        others = other_workloads(msk, torch, local, stream)
+
     # ---- roofline of the engine kernel ------------------------------------------------------
     roof = engine_roofline(msk, local, stream, matvecs / a.steps * w.d * w.d, engine_ms,
                            "engine_kernel<float,128,1,512>")
@@ -913,6 +920,7 @@ def run_ours(a):
         "path_status_max": status_bits,
         "fp64": fp64,
         "comparators": comparators,
+        "other_workloads": others,
     }
     solver.close()
     if rank == 0:
@@ -920,6 +928,67 @@ def run_ours(a):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ the other configurations, compactly
+
+def other_workloads(msk, torch, local, stream):
+    """The other configurations timed once each after the headline, with the L2 flushed
+    before every timed call (event-timed on the launching stream): the uneven batch
+    (autotuned layout, three runs), the 512^2 grid at sigma = 0.5 (float order 2, K = 64,
+    1024 paths) and the paper's variable-coefficient grids (float order 3 at the paper's
+    steps).  The full protocols -- error gates, double precision, Euler references -- are
+    --workload batch / large512 / paper_var."""
+    from workloads import BATCH_GRIDS, LARGE_512, PAPER_VAR
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+
+    def ev_ms(fn, reps=1):
+        flush.fill_(1)
+        e0, e1 = _events(torch, stream)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # uneven batch: 9362 x 64^2, 4681 x 128^2, 2341 x 256^2, order 3, K = 16
+    solvers = [msk.Solver(w, device=local) for w in BATCH_GRIDS]
+    outs = [s.state(w.paths, msk.MSK_F32) for s, w in zip(solvers, BATCH_GRIDS)]
+    sts = [torch.zeros(w.paths, dtype=torch.int32, device="cuda") for w in BATCH_GRIDS]
+    b = msk.msk_batch_create([(s.ctx, 3, 16, w.paths, o, st)
+                              for s, w, o, st in zip(solvers, BATCH_GRIDS, outs, sts)])
+    variant, tune_ms = msk.msk_batch_tune(b, stream=stream)
+    ms = ev_ms(lambda: msk.msk_batch_run(b, stream), reps=3)
+    total = sum(w.paths for w in BATCH_GRIDS)
+    out["batch_64_128_256"] = {"paths": total, "order": 3, "magnus_steps": 16, "ms": ms,
+                               "paths_per_s": total / (ms / 1e3), "variant": variant, "tune_ms": tune_ms,
+                               "flagged_paths": int(sum(int((st != 0).sum()) for st in sts))}
+    msk.msk_batch_destroy(b)
+    for s in solvers:
+        s.close()
+    # 512^2, sigma = 0.5: float order 2 with K = 64 (the step the error gate picks there)
+    w = LARGE_512[1]
+    s = msk.Solver(w, device=local)
+    u = s.state(w.paths, msk.MSK_F32)
+    msk.msk_solve_magnus(s.ctx, 2, 64, 16, msk.MSK_F32, u, None, stream)   # warm-up (16 paths)
+    ms = ev_ms(lambda: msk.msk_solve_magnus(s.ctx, 2, 64, w.paths, msk.MSK_F32, u, None, stream))
+    out["large512_sigma0.5"] = {"paths": w.paths, "order": 2, "magnus_steps": 64, "ms": ms,
+                                "paths_per_s": w.paths / (ms / 1e3), "engine": "automatic (streamed)"}
+    s.close()
+    # the paper's variable-coefficient grids (Section 3.2), float order 3 at the paper's steps
+    for w0 in PAPER_VAR:
+        d = w0.d
+        P, K = VAR_PATHS[d], VAR_STEPS[d]
+        s = msk.Solver(w0.with_(paths=P), device=local)
+        u = s.state(P, msk.MSK_F32)
+        msk.msk_solve_magnus(s.ctx, ORDER, K, 16, msk.MSK_F32, u, None, stream)   # warm-up (16 paths)
+        ms = ev_ms(lambda: msk.msk_solve_magnus(s.ctx, ORDER, K, P, msk.MSK_F32, u, None, stream))
+        out[f"paper_var_d{d}"] = {"paths": P, "order": ORDER, "magnus_steps": K, "ms": ms,
+                                  "paths_per_s": P / (ms / 1e3)}
+        s.close()
+    return out
 
 
 # ------------------------------------------------------------------ reference arm (CPU oracle)
