@@ -386,17 +386,23 @@ typedef struct {
 
 typedef struct msk_batch msk_batch;
 
-/* Build a batch: library-owned scratch for every item, the work-unit queue of
- * the persistent kernel (one 256^2 path per 4-CTA cluster, four 128^2 paths,
- * or four/eight 64^2 paths per cluster), and the variant cached under
- * `tune_cache` for this device and batch shape (NULL or "": default variant). */
+/* Build a batch: library-owned scratch for every item, the work lists of the
+ * persistent kernels (units of a 4-CTA cluster: one 256^2 path, four 128^2
+ * paths, or four/eight 64^2 paths; tasks of one CTA: one 128^2 path, or one or
+ * two 64^2 paths), and the variant cached under `tune_cache` for this device
+ * and batch shape (NULL or "": default variant 0). */
 msk_status msk_batch_create(msk_batch** out, const msk_batch_item* items, int n_items,
                             const char* tune_cache);
 
-/* Run the batch on `stream`: per-item Brownian functionals and weights, then one
- * persistent launch of the megakernel over all items' paths.  The first run
- * captures these launches into a CUDA graph (on a private stream of the batch);
- * every run launches that graph on `stream`. */
+/* Run the batch on `stream`: per-item Brownian functionals, weights and path
+ * cost order, then the persistent kernels over all items' paths (variants 0 and
+ * 2: the cluster megakernel over the 256^2 paths and, as its programmatic
+ * dependent, the task kernel over the smaller grids' paths; 1 and 3: the
+ * megakernel over every path; 4: each item's own engine launch).  The first
+ * run captures these launches into a CUDA graph (on a private stream of the
+ * batch); every run launches that graph on `stream`.  One batch holds one set
+ * of queue counters and scratch: runs of the same batch must not overlap
+ * (successive runs on one stream are fine). */
 msk_status msk_batch_run(msk_batch* b, void* stream);
 
 /* Autotune: time every variant (queue order x 64^2 packing of the megakernel,
@@ -406,9 +412,11 @@ msk_status msk_batch_run(msk_batch* b, void* stream);
 msk_status msk_batch_tune(msk_batch* b, void* stream, const char* tune_cache, int* variant_out,
                           float* ms_out);
 
-/* Current variant of the batch (0..3 megakernel: bit 0 interleaved queue, bit 1
- * one 64^2 path per CTA; 4: each item's own engine launch), and setting it
- * explicitly (0..4; the next run re-captures the graph). */
+/* Current variant of the batch (0..3 persistent kernels: bit 0 every path in
+ * cluster units with the items interleaved, else 256^2 units plus one-CTA
+ * tasks largest grid first; bit 1 one 64^2 path per CTA instead of two; 4: each
+ * item's own engine launch), and setting it explicitly (0..4; the next run
+ * re-captures the graph). */
 int msk_batch_variant(const msk_batch* b);
 msk_status msk_batch_set_variant(msk_batch* b, int variant);
 
