@@ -219,13 +219,6 @@ __device__ __forceinline__ double wmax(double x) {
 }
 template <typename T> __device__ __forceinline__ T vabsnan(T x) { return (x == x) ? fabs(x) : T(INFINITY); }
 
-__device__ __forceinline__ double var_sigma_t(const CoefDev& c, double t) {
-  return c.s0 * (1.0 + c.s1 * cospi(2.0 * t));
-}
-__device__ __forceinline__ double var_alpha_t(const CoefDev& c, double t) {
-  return 0.5 * (c.a0 + c.a1 * sinpi(2.0 * t));
-}
-
 // Norm reduction shared by the engines of this file: every warp publishes its
 // maxima in shared memory; with clusters warp 0 of each CTA folds them into one
 // pair and pushes it into slot `rank` of every CTA of the cluster (shared::cluster
@@ -666,6 +659,287 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine_kernel(const Var
   }
 }
 
+// ------------------------------------------------------------------ one cluster barrier per term
+// Magnus with constant a and sigma on clusters (C > 1).  Pass A also evaluates
+// p and q on the row just beyond each slab edge that faces another CTA, from
+// term halos three rows deep, so pass B reads no p, q of the neighbours and
+// follows pass A after a CTA barrier only; the cluster barrier that publishes
+// the term's norms is the only one per term.  The term field is double-
+// buffered: pass B writes the next term into the other buffer (its own rows,
+// and its edge rows into the facing halos of that buffer in the neighbours),
+// which no CTA reads before that barrier; the buffer being read is written
+// again only after it.  The arithmetic per point is that of var_engine_kernel.
+// Layout per CTA (elements of T): two term fields of (RS + 6) x W (three halo
+// rows each side), p and q of (RS + 2) x W (one halo row), the partial sum
+// [RS][W], the per-row Bx coefficient of the rows -2 .. RS + 1, 1/(s k), the
+// norm slots and the cluster's next path.
+struct Var1Layout {
+  int TS, PS, off_p, off_q, off_acc, off_cx, off_scale, off_slot, off_cslot, off_path, total;
+};
+__host__ __device__ inline Var1Layout var1_layout(int RS, int W, int NT) {
+  Var1Layout L;
+  L.TS = (RS + 6) * W;
+  L.PS = (RS + 2) * W;
+  L.off_p = 2 * L.TS;
+  L.off_q = L.off_p + L.PS;
+  L.off_acc = L.off_q + L.PS;
+  L.off_cx = L.off_acc + RS * W;
+  L.off_scale = L.off_cx + RS + 4;
+  L.off_slot = L.off_scale + kVarMaxTerms + 1;
+  L.off_cslot = (L.off_slot + 4 * (NT / 32) + 3) / 4 * 4;   // [2][16][2], 16-byte aligned
+  L.off_path = L.off_cslot + 4 * kVarMaxCluster;            // the cluster's next path (8 bytes)
+  L.total = L.off_path + 2;
+  return L;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVarMaxThreads, 1) var_engine1_kernel(const VarArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x, NT = blockDim.x, NW = NT >> 5;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int C = a.C, RS = a.RS, d = a.d, W = a.pitch;
+  const int rank = (int)cg::this_cluster().block_rank();
+  const Var1Layout L = var1_layout(RS, W, NT);
+  T* Pf = sm + L.off_p;
+  T* Qf = sm + L.off_q;
+  T* accs = sm + L.off_acc;
+  T* cxr = sm + L.off_cx + 2;   // cxr[p], p in [-2, RS + 1]
+  T* scale_tab = sm + L.off_scale;
+  T* slots = sm + L.off_slot;
+  T* cslot = sm + L.off_cslot;
+  auto sync_all = [&]() { cg::this_cluster().sync(); };
+
+  const int r0 = rank * RS;          // first global v-row of this CTA
+  const int rs = min(RS, d - r0);    // rows held by this CTA
+  const bool act = tid < a.ns;
+  int col, p0, nrows;
+  strip_of(tid, d, a.ns, rs, col, p0, nrows);
+  // pass A's rows: the strip, and row -1 (first strip of the column) or row rs
+  // (last strip) where that edge faces another CTA
+  const int pa0 = (act && tid / d == 0 && rank > 0) ? -1 : p0;
+  const int pa1 = (act && p0 + nrows == rs && rank < C - 1) ? rs + 1 : p0 + nrows;
+
+  for (int e = tid; e < L.off_acc; e += NT) sm[e] = T(0);   // halos beyond the grid stay zero
+  for (int p = tid - 2; p < RS + 2; p += NT) {
+    const int jg = r0 + p;
+    const double v = a.av + (double)(jg + 1) * a.dv;
+    cxr[p] = (jg >= 0 && jg < d) ? (T)(a.kappa * v * (0.5 / a.dx)) : T(0);   // Bx: kappa v_j / (2 dx)
+  }
+  auto colc = [&](int c, T& cvb, T& cav) {
+    if (c >= 0 && c < d) {
+      const double ps = a.psi[c];
+      cvb = (T)(0.5 * a.c.a0 * ps / (a.dv * a.dv));   // alpha Bvv
+      cav = (T)(sqrt(ps) * (0.5 / a.dv));             // A0
+    } else {
+      cvb = cav = T(0);
+    }
+  };
+  T cvB, ca, cvBL, caL, cvBR, caR;
+  colc(act ? col : -1, cvB, ca);
+  colc(act ? col - 1 : -1, cvBL, caL);
+  colc(act ? col + 1 : -1, cvBR, caR);
+  const T mL = (act && col > 0) ? T(1) : T(0), mR = (act && col < d - 1) ? T(1) : T(0);
+  sync_all();   // every CTA zeroed before any halo store reaches it
+
+  const uint32_t peer_lo = rank > 0 ? cl_addr(sm, rank - 1) : 0u;
+  const uint32_t peer_hi = rank < C - 1 ? cl_addr(sm, rank + 1) : 0u;
+  // offsets of (local row p, own column): in term buffer b, and within p or q
+  auto atT = [&](int b, int p) -> int { return b * L.TS + (p + 3) * W + col + 2; };
+  auto atP = [&](int p) -> int { return (p + 1) * W + col + 2; };
+  // an own point of term buffer b, and its copy in the facing halo (three rows
+  // deep) of the neighbouring CTA
+  auto storeT = [&](int b, int p, T v) {
+    sm[atT(b, p)] = v;
+    if (p < 3 && rank > 0) cl_st(peer_lo + (uint32_t)(atT(b, RS + p) * (int)sizeof(T)), v);
+    if (p >= rs - 3 && rank < C - 1) cl_st(peer_hi + (uint32_t)(atT(b, p - rs) * (int)sizeof(T)), v);
+  };
+  const NormSlots<T> norms{slots, cslot, NW, C, lane, warp, rank};
+  auto rowm = [&](int p) -> T { return (r0 + p >= 0 && r0 + p < d) ? T(1) : T(0); };
+  const T tol = sizeof(T) == 4 ? (T)a.tol32 : (T)a.tol64;
+
+  // ---- pass A over rows [ra, rb): p, q from term buffer b (a = A0 t, b = B t at
+  // the own point and its four neighbours, zero off the grid), stored locally
+  auto passA = [&](int b, int ra, int rb, T wB, T wA, T wAA, T wBA, T wBAA, T wBAB) {
+    if (ra >= rb) return;
+    const T* t = sm + b * L.TS;
+    int o = atT(0, ra), op = atP(ra);
+    T c0 = t[o - W], c1_ = t[o], c2 = t[o + W];
+    T l0 = t[o - W - 1], l1 = t[o - 1], l2 = t[o + W - 1];
+    T q0 = t[o - W + 1], q1 = t[o + 1], q2 = t[o + W + 1];
+    T am, a0, bm, b0;
+    {
+      const T cm2 = t[o - 2 * W];
+      const T mrow = rowm(ra - 1);
+      am = mrow * ca * (c1_ - cm2);
+      bm = mrow * fma(cxr[ra - 1], q0 - l0, cvB * fma(T(-2), c0, c1_ + cm2));
+      a0 = ca * (c2 - c0);
+      b0 = fma(cxr[ra], q1 - l1, cvB * fma(T(-2), c1_, c2 + c0));
+    }
+    for (int p = ra; p < rb; ++p, o += W, op += W) {
+      const T c3 = t[o + 2 * W];
+      const T xl = t[o - 2], xr = t[o + 2];
+      const T cx = cxr[p];
+      const T mdn = rowm(p + 1);
+      const T ap = mdn * ca * (c3 - c1_);
+      const T bp = mdn * fma(cxr[p + 1], q2 - l2, cvB * fma(T(-2), c2, c3 + c1_));
+      const T aL = mL * caL * (l2 - l0), aR = mR * caR * (q2 - q0);
+      const T bL = mL * fma(cx, c1_ - xl, cvBL * fma(T(-2), l1, l2 + l0));
+      const T bR = mR * fma(cx, xr - c1_, cvBR * fma(T(-2), q1, q2 + q0));
+      const T aa = ca * (ap - am), ab = ca * (bp - bm);
+      const T ba = fma(cx, aR - aL, cvB * fma(T(-2), a0, ap + am));
+      const T bb = fma(cx, bR - bL, cvB * fma(T(-2), b0, bp + bm));
+      Pf[op] = fma(wB, c1_, fma(wBA, a0, fma(wBAA, aa, wBAB * fma(T(2), ab, -ba))));
+      Qf[op] = fma(wA, c1_, fma(wAA, a0, fma(-wBA, b0, fma(wBAA, fma(T(-2), ba, ab), -wBAB * bb))));
+      am = a0; a0 = ap; bm = b0; b0 = bp;
+      c0 = c1_; c1_ = c2; c2 = c3;
+      l0 = l1; l1 = l2; l2 = t[o + 2 * W - 1];
+      q0 = q1; q1 = q2; q2 = t[o + 2 * W + 1];
+    }
+  };
+  // ---- pass B over the strip: next term (B p + A0 q - mu t) / (s k) from buffer b
+  // into buffer b ^ 1, added to the partial sum; mn, ma: running maxima of both
+  auto passB = [&](int b, T sc, T scmu, T& mn, T& ma) {
+    if (nrows <= 0) return;
+    const T* t = sm + b * L.TS;
+    int o = atT(0, p0), op = atP(p0);
+    T pu = Pf[op - W], pc = Pf[op], qu = Qf[op - W], qc = Qf[op];
+    for (int p = p0; p < p0 + nrows; ++p, o += W, op += W) {
+      const T pd = Pf[op + W], qd = Qf[op + W], pl = Pf[op - 1], pr = Pf[op + 1];
+      const T Bp = fma(cxr[p], pr - pl, cvB * fma(T(-2), pc, pd + pu));
+      const T tn_ = fma(sc, fma(ca, qd - qu, Bp), -scmu * t[o]);
+      storeT(b ^ 1, p, tn_);
+      T& ac = accs[p * W + col];
+      const T s_ = ac + tn_;
+      ac = s_;
+      mn = vmax(mn, fabs(tn_));
+      ma = vmax(ma, fabs(s_));
+      pu = pc;
+      pc = pd;
+      qu = qc;
+      qc = qd;
+    }
+  };
+
+  const int64_t cid = blockIdx.x / C, ncl = gridDim.x / C;
+  int par = 0;
+  long long* qslot = reinterpret_cast<long long*>(sm + L.off_path);
+  // (the double engine, used for checks, keeps the static assignment)
+  unsigned long long* queue = sizeof(T) == 8 ? nullptr : a.queue;
+  for (int64_t it = cid;; it += ncl) {
+    const int64_t path = var_next_path(a.order, queue, a.paths, qslot, tid, rank, C, it, sync_all);
+    if (path < 0) break;
+    int cur = 0;   // the term buffer holding the current term
+    T m0 = T(0);
+    const T* self0 = a.u0_self ? reinterpret_cast<const T*>(a.out) + (size_t)path * d * d : nullptr;
+    for (int r = 0; r < nrows; ++r) {
+      const int p = p0 + r;
+      const size_t g = (size_t)(r0 + p) * d + col;
+      const T v = self0 ? self0[g] : (T)a.u0[g];
+      accs[p * W + col] = v;
+      storeT(cur, p, v);
+      m0 = vmax(m0, vabsnan(v));
+    }
+    norms.publish(par, m0, m0);
+    sync_all();
+    T unorm, u0max;
+    norms.gather(par, unorm, u0max);
+    par ^= 1;
+    bool scale_cap = false;
+    unsigned long long nmv = 0;
+
+    auto snapshot = [&](int n) {
+      if (!a.snap) return;
+      const int q0 = a.snap_first[n], nq = a.snap_cnt[n];
+      for (int q = q0; q < q0 + nq; ++q) {
+        T* dst = reinterpret_cast<T*>(a.snap) + ((size_t)path * a.n_out + q) * d * d;
+        for (int r = 0; r < nrows; ++r) dst[(size_t)(r0 + p0 + r) * d + col] = accs[(p0 + r) * W + col];
+      }
+    };
+    for (int n = 0; n < a.steps; ++n) {
+      snapshot(n);
+      // the record in the working precision: lane q of every warp converts entry q
+      // (weights 0..12, then mu, s, m) once, shuffles broadcast it
+      const double* rec = a.Wt + ((size_t)path * a.steps + n) * MSK_NWT;
+      T rl = T(0);
+      if (lane < MSK_NOPS) rl = (T)rec[lane];
+      else if (lane == MSK_NOPS) rl = (T)rec[MSK_WT_MU];
+      else if (lane == MSK_NOPS + 1) rl = (T)rec[MSK_WT_S];
+      else if (lane == MSK_NOPS + 2) rl = (T)rec[MSK_WT_M];
+      const T wB = __shfl_sync(0xffffffffu, rl, MSK_OP_BX), wA = __shfl_sync(0xffffffffu, rl, MSK_OP_A0);
+      const T wAA = __shfl_sync(0xffffffffu, rl, MSK_OP_A0A0), wBA = __shfl_sync(0xffffffffu, rl, MSK_OP_BX_A0);
+      const T wBAA = __shfl_sync(0xffffffffu, rl, MSK_OP_BXA0_A0);
+      const T wBAB = __shfl_sync(0xffffffffu, rl, MSK_OP_BXA0_BX);
+      const T muT = __shfl_sync(0xffffffffu, rl, MSK_NOPS);
+      const T sT = __shfl_sync(0xffffffffu, rl, MSK_NOPS + 1), mT = __shfl_sync(0xffffffffu, rl, MSK_NOPS + 2);
+      const int s_steps = max(1, (int)sT);               // exact: s <= 2^14, m <= 128
+      const int m_terms = min((int)mT, kVarMaxTerms);
+      if (sT >= (T)a.s_cap) scale_cap = true;
+      T te;
+      if constexpr (sizeof(T) == 4) te = (T)expf((float)muT / (float)s_steps);
+      else te = (T)exp(rec[MSK_WT_MU] / s_steps);
+      for (int k = tid; k <= kVarMaxTerms; k += NT)
+        scale_tab[k] = k == 0 ? T(1) : T(1) / ((T)s_steps * (T)k);
+      __syncthreads();
+
+      for (int sub = 0; sub < s_steps; ++sub) {
+        T c1 = unorm;   // norm of the previous Taylor term (term 0 = the state)
+        for (int k = 1; k <= m_terms; ++k) {
+          const T sc = scale_tab[k];
+          const T scmu = sc * muT;
+          passA(cur, pa0, pa1, wB, wA, wAA, wBA, wBAA, wBAB);
+          __syncthreads();   // p, q of this CTA's rows and the two rows beyond them
+          T mn = T(0), ma = T(0);
+          passB(cur, sc, scmu, mn, ma);
+          norms.publish(par, mn, ma);
+          sync_all();        // the next term and its halos are complete in every CTA
+          T gn, ga;
+          norms.gather(par, gn, ga);
+          par ^= 1;
+          ++nmv;
+          cur ^= 1;
+          unorm = ga;
+          if (c1 + gn <= tol * ga) break;
+          c1 = gn;
+        }
+        // u <- e^{mu/s} (partial sum), the next sub-step's t, into the buffer not
+        // holding the last term (nobody reads it after the barrier above)
+        for (int r = 0; r < nrows; ++r) {
+          T& ac = accs[(p0 + r) * W + col];
+          const T v = ac * te;
+          ac = v;
+          storeT(cur ^ 1, p0 + r, v);
+        }
+        unorm = unorm * te;
+        sync_all();
+        cur ^= 1;
+      }
+    }
+
+    snapshot(a.steps);
+    T mfin = T(0);
+    for (int r = 0; r < nrows; ++r) {
+      const T v = accs[(p0 + r) * W + col];
+      if (a.out) reinterpret_cast<T*>(a.out)[(size_t)path * d * d + (size_t)(r0 + p0 + r) * d + col] = v;
+      mfin = vmax(mfin, vabsnan(v));
+    }
+    if (a.work && rank == 0 && tid == 0) atomicAdd(a.work, nmv);
+    norms.publish(par, mfin, mfin);
+    sync_all();
+    T gfin, gfin2;
+    norms.gather(par, gfin, gfin2);
+    par ^= 1;
+    if (a.status && rank == 0 && tid == 0) {
+      uint32_t st = 0;
+      if (!(gfin < T(INFINITY))) st |= MSK_PATH_NONFINITE;
+      if (scale_cap) st |= MSK_PATH_SCALE_CAP;
+      if (!((double)gfin <= 10.0 * (double)u0max)) st |= MSK_PATH_BLOWUP;
+      a.status[path] = st;
+    }
+    sync_all();   // nobody may still read this path's fields or slots
+  }
+}
+
 // ------------------------------------------------------------------ general coefficients
 // Eq. generalSPDE with time-independent coefficient functions of (x, v): B is the
 // nine-point stencil of h, f^x, f^v, g^xx, g^xv, g^vv and A the five-point stencil
@@ -718,8 +992,7 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine_kernel(const Var
 
   const int r0 = rank * RS;
   const int rs = min(RS, d - r0);
-  const bool act = tid < a.ns;   // strip of rows [p0, p0 + nrows) of column col (strip_of)
-  int col, p0, nrows;
+  int col, p0, nrows;   // strip of rows [p0, p0 + nrows) of column col (strip_of)
   strip_of(tid, d, a.ns, rs, col, p0, nrows);
 
   for (int e = tid; e < kGenFields * FS; e += NT) sm[e] = T(0);
@@ -1152,6 +1425,7 @@ __global__ void psi_rational_kernel(int d, double ax, double dx, double c, doubl
 struct VarPlan {
   int C = 0, RS = 0, ns = 0, NT = 0, pitch = 0, clusters = 0;
   size_t smem = 0;
+  bool onebar = false;   // var_engine1_kernel (one cluster barrier per Taylor term)
 };
 
 std::mutex g_plan_mu;
@@ -1186,6 +1460,15 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
   st = msk_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
                 "cluster attribute");
   if (st != MSK_OK) return st;
+  constexpr bool kOneBar = MODE == kModeVar && !EULER;   // solves that may take var_engine1_kernel
+  if constexpr (kOneBar) {
+    st = msk_cuda(ctx, cudaFuncSetAttribute(var_engine1_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kVarSmemCap), "smem attribute");
+    if (st == MSK_OK)
+      st = msk_cuda(ctx, cudaFuncSetAttribute(var_engine1_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
+                    "cluster attribute");
+    if (st != MSK_OK) return st;
+  }
   if (d > kVarMaxThreads) return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "grid too wide for the variable-coefficient engine");
   std::vector<VarPlan> cands;
   int best_used = 0;
@@ -1203,8 +1486,22 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
     };
     int W = var_pitch(d, RS, ns, pad);
     if ((size_t)total_of(W) * sizeof(T) > kVarSmemCap) W = d + pad;
-    const size_t smem = (size_t)total_of(W) * sizeof(T);
+    size_t smem = (size_t)total_of(W) * sizeof(T);
     if (smem > kVarSmemCap) continue;
+    // on clusters, one cluster barrier per term wherever its larger layout fits
+    bool onebar = false;
+    if constexpr (kOneBar) {
+      if (C > 1) {
+        int Wo = var_pitch(d, RS, ns, pad);
+        if ((size_t)var1_layout(RS, Wo, NT).total * sizeof(T) > kVarSmemCap) Wo = d + pad;
+        const size_t so = (size_t)var1_layout(RS, Wo, NT).total * sizeof(T);
+        if (so <= kVarSmemCap) {
+          onebar = true;
+          W = Wo;
+          smem = so;
+        }
+      }
+    }
     int clusters = 0;
     if (C == 1) {
       int per_sm = 0;
@@ -1224,7 +1521,10 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
       cfg.blockDim = dim3(NT, 1, 1);
       cfg.dynamicSmemBytes = smem;
       int nc = 0;
-      if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess) {
+      const void* kq = (const void*)kern;
+      if constexpr (kOneBar)
+        if (onebar) kq = (const void*)var_engine1_kernel<T>;
+      if (cudaOccupancyMaxActiveClusters(&nc, kq, &cfg) != cudaSuccess) {
         cudaGetLastError();
         nc = 0;
       }
@@ -1239,12 +1539,17 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
     p.pitch = W;
     p.clusters = clusters;
     p.smem = smem;
+    p.onebar = onebar;
     cands.push_back(p);
     best_used = std::max(best_used, clusters * C);
   }
-  // the smallest cluster that keeps at least 97 % of the best SM count busy
-  for (const VarPlan& p : cands) {
-    if (p.clusters * p.C * 100 >= best_used * 97) {
+  // the smallest cluster that keeps at least 97 % of the best SM count busy, taken
+  // first among the layouts with at most one cluster barrier per term (one CTA
+  // per path, or var_engine1_kernel: measured faster than two barriers per term
+  // on one more SM in 45)
+  for (int pass = 0; pass < 2; ++pass) {
+    for (const VarPlan& p : cands) {
+      if ((pass == 0 && !(p.onebar || p.C == 1)) || p.clusters * p.C * 100 < best_used * 97) continue;
       std::lock_guard<std::mutex> lock(g_plan_mu);
       g_plans[key] = p;
       *out = p;
@@ -1279,7 +1584,10 @@ msk_status launch_var_typed(msk_ctx* ctx, VarArgs a, int64_t paths, cudaStream_t
     cfg.attrs = attr;
     cfg.numAttrs = 1;
   }
-  return msk_cuda(ctx, cudaLaunchKernelEx(&cfg, engine_of<T, EULER, MODE>(), a), "variable-coefficient engine");
+  auto kern = engine_of<T, EULER, MODE>();
+  if constexpr (MODE == kModeVar && !EULER)
+    if (pl.onebar) kern = var_engine1_kernel<T>;
+  return msk_cuda(ctx, cudaLaunchKernelEx(&cfg, kern, a), "variable-coefficient engine");
 }
 
 }  // namespace
