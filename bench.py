@@ -1799,7 +1799,7 @@ def run_paper_var(a):
                        "parallelism": f"replicas x{world} (path ranges)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": None,
-                         "kernel": "var_engine_kernel<float> (d = 100, one CTA per path) / var_engine1_kernel<float> (d = 200, 300: clusters of 4 / 9, one cluster barrier per term); B and A0 composed",
+                         "kernel": "var_engine2_kernel<float> (two columns per thread, one cluster barrier per term; d = 100 one CTA per path, d = 200 / 300 clusters of 4 / 9); B and A0 composed",
                          "flops_per_point_per_term": VAR_FLOPS_PER_POINT,
                          "peak_note": f"FP32 FMA peak 148 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz ({peak_src} clock)"},
             "cpu_baseline": cpu,
