@@ -79,11 +79,13 @@ def rounding_bound(w, w6, u, eps):
 
 
 @pytest.mark.parametrize("d,prec", [(24, msk.MSK_F64), (41, msk.MSK_F64), (100, msk.MSK_F64),
-                                    (100, msk.MSK_F32), (200, msk.MSK_F32), (300, msk.MSK_F32)])
+                                    (100, msk.MSK_F32), (200, msk.MSK_F32), (300, msk.MSK_F32),
+                                    (151, msk.MSK_F64), (201, msk.MSK_F32)])
 def test_one_omega_application_matches_the_oracle(d, prec):
-    """u + Omega u with the six operators composed on the GPU (clusters of 1 to 7 CTAs
-    for d = 24 .. 300) against the oracle's sparse commutators, within the rounding
-    bound of the working precision."""
+    """u + Omega u with the six operators composed on the GPU (one CTA per path up to
+    clusters of 9 for d = 24 .. 300; even d two columns per thread, odd d on clusters
+    one column per thread with one cluster barrier per term) against the oracle's
+    sparse commutators, within the rounding bound of the working precision."""
     w = var_case(d, paths=2, drift_sign=-1)
     rng = np.random.default_rng(d)
     w6 = rng.normal(size=(2, 6)) * np.array([2e-3, 0.05, 1e-3, 1e-3, 1e-4, 1e-5])
