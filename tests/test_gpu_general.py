@@ -79,8 +79,12 @@ def oracle_magnus(w, B, A, order, K, p):
     return U.reshape(w.d, w.d)
 
 
-def test_one_omega_application_matches_the_oracle():
-    w = case(22, paths=2)
+@pytest.mark.parametrize("d", [22, 21, 100])
+def test_one_omega_application_matches_the_oracle(d):
+    """u + Omega u on the GPU against the oracle's Kronecker assembly and sparse
+    commutators: d = 22 two columns per thread on one CTA, d = 21 one column per thread,
+    d = 100 two columns per thread on clusters (halos of the extended passes)."""
+    w = case(d, paths=2)
     B, A = oracle_ops(w, COEFS)
     rng = np.random.default_rng(5)
     w6 = rng.normal(size=(2, 6)) * np.array([1e-2, 0.05, 1e-3, 1e-3, 1e-4, 1e-4])
