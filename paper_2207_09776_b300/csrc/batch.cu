@@ -50,15 +50,22 @@ struct BatchUnit {
   int32_t count, pad;
 };
 
-constexpr int kNT = 512;
-using K256 = Cfg<float, 256, 4, kNT>;
+constexpr int kNT = 512;    // threads of a CTA that runs the smaller grids' paths
+constexpr int kNT256 = 256;  // threads of a CTA of the clusters that run only 256^2 units
+template <int NTB> using K256 = Cfg<float, 256, 4, NTB>;
 using K128 = Cfg<float, 128, 1, kNT>;
 using K64h = Cfg<float, 64, 1, kNT / 2>;
 using K64 = Cfg<float, 64, 1, kNT>;
 constexpr size_t kHalf64 = (K64h::SMEM + 255) / 256 * 256;   // byte offset of the second half-slab
-constexpr size_t kSlabBytes = std::max(std::max(K256::SMEM, K128::SMEM), std::max(2 * kHalf64, K64::SMEM));
-constexpr size_t kBatchSmem = kSlabBytes + 16;                 // + the unit and task index slots
-static_assert(kBatchSmem <= 232448, "batch slab does not fit shared memory");
+constexpr size_t kSmallBytes = std::max(K128::SMEM, std::max(2 * kHalf64, K64::SMEM));
+// slab of a megakernel CTA (+ 16 bytes: the unit index slot): with 512 threads it
+// runs every unit type, with 256 threads only 256^2 units (partial sum in registers)
+template <int NTB> constexpr size_t slab_bytes() {
+  return NTB == kNT ? std::max(K256<kNT>::SMEM, kSmallBytes) : K256<NTB>::SMEM;
+}
+template <int NTB> constexpr size_t batch_smem() { return slab_bytes<NTB>() + 16; }
+constexpr size_t kTaskSmem = kSmallBytes + 16;   // + the task index slot
+static_assert(batch_smem<kNT>() <= 232448 && batch_smem<kNT256>() <= 232448, "batch slab does not fit shared memory");
 
 // Position pos of an item's cost order -> path index (identity without an order).
 __device__ __forceinline__ int64_t path_at(const EngineArgs& a, int64_t pos) { return a.order ? a.order[pos] : pos; }
@@ -94,13 +101,14 @@ __device__ __forceinline__ void run_small(const BatchUnit& un, const EngineArgs&
   }
 }
 
-// The units, each taken by a whole cluster from counter[0].
-__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kNT, 1)
+// The units, each taken by a whole cluster from counter[0] (NTB = 256: 256^2 units only).
+template <int NTB>
+__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(NTB, 1)
     batch_kernel(const EngineArgs* __restrict__ items, const BatchUnit* __restrict__ units, int n_units,
                  unsigned int* __restrict__ counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
-  int* s_unit = reinterpret_cast<int*>(smem_raw + kSlabBytes);
+  int* s_unit = reinterpret_cast<int*>(smem_raw + slab_bytes<NTB>());
   const int tid = threadIdx.x;
   const int rank = (int)cg::this_cluster().block_rank();
   const ClusterSync csync;
@@ -121,10 +129,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kNT, 1)
     const BatchUnit un = units[u];
     const EngineArgs a = items[un.item];
     if (un.type == UNIT_D256) {
-      slab_init<float, 256, 4, kNT>(sm, tid, rank, csync);
-      solve_path<float, 256, 4, kNT, false>(a, path_at(a, un.first), sm, tid, rank, csync);
+      slab_init<float, 256, 4, NTB>(sm, tid, rank, csync);
+      solve_path<float, 256, 4, NTB, false>(a, path_at(a, un.first), sm, tid, rank, csync);
     } else {
-      run_small(un, a, rank, smem_raw, tid);
+      if constexpr (NTB == kNT) run_small(un, a, rank, smem_raw, tid);
     }
   }
 }
@@ -135,7 +143,7 @@ __global__ void __launch_bounds__(kNT, 1)
     batch_task_kernel(const EngineArgs* __restrict__ items, const BatchUnit* __restrict__ tasks, int n_tasks,
                       unsigned int* __restrict__ counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  int* s_task = reinterpret_cast<int*>(smem_raw + kSlabBytes);
+  int* s_task = reinterpret_cast<int*>(smem_raw + kSmallBytes);
   const int tid = threadIdx.x;
   for (;;) {
     if (tid == 0) *s_task = (int)atomicAdd(counter + 1, 1u);
@@ -296,18 +304,21 @@ msk_status enqueue(msk_batch* b, cudaStream_t s) {
   }
   const BatchUnit* units = b->d_units;
   if (b->n_units > 0) {
+    // interleaved units need the 512-thread megakernel; 256^2 units alone run on
+    // 256-thread CTAs with the Taylor partial sum in registers
+    const bool all_types = b->variant & 1;
+    auto kern = all_types ? batch_kernel<kNT> : batch_kernel<kNT256>;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(148 * 4, 1, 1);
-    cfg.blockDim = dim3(kNT, 1, 1);
-    cfg.dynamicSmemBytes = kBatchSmem;
+    cfg.blockDim = dim3(all_types ? kNT : kNT256, 1, 1);
+    cfg.dynamicSmemBytes = all_types ? batch_smem<kNT>() : batch_smem<kNT256>();
     cfg.stream = s;
     int nc = 0;
-    st = bcuda(b, cudaOccupancyMaxActiveClusters(&nc, batch_kernel, &cfg), "occupancy clusters");
+    st = bcuda(b, cudaOccupancyMaxActiveClusters(&nc, kern, &cfg), "occupancy clusters");
     if (st != MSK_OK) return st;
     if (nc < 1) return bfail(b, MSK_ERR_UNSUPPORTED, "batch cluster configuration cannot be scheduled");
     cfg.gridDim = dim3((unsigned)(std::min(nc, b->n_units) * 4), 1, 1);
-    st = bcuda(b, cudaLaunchKernelEx(&cfg, batch_kernel, (const EngineArgs*)b->d_args, units, b->n_units,
-                                     b->d_counter),
+    st = bcuda(b, cudaLaunchKernelEx(&cfg, kern, (const EngineArgs*)b->d_args, units, b->n_units, b->d_counter),
                "batch launch");
     if (st != MSK_OK) return st;
   }
@@ -321,7 +332,7 @@ msk_status enqueue(msk_batch* b, cudaStream_t s) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.gridDim = dim3((unsigned)std::min<int64_t>(b->items[0].ctx->num_sms, b->n_tasks), 1, 1);
     cfg.blockDim = dim3(kNT, 1, 1);
-    cfg.dynamicSmemBytes = kBatchSmem;
+    cfg.dynamicSmemBytes = kTaskSmem;
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = b->n_units > 0 ? 1 : 0;
@@ -443,11 +454,16 @@ extern "C" msk_status msk_batch_create(msk_batch** out, const msk_batch_item* it
     st = bcuda(b, cudaMemcpy(b->d_args, b->args.data(), n_items * sizeof(EngineArgs), cudaMemcpyHostToDevice),
                "item table upload");
   if (st == MSK_OK)
-    st = bcuda(b, cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem),
+    st = bcuda(b, cudaFuncSetAttribute(batch_kernel<kNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)batch_smem<kNT>()),
+               "smem attribute");
+  if (st == MSK_OK)
+    st = bcuda(b, cudaFuncSetAttribute(batch_kernel<kNT256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)batch_smem<kNT256>()),
                "smem attribute");
   if (st == MSK_OK)
     st = bcuda(b, cudaFuncSetAttribute(batch_task_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kBatchSmem),
+                                       (int)kTaskSmem),
                "smem attribute");
   if (st == MSK_OK) st = bcuda(b, cudaDeviceSynchronize(), "prepare");
   if (st == MSK_OK) {

@@ -101,10 +101,11 @@ struct Cfg {
   static constexpr size_t OFF_B0 = OFF_COEF + 5 * MSK_NCOEF;      // RS: centre of V1 per local row
   static constexpr size_t OFF_SCALE = OFF_B0 + RS;                // kMaxTerms + 1: 1/(s k)
   static constexpr size_t OFF_SLOT = OFF_SCALE + kMaxTerms + 1;   // 2 x NW x 2 norm slots
-  // Clustered slabs keep the Taylor partial sum in shared memory ([RS][D], each
-  // thread's own points) instead of registers: their halo-exchange code needs
-  // the registers, and the register-resident sum spills there.
-  static constexpr bool ACC_SMEM = C > 1;
+  // Clustered slabs of 512 threads (and double ones) keep the Taylor partial sum
+  // in shared memory ([RS][D], each thread's own points) instead of registers:
+  // their halo-exchange code needs the registers, and the register-resident sum
+  // spills there.  With 256 threads (255 registers each) a float sum fits.
+  static constexpr bool ACC_SMEM = C > 1 && (NT > 256 || sizeof(T) == 8);
   // 2 x C x 2 CTA-level norm slots; each pair is written by one vector store
   // through the cluster, so the region starts on a 16-byte boundary
   static constexpr size_t OFF_CSLOT = (OFF_SLOT + 4 * NW + 3) / 4 * 4;
