@@ -122,7 +122,7 @@ msk_status dispatch(msk_ctx* ctx, int precision, const EngineArgs& a, cudaStream
       case 64: return launch_one<float, 64, 1, 128, EULER>(ctx, a, s);
       case 128: return launch_one<float, 128, 1, 512, EULER>(ctx, a, s);
       case 256: return launch_one<float, 256, 4, 256, EULER>(ctx, a, s);
-      case 512: return launch_one<float, 512, 16, 512, EULER>(ctx, a, s);
+      case 512: return launch_one<float, 512, 16, 256, EULER>(ctx, a, s);
     }
   } else {
     switch (d) {
