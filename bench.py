@@ -975,7 +975,7 @@ def other_workloads(msk, torch, local, stream):
     msk.msk_solve_magnus(s.ctx, 2, 64, 16, msk.MSK_F32, u, None, stream)   # warm-up (16 paths)
     ms = ev_ms(lambda: msk.msk_solve_magnus(s.ctx, 2, 64, w.paths, msk.MSK_F32, u, None, stream))
     out["large512_sigma0.5"] = {"paths": w.paths, "order": 2, "magnus_steps": 64, "ms": ms,
-                                "paths_per_s": w.paths / (ms / 1e3), "engine": "automatic (streamed)"}
+                                "paths_per_s": w.paths / (ms / 1e3), "engine": "automatic (resident 16-CTA clusters)"}
     s.close()
     # the paper's variable-coefficient grids (Section 3.2), float order 3 at the paper's steps
     for w0 in PAPER_VAR:

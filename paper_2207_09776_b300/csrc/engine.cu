@@ -162,10 +162,10 @@ bool engine_is_streamed(const msk_ctx* ctx, int precision) {
   if (ctx->xprof || ctx->gen) return false;
   if (ctx->engine_mode == MSK_ENGINE_STREAMED) return true;
   if (ctx->engine_mode == MSK_ENGINE_RESIDENT) return false;
-  // automatic: the streamed engine at 512^2 (measured faster in float: one CTA per path
-  // on all SMs against 16-CTA clusters on 112 of them; the only engine in double),
-  // the resident engines below
-  if (ctx->d >= 512 && stream_engine_available(ctx->d, precision)) return true;
+  // automatic: the resident engine wherever it holds the grid (at 512^2 in float its
+  // 16-CTA clusters of 256 threads measured as fast as streaming or faster, with
+  // termination per Taylor term instead of per sweep), the streamed engine where only
+  // it does (double at 512^2)
   return !resident_engine_available(ctx->d, precision) && stream_engine_available(ctx->d, precision);
 }
 

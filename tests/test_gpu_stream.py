@@ -96,11 +96,12 @@ def test_streamed_equals_resident_on_many_paths(d, precision, tol):
 
 def test_large_grid_float_vs_double_per_path():
     """The 512^2 precision study (a = 1, sigma = 0.5, order 2, K = 32 to T = 1) on 48
-    paths: float against double (both on the streamed engine, the automatic choice at
-    512^2), relative L2 per path well inside the float tolerance; the double result
+    paths: float against double (both on the streamed engine, the only one holding double
+    at 512^2), relative L2 per path well inside the float tolerance; the double result
     against the oracle on one sampled path is covered at a short horizon above."""
     w = LARGE_512[1].with_(paths=48)
     s = msk.Solver(w)
+    msk.msk_set_engine(s.ctx, msk.MSK_ENGINE_STREAMED)
     u64, st64 = s.magnus(2, 32, precision=msk.MSK_F64, status=True)
     u32, st32 = s.magnus(2, 32, precision=msk.MSK_F32, status=True)
     ok = (st64.cpu().numpy()[: w.paths] == 0) & (st32.cpu().numpy()[: w.paths] == 0)
@@ -119,15 +120,18 @@ def test_engine_mode_is_validated():
     s.close()
 
 
-def test_streamed_d512_full_size_on_a_sampled_path():
+def test_d512_full_size_on_a_sampled_path_both_engines():
     """The 512^2 configuration at full size as the bench runs it for sigma = 0.5 (1024 paths,
-    order 2, K = 64, 2^14 fine cells; the automatic engine choice streams it): every path
-    finite and unflagged, the last path against the oracle."""
+    order 2, K = 64, 2^14 fine cells) on both engines (the bench times both; the automatic
+    choice is the resident one): every path finite and unflagged, the last path against the
+    oracle."""
     w = LARGE_512[1]
     s = msk.Solver(w)
-    u, st = s.magnus(2, 64, precision=msk.MSK_F32, status=True)
-    assert bool(torch.isfinite(u).all())
-    assert int(st[: w.paths].max()) == 0
     ref = omagnus.solve(w, 2, 64, [w.paths - 1])
-    assert rel_l2(u[w.paths - 1:].cpu().numpy(), ref).max() <= TOL32
+    for mode in (msk.MSK_ENGINE_STREAMED, msk.MSK_ENGINE_AUTO):
+        msk.msk_set_engine(s.ctx, mode)
+        u, st = s.magnus(2, 64, precision=msk.MSK_F32, status=True)
+        assert bool(torch.isfinite(u).all())
+        assert int(st[: w.paths].max()) == 0
+        assert rel_l2(u[w.paths - 1:].cpu().numpy(), ref).max() <= TOL32
     s.close()
