@@ -2159,7 +2159,8 @@ msk_status plan_var(msk_ctx* ctx, VarPlan* out) {
     bool onebar = false, pairs = false;
     if constexpr (kOneBar) {
       const bool pr = d % 2 == 0;
-      if (MODE == kModeVar ? (C > 1 || pr) : pr) {
+      // (on clusters the term halos are three rows deep, all from the adjacent slab)
+      if ((MODE == kModeVar ? (C > 1 || pr) : pr) && (C == 1 || RS >= 3)) {
         const int nso = pr ? std::min(kVarMaxThreads, (d / 2) * std::max(1, RS / 2)) : ns;
         const int NTo = 32 * ((nso + 31) / 32);
         const int pado = MODE == kModeGen ? 4 : pad;   // two zero columns left of the pairs
