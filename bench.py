@@ -82,6 +82,9 @@ def parse():
                    help="engine of the --profile-case solves")
     p.add_argument("--profile-precision", default="f32", choices=("f32", "f64"),
                    help="precision of the --profile-case solves")
+    p.add_argument("--profile-general", action="store_true",
+                   help="with --profile-grid 100 / 200 / 300: the same problem written as general "
+                        "coefficients (nine-point B, five-point A stencil fields)")
     p.add_argument("--profile-case", type=int, default=0, metavar="PATHS",
                    help="run two plain solves of the benchmark workload with PATHS paths at K = 8 "
                         "(a small case for ncu captures) and exit")
@@ -1635,6 +1638,18 @@ def _oracle_var_paths(args):
     return len(paths)
 
 
+def general_coefficients(w):
+    """The paper's variable-coefficient Langevin problem (x profile psi) written as the nine
+    general coefficient grids h, f^x, f^v, g^xx, g^xv, g^vv, sigma, sigma^x, sigma^v."""
+    import numpy as np
+    d = w.d
+    xs = w.ax + (w.bx - w.ax) / (d + 1) * np.arange(1, d + 1)
+    X, V = np.meshgrid(xs, xs, indexing="xy")
+    psi = 1.0 + w.x_profile_c / (1.0 + X * X)
+    z = np.zeros_like(X)
+    return np.stack([z, w.drift_sign * V, z, z, z, w.a0 * psi, z, z, w.s0 * np.sqrt(psi)])
+
+
 def run_paper_var(a):
     """The paper's variable-coefficient experiment (Section 3.2, Table errorsVar): d = 100,
     200, 300 on [-4, 4]^2, g^vv = 1.1 (1 + 1/(x^2+1)), sigma^v = 10^-1/2 sqrt(1 + 1/(x^2+1)),
@@ -1726,12 +1741,7 @@ def run_paper_var(a):
         if d == 100:
             # the same problem through the general-coefficient path (nine-point B, five-point
             # A with per-point coefficients): the cost of generality, and agreement
-            import numpy as np
-            xs = w.ax + (w.bx - w.ax) / (d + 1) * np.arange(1, d + 1)
-            X, V = np.meshgrid(xs, xs, indexing="xy")
-            psi = 1.0 + w.x_profile_c / (1.0 + X * X)
-            z = np.zeros_like(X)
-            coef = np.stack([z, w.drift_sign * V, z, z, z, w.a0 * psi, z, z, w.s0 * np.sqrt(psi)])
+            coef = general_coefficients(w)
             msk.msk_solve_magnus(s.ctx, ORDER, K, P, msk.MSK_F32, out, st, stream)   # variable engine
             ref_var = out.clone()
             msk.msk_set_general_coefficients(s.ctx, coef)
@@ -1856,6 +1866,8 @@ def run_profile_case(a):
     else:
         w, K, order = LANGEVIN_TRIG_128.with_(paths=P), K_CANDIDATES[0], ORDER
     s = msk.Solver(w)
+    if a.profile_general and a.profile_grid in VAR_STEPS:
+        msk.msk_set_general_coefficients(s.ctx, general_coefficients(w))
     msk.msk_set_engine(s.ctx, {"auto": msk.MSK_ENGINE_AUTO, "resident": msk.MSK_ENGINE_RESIDENT,
                                "streamed": msk.MSK_ENGINE_STREAMED}[a.profile_engine])
     prec = msk.MSK_F32 if a.profile_precision == "f32" else msk.MSK_F64
