@@ -146,19 +146,34 @@ msk_status msk_fma_throughput(int device, int precision, double* tflops_out, voi
 /* Engine of the Magnus solves of the Langevin operators (constant or
  * time-dependent coefficients):
  *   MSK_ENGINE_AUTO      the resident engine wherever it holds the grid, the streamed
- *                        engine where only it does (double at d = 512) (default)
+ *                        engine where only it does (double at d = 512); in float at
+ *                        d = 512 the split below (default)
  *   MSK_ENGINE_RESIDENT  each path's state in shared memory (a cluster of up to 16
  *                        CTAs; d = 32 .. 512 in float, 32 .. 256 in double)
  *   MSK_ENGINE_STREAMED  each path's state in HBM, swept by one CTA per path with
  *                        several Taylor terms per sweep (d = 256, 512; float and
  *                        double); needs two d x d grids of library scratch per CTA,
  *                        so msk_solve_magnus_noalloc refuses it
+ *   MSK_ENGINE_SPLIT     where both engines exist (d = 256 in float and double,
+ *                        d = 512 in float): the resident clusters take the paths of
+ *                        the lower indices on the SMs they fill, the streamed engine
+ *                        the last n_s paths on the SMs the clusters leave free, both
+ *                        at once; n_s = a whole number of paths per free SM, from
+ *                        the two engines' measured rates.  Only msk_solve_magnus and
+ *                        msk_magnus_from_weights with more than two paths per SM split
+ *                        (msk_solve_magnus_host does not: the streamed engine would
+ *                        sweep the host-memory output over the bus); elsewhere this
+ *                        mode acts as MSK_ENGINE_AUTO.  Every
+ *                        path's result equals, bit for bit, the one of the engine that
+ *                        took it, and which engine takes a path depends only on the
+ *                        path count and the device's SM count.
  * Euler-Maruyama, output times, x profiles and general coefficients always use the
  * resident engines.  Both engines give the same solution within the Taylor
  * tolerance.  Bad mode -> MSK_ERR_ARG. */
 #define MSK_ENGINE_AUTO 0
 #define MSK_ENGINE_RESIDENT 1
 #define MSK_ENGINE_STREAMED 2
+#define MSK_ENGINE_SPLIT 3
 msk_status msk_set_engine(msk_ctx* ctx, int mode);
 
 /* Last error message of the context ("" if none).  For ctx NULL: the message

@@ -319,11 +319,11 @@ def msk_power_norms(ctx, order, steps, stream=None):
     return out[: rows.value * 9].view(rows.value, 9)
 
 
-MSK_ENGINE_AUTO, MSK_ENGINE_RESIDENT, MSK_ENGINE_STREAMED = 0, 1, 2
+MSK_ENGINE_AUTO, MSK_ENGINE_RESIDENT, MSK_ENGINE_STREAMED, MSK_ENGINE_SPLIT = 0, 1, 2, 3
 
 
 def msk_set_engine(ctx, mode):
-    """Engine of the Magnus solves: MSK_ENGINE_AUTO / _RESIDENT / _STREAMED."""
+    """Engine of the Magnus solves: MSK_ENGINE_AUTO / _RESIDENT / _STREAMED / _SPLIT."""
     _check(load_library().msk_set_engine(ctx, mode), ctx)
 
 

@@ -121,7 +121,8 @@ extern "C" msk_status msk_set_coefficients(msk_ctx* ctx, const msk_coeffs* c) {
 
 extern "C" msk_status msk_set_engine(msk_ctx* ctx, int mode) {
   if (!ctx) return MSK_ERR_ARG;
-  if (mode != MSK_ENGINE_AUTO && mode != MSK_ENGINE_RESIDENT && mode != MSK_ENGINE_STREAMED)
+  if (mode != MSK_ENGINE_AUTO && mode != MSK_ENGINE_RESIDENT && mode != MSK_ENGINE_STREAMED &&
+      mode != MSK_ENGINE_SPLIT)
     return msk_fail(ctx, MSK_ERR_ARG, "bad engine mode");
   ctx->engine_mode = mode;
   return MSK_OK;
@@ -203,8 +204,11 @@ extern "C" msk_status msk_brownian_increments(msk_ctx* ctx, int steps, int64_t p
   return launch_brownian(ctx, steps, paths, dW_dev, true, (cudaStream_t)stream);
 }
 
-extern "C" msk_status msk_solve_magnus(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
-                                       void* u_out_dev, uint32_t* path_status_dev, void* stream) {
+// out_on_host: u_out_dev is the device address of mapped host memory, which the split
+// solve's streamed share would sweep over the bus for every group of Taylor terms; those
+// solves keep every path on the resident engine.
+static msk_status solve_magnus(msk_ctx* ctx, int order, int steps, int64_t paths, int precision, void* u_out_dev,
+                               uint32_t* path_status_dev, void* stream, bool out_on_host) {
   if (!ctx) return MSK_ERR_ARG;
   if (order < 1 || order > 3) return msk_fail(ctx, MSK_ERR_ARG, "order must be 1, 2 or 3");
   if (precision != MSK_F64 && precision != MSK_F32) return msk_fail(ctx, MSK_ERR_ARG, "bad precision");
@@ -215,9 +219,9 @@ extern "C" msk_status msk_solve_magnus(msk_ctx* ctx, int order, int steps, int64
   cudaStream_t s = (cudaStream_t)stream;
   st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
   if (st != MSK_OK) return st;
-  // scratch: functionals, weights, then the path order and queue counter of the engine
+  // scratch: functionals, weights, then the path order and two queue counters of the engine
   const size_t nF = (size_t)paths * steps * MSK_NF, nW = (size_t)paths * steps * MSK_NWT;
-  st = msk_ensure_scratch(ctx, (nF + nW + (size_t)paths + 1) * sizeof(double));
+  st = msk_ensure_scratch(ctx, (nF + nW + (size_t)paths + 2) * sizeof(double));
   if (st != MSK_OK) return st;
   double* F = reinterpret_cast<double*>(ctx->scratch);
   double* Wt = F + nF;
@@ -226,8 +230,14 @@ extern "C" msk_status msk_solve_magnus(msk_ctx* ctx, int order, int steps, int64
   st = launch_brownian(ctx, steps, paths, F, false, s, precision == MSK_F32);
   if (st == MSK_OK) st = launch_omega(ctx, order, steps, paths, precision, F, Wt, s);
   if (st == MSK_OK)
-    st = launch_magnus_queued(ctx, steps, paths, precision, Wt, u_out_dev, path_status_dev, s, order_buf, queue);
+    st = launch_magnus_queued(ctx, steps, paths, precision, Wt, u_out_dev, path_status_dev, s, order_buf, queue,
+                              out_on_host ? nullptr : queue + 1);
   return st;
+}
+
+extern "C" msk_status msk_solve_magnus(msk_ctx* ctx, int order, int steps, int64_t paths, int precision,
+                                       void* u_out_dev, uint32_t* path_status_dev, void* stream) {
+  return solve_magnus(ctx, order, steps, paths, precision, u_out_dev, path_status_dev, stream, false);
 }
 
 // The device address of a page-locked, mapped host buffer (nullptr if it is not one).
@@ -274,7 +284,7 @@ extern "C" msk_status msk_solve_magnus_host(msk_ctx* ctx, int order, int steps, 
                   "copy u0 from the host");
     if (st != MSK_OK) return st;
   }
-  return msk_solve_magnus(ctx, order, steps, paths, precision, out, status, stream);
+  return solve_magnus(ctx, order, steps, paths, precision, out, status, stream, true);
 }
 
 extern "C" msk_status msk_solve_euler(msk_ctx* ctx, int steps, int64_t paths, int precision, void* u_out_dev,
@@ -314,13 +324,13 @@ extern "C" msk_status msk_magnus_from_weights(msk_ctx* ctx, int steps, int64_t p
   if (!Wt_dev || !u_out_dev) return msk_fail(ctx, MSK_ERR_ARG, "null buffer");
   st = msk_cuda(ctx, cudaSetDevice(ctx->device), "set device");
   if (st != MSK_OK) return st;
-  // scratch: the engine's path order and queue counter
-  st = msk_ensure_scratch(ctx, ((size_t)paths + 1) * sizeof(double));
+  // scratch: the engine's path order and two queue counters
+  st = msk_ensure_scratch(ctx, ((size_t)paths + 2) * sizeof(double));
   if (st != MSK_OK) return st;
   long long* order_buf = reinterpret_cast<long long*>(ctx->scratch);
   unsigned long long* queue = reinterpret_cast<unsigned long long*>(order_buf + paths);
   return launch_magnus_queued(ctx, steps, paths, precision, Wt_dev, u_out_dev, path_status_dev,
-                              (cudaStream_t)stream, order_buf, queue);
+                              (cudaStream_t)stream, order_buf, queue, queue + 1);
 }
 
 extern "C" msk_status msk_work_counter(msk_ctx* ctx, uint64_t* matvecs_host, int reset, void* stream) {

@@ -17,6 +17,11 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineArgs a) {
   int rank = 0;
   if constexpr (C > 1) rank = (int)cg::this_cluster().block_rank();
   const int64_t cid = blockIdx.x / C, ncl = gridDim.x / C;
+  // Every cluster of a launch is resident at once (the grid is sized to one wave): a
+  // kernel launched as this one's programmatic dependent (the streamed share of a
+  // split solve) may start on the SMs that the clusters leave free.  Without such
+  // a dependent this has no effect.
+  if constexpr (C > 1) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if constexpr (C > 1 && QUEUE) {
     // dynamic assignment on a cluster: rank 0 takes the queue position and publishes
     // the path in its slot; every CTA reads it through the cluster, and a second
@@ -29,7 +34,7 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineArgs a) {
     for (;;) {
       if (rank == 0 && tid == 0) {
         const unsigned long long q = atomicAdd(a.queue, 1ull);
-        *slot = q < (unsigned long long)a.paths ? a.order[q] : -1;
+        *slot = q < (unsigned long long)(a.qlen > 0 ? a.qlen : a.paths) ? a.order[q] : -1;
       }
       sync();
       const long long path = dsmem_ld_s64(slot0);
@@ -50,7 +55,7 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineArgs a) {
     for (;;) {
       if (tid == 0) {
         const unsigned long long q = atomicAdd(a.queue, 1ull);
-        *next_path = q < (unsigned long long)a.paths ? a.order[q] : -1;
+        *next_path = q < (unsigned long long)(a.qlen > 0 ? a.qlen : a.paths) ? a.order[q] : -1;
       }
       sync();
       const long long path = *next_path;   // rewritten only after solve_path's closing barrier
@@ -64,53 +69,69 @@ __global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineArgs a) {
   }
 }
 
+// The kernel of one configuration, its dynamic shared memory and attributes, and
+// how many of its clusters (CTAs when C = 1) are resident on the device at once.
 template <typename T, int D, int C, int NT, bool EULER>
-msk_status launch_one(msk_ctx* ctx, const EngineArgs& a, cudaStream_t stream) {
+struct Launch {
   using K = Cfg<T, D, C, NT>;
   // the dynamic path queue (Magnus solves) needs 16 bytes past the slab
-  constexpr bool kQ = !EULER && queue_slot_offset(K::SMEM) + 16 <= 232448;
-  const bool queued = kQ && a.queue;
-  auto kern = queued ? engine_kernel<T, D, C, NT, EULER, kQ> : engine_kernel<T, D, C, NT, EULER, false>;
-  const size_t smem = queued ? queue_slot_offset(K::SMEM) + 16 : K::SMEM;
-  msk_status st = msk_cuda(
-      ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-      "smem attribute");
-  if (st != MSK_OK) return st;
-  if (C > 8) {
-    st = msk_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
-                  "cluster attribute");
-    if (st != MSK_OK) return st;
-  }
+  static constexpr bool kQ = !EULER && queue_slot_offset(K::SMEM) + 16 <= 232448;
+  void (*kern)(const EngineArgs) = nullptr;
+  size_t smem = 0;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
-  cfg.blockDim = dim3(NT, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = stream;
-  int64_t clusters = 0;
-  if (C > 1) {
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cfg.gridDim = dim3(C, 1, 1);
-    int nc = 0;
-    st = msk_cuda(ctx, cudaOccupancyMaxActiveClusters(&nc, kern, &cfg), "occupancy clusters");
+  int64_t capacity = 0;
+
+  msk_status prepare(msk_ctx* ctx, bool queued, cudaStream_t stream) {
+    queued = queued && kQ;
+    kern = queued ? engine_kernel<T, D, C, NT, EULER, kQ> : engine_kernel<T, D, C, NT, EULER, false>;
+    smem = queued ? queue_slot_offset(K::SMEM) + 16 : K::SMEM;
+    msk_status st = msk_cuda(
+        ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+        "smem attribute");
     if (st != MSK_OK) return st;
-    if (nc < 1) return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "cluster configuration cannot be scheduled");
-    clusters = nc;
-  } else {
-    int per_sm = 0;
-    st = msk_cuda(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem),
-                  "occupancy");
-    if (st != MSK_OK) return st;
-    if (per_sm < 1) return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "kernel does not fit on an SM");
-    clusters = (int64_t)per_sm * ctx->num_sms;
+    if (C > 8) {
+      st = msk_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
+                    "cluster attribute");
+      if (st != MSK_OK) return st;
+    }
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    if (C > 1) {
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cfg.gridDim = dim3(C, 1, 1);
+      int nc = 0;
+      st = msk_cuda(ctx, cudaOccupancyMaxActiveClusters(&nc, kern, &cfg), "occupancy clusters");
+      if (st != MSK_OK) return st;
+      if (nc < 1) return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "cluster configuration cannot be scheduled");
+      capacity = nc;
+    } else {
+      int per_sm = 0;
+      st = msk_cuda(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem),
+                    "occupancy");
+      if (st != MSK_OK) return st;
+      if (per_sm < 1) return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "kernel does not fit on an SM");
+      capacity = (int64_t)per_sm * ctx->num_sms;
+    }
+    return MSK_OK;
   }
-  clusters = std::min<int64_t>(clusters, a.paths);
-  cfg.gridDim = dim3((unsigned)(clusters * C), 1, 1);
-  return msk_cuda(ctx, cudaLaunchKernelEx(&cfg, kern, a), "engine launch");
+};
+
+template <typename T, int D, int C, int NT, bool EULER>
+msk_status launch_one(msk_ctx* ctx, const EngineArgs& a, cudaStream_t stream) {
+  Launch<T, D, C, NT, EULER> L;
+  msk_status st = L.prepare(ctx, a.queue != nullptr, stream);
+  if (st != MSK_OK) return st;
+  // one wave: every cluster resident at once (a programmatic dependent relies on it)
+  const int64_t clusters = std::min<int64_t>(L.capacity, a.order && a.qlen > 0 ? a.qlen : a.paths);
+  L.cfg.gridDim = dim3((unsigned)(clusters * C), 1, 1);
+  return msk_cuda(ctx, cudaLaunchKernelEx(&L.cfg, L.kern, a), "engine launch");
 }
 
 template <bool EULER>
@@ -148,6 +169,27 @@ __global__ void em_table_kernel(CoefDev c, double T, int steps, double* em_d, fl
 
 }  // namespace
 
+// SMs that the queued Magnus form of the resident engine occupies when it fills the
+// device (its clusters x C); 0 where the configuration is not built.
+static msk_status resident_sms(msk_ctx* ctx, int precision, int64_t* sms) {
+  *sms = 0;
+  msk_status st = MSK_OK;
+  if (precision == MSK_F32 && ctx->d == 512) {
+    Launch<float, 512, 16, 256, false> L;
+    st = L.prepare(ctx, true, nullptr);
+    *sms = L.capacity * 16;
+  } else if (precision == MSK_F32 && ctx->d == 256) {
+    Launch<float, 256, 4, 256, false> L;
+    st = L.prepare(ctx, true, nullptr);
+    *sms = L.capacity * 4;
+  } else if (precision == MSK_F64 && ctx->d == 256) {
+    Launch<double, 256, 8, 256, false> L;
+    st = L.prepare(ctx, true, nullptr);
+    *sms = L.capacity * 8;
+  }
+  return st;
+}
+
 msk_status launch_em_table(msk_ctx* ctx, int steps, double* em_d, float* em_f, cudaStream_t stream) {
   em_table_kernel<<<(steps + 255) / 256, 256, 0, stream>>>(coef_dev(ctx->coef), ctx->T, steps, em_d, em_f);
   return msk_cuda(ctx, cudaGetLastError(), "euler table");
@@ -162,11 +204,61 @@ bool engine_is_streamed(const msk_ctx* ctx, int precision) {
   if (ctx->xprof || ctx->gen) return false;
   if (ctx->engine_mode == MSK_ENGINE_STREAMED) return true;
   if (ctx->engine_mode == MSK_ENGINE_RESIDENT) return false;
-  // automatic: the resident engine wherever it holds the grid (at 512^2 in float its
-  // 16-CTA clusters of 256 threads measured as fast as streaming or faster, with
-  // termination per Taylor term instead of per sweep), the streamed engine where only
-  // it does (double at 512^2)
+  // automatic (and the split mode wherever it does not split): the resident engine
+  // wherever it holds the grid (at 512^2 in float its 16-CTA clusters of 256 threads
+  // measured as fast as streaming or faster, with termination per Taylor term instead
+  // of per sweep), the streamed engine where only it does (double at 512^2)
   return !resident_engine_available(ctx->d, precision) && stream_engine_available(ctx->d, precision);
+}
+
+// Speed of the streamed engine per SM relative to the resident clusters' per SM, for
+// the split (float, 512^2, a = 1, sigma = 0.5, order 2, K = 64: 965 paths/s on 148
+// SMs against 1,008 paths/s on the 112 SMs of seven 16-CTA clusters).
+static constexpr double kStreamedPerSm = 0.72;
+
+msk_status engine_split(msk_ctx* ctx, int precision, int64_t paths, int64_t* n_s, int64_t* free_sms) {
+  *n_s = 0;
+  *free_sms = 0;
+  if (ctx->xprof || ctx->gen) return MSK_OK;
+  const int d = ctx->d;
+  const bool both = resident_engine_available(d, precision) && stream_engine_available(d, precision);
+  const bool want = ctx->engine_mode == MSK_ENGINE_SPLIT ||
+                    (ctx->engine_mode == MSK_ENGINE_AUTO && d == 512 && precision == MSK_F32);
+  if (!both || !want) return MSK_OK;
+  int64_t used = 0;
+  msk_status st = resident_sms(ctx, precision, &used);
+  if (st != MSK_OK) return st;
+  const int64_t fr = (int64_t)ctx->num_sms - used;
+  if (used < 1 || fr < 1) return MSK_OK;
+  // the streamed share by the two engines' throughput on their SMs, in whole paths
+  // per streamed CTA (rounded down: its paths are long, so it should finish first)
+  const double share = fr * kStreamedPerSm / (fr * kStreamedPerSm + (double)used);
+  const int64_t per_cta = (int64_t)((double)paths * share / (double)fr);
+  *n_s = std::min<int64_t>(per_cta * fr, paths - 1);
+  *free_sms = fr;
+  return MSK_OK;
+}
+
+msk_status launch_engine_split(msk_ctx* ctx, int steps, int64_t paths, int64_t n_s, int64_t free_sms, int precision,
+                               const double* Wt, void* out, uint32_t* status, cudaStream_t stream,
+                               long long* order_buf, unsigned long long* queue, unsigned long long* queue2) {
+  const int64_t n_r = paths - n_s;
+  // the term grids first: growing them frees memory, which would wait for the clusters
+  msk_status st = ensure_stream_scratch(ctx, precision, free_sms);
+  if (st == MSK_OK) st = launch_path_order(ctx, Wt, steps, n_r, order_buf, queue, stream, 0);
+  if (st == MSK_OK) st = launch_path_order(ctx, Wt, steps, n_s, order_buf + n_r, queue2, stream, n_r);
+  if (st != MSK_OK) return st;
+  // paths 0 .. n_r - 1 on the resident clusters (engine_is_streamed is false here) ...
+  EngineSnap x;
+  x.order = order_buf;
+  x.queue = queue;
+  x.qlen = n_r;
+  st = launch_engine_ex(ctx, false, steps, paths, precision, Wt, nullptr, out, status, stream, x);
+  if (st != MSK_OK) return st;
+  // ... and n_r .. paths - 1 on the streamed engine, one CTA per free SM, started
+  // while the clusters run
+  return launch_engine_stream(ctx, steps, paths, precision, Wt, out, status, stream, order_buf + n_r, queue2, n_s,
+                              free_sms, true);
 }
 
 msk_status launch_engine(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
@@ -196,6 +288,7 @@ msk_status launch_engine_ex(msk_ctx* ctx, bool euler, int steps, int64_t paths, 
   a.em_f = x.em_f;
   a.order = x.order;
   a.queue = x.queue;
+  a.qlen = x.qlen;
   a.band = ctx->band;
   a.u0 = ctx->u0;
   a.Wt = Wt;

@@ -75,6 +75,7 @@ struct EngineArgs {
   // are the cheapest (longest-processing-time-first).  Null: static striding.
   const long long* order;
   unsigned long long* queue;
+  int64_t qlen;       // entries of order handed out by the queue (0: paths)
   int64_t paths;
   int steps;
   double dx, T, s_cap;

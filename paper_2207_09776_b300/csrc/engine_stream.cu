@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(NT, 1) stream_engine_kernel(const StreamArgs s
     if (a.queue) {
       if (tid == 0) {
         const unsigned long long q = atomicAdd(a.queue, 1ull);
-        *next_path = q < (unsigned long long)a.paths ? a.order[q] : -1;
+        *next_path = q < (unsigned long long)(a.qlen > 0 ? a.qlen : a.paths) ? a.order[q] : -1;
       }
       __syncthreads();
       path = *next_path;
@@ -439,14 +439,36 @@ __global__ void __launch_bounds__(NT, 1) stream_engine_kernel(const StreamArgs s
     }
     __syncthreads();
   }
+  // Launched as the programmatic dependent of the resident clusters (split solve),
+  // this grid ends only after that one has completed, so whatever follows on the
+  // stream sees both grids' results; otherwise this returns at once.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 }  // namespace
 
 namespace {
 
+// Two d x d term grids per CTA for `grid` CTAs, library-owned, grown on demand.
+template <typename T, int D>
+msk_status ensure_term_grids(msk_ctx* ctx, int64_t grid) {
+  const size_t need = (size_t)grid * 2 * (size_t)D * D * sizeof(T);
+  if (need <= ctx->stream_bytes) return MSK_OK;
+  if (ctx->stream_scratch) cudaFree(ctx->stream_scratch);   // waits for work that may still use it
+  ctx->stream_scratch = nullptr;
+  ctx->stream_bytes = 0;
+  msk_status st = msk_cuda(ctx, cudaMalloc(&ctx->stream_scratch, need), "streamed engine scratch");
+  if (st != MSK_OK) return st;
+  ctx->stream_bytes = need;
+  return MSK_OK;
+}
+
+// grid_cap > 0: at most that many CTAs.  dependent: launched as the programmatic
+// dependent of the kernel before it on the stream (it may start while that kernel
+// still runs, on the SMs it leaves free; the two share no data but their inputs).
 template <typename T, int D, int NT, int LV, int RS>
-msk_status launch_stream_one(msk_ctx* ctx, const EngineArgs& e, cudaStream_t stream) {
+msk_status launch_stream_one(msk_ctx* ctx, const EngineArgs& e, cudaStream_t stream, int64_t grid_cap,
+                             bool dependent) {
   using K = SCfg<T, D, NT, LV, RS>;
   auto kern = stream_engine_kernel<T, D, NT, LV, RS>;
   msk_status st = msk_cuda(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM),
@@ -456,20 +478,22 @@ msk_status launch_stream_one(msk_ctx* ctx, const EngineArgs& e, cudaStream_t str
   st = msk_cuda(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, K::SMEM), "occupancy");
   if (st != MSK_OK) return st;
   if (per_sm < 1) return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "streamed engine does not fit on an SM");
-  const int64_t grid = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, e.paths);
-  // two d x d term grids per CTA, library-owned, grown on demand
-  const size_t need = (size_t)grid * 2 * (size_t)D * D * sizeof(T);
-  if (need > ctx->stream_bytes) {
-    if (ctx->stream_scratch) cudaFree(ctx->stream_scratch);   // waits for work that may still use it
-    ctx->stream_scratch = nullptr;
-    ctx->stream_bytes = 0;
-    st = msk_cuda(ctx, cudaMalloc(&ctx->stream_scratch, need), "streamed engine scratch");
-    if (st != MSK_OK) return st;
-    ctx->stream_bytes = need;
-  }
+  int64_t grid = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, e.order && e.qlen > 0 ? e.qlen : e.paths);
+  if (grid_cap > 0) grid = std::min<int64_t>(grid, grid_cap);
+  st = ensure_term_grids<T, D>(ctx, grid);
+  if (st != MSK_OK) return st;
   StreamArgs sa{e, ctx->stream_scratch};
-  kern<<<(unsigned)grid, NT, K::SMEM, stream>>>(sa);
-  return msk_cuda(ctx, cudaGetLastError(), "streamed engine launch");
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.gridDim = dim3((unsigned)grid, 1, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.dynamicSmemBytes = K::SMEM;
+  cfg.stream = stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = dependent ? 1 : 0;
+  return msk_cuda(ctx, cudaLaunchKernelEx(&cfg, kern, sa), "streamed engine launch");
 }
 
 }  // namespace
@@ -478,9 +502,17 @@ bool stream_engine_available(int d, int precision) {
   return d == 512 || d == 256 ? (precision == MSK_F32 || precision == MSK_F64) : false;
 }
 
+msk_status ensure_stream_scratch(msk_ctx* ctx, int precision, int64_t grid) {
+  if (ctx->d == 512) return precision == MSK_F32 ? ensure_term_grids<float, 512>(ctx, grid)
+                                                 : ensure_term_grids<double, 512>(ctx, grid);
+  if (ctx->d == 256) return precision == MSK_F32 ? ensure_term_grids<float, 256>(ctx, grid)
+                                                 : ensure_term_grids<double, 256>(ctx, grid);
+  return MSK_OK;
+}
+
 msk_status launch_engine_stream(msk_ctx* ctx, int steps, int64_t paths, int precision, const double* Wt, void* out,
                                 uint32_t* status, cudaStream_t stream, const long long* order,
-                                unsigned long long* queue) {
+                                unsigned long long* queue, int64_t qlen, int64_t grid_cap, bool dependent) {
   if (paths == 0) return MSK_OK;
   if (!out) return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "the streamed engine keeps the partial sum in the output");
   EngineArgs e{};
@@ -492,6 +524,7 @@ msk_status launch_engine_stream(msk_ctx* ctx, int steps, int64_t paths, int prec
   e.work = ctx->work;
   e.order = order;
   e.queue = queue;
+  e.qlen = qlen;
   e.paths = paths;
   e.steps = steps;
   e.dx = ctx->dx;
@@ -502,13 +535,13 @@ msk_status launch_engine_stream(msk_ctx* ctx, int steps, int64_t paths, int prec
   e.c = coef_dev(ctx->coef);
   if (precision == MSK_F32) {
     switch (ctx->d) {
-      case 512: return launch_stream_one<float, 512, 256, 4, 4>(ctx, e, stream);
-      case 256: return launch_stream_one<float, 256, 256, 4, 4>(ctx, e, stream);
+      case 512: return launch_stream_one<float, 512, 256, 4, 4>(ctx, e, stream, grid_cap, dependent);
+      case 256: return launch_stream_one<float, 256, 256, 4, 4>(ctx, e, stream, grid_cap, dependent);
     }
   } else {
     switch (ctx->d) {
-      case 512: return launch_stream_one<double, 512, 256, 1, 4>(ctx, e, stream);
-      case 256: return launch_stream_one<double, 256, 256, 1, 4>(ctx, e, stream);
+      case 512: return launch_stream_one<double, 512, 256, 1, 4>(ctx, e, stream, grid_cap, dependent);
+      case 256: return launch_stream_one<double, 256, 256, 1, 4>(ctx, e, stream, grid_cap, dependent);
     }
   }
   return msk_fail(ctx, MSK_ERR_UNSUPPORTED, "grid size / precision combination not built (streamed engine)");

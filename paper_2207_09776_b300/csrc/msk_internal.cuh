@@ -128,17 +128,29 @@ struct EngineSnap {
   // launch_path_order (null: static assignment of paths to CTAs)
   const long long* order = nullptr;
   unsigned long long* queue = nullptr;
+  int64_t qlen = 0;   // entries of order the queue hands out (0: paths)
 };
 // Order the paths by decreasing estimated Taylor cost sum_n s_n m_n (from the
 // records Wt) into order[paths] and reset *queue to 0, for the engine's dynamic queue.
+// With first > 0: paths first .. first + paths - 1 (order holds their global indices).
 msk_status launch_path_order(msk_ctx* ctx, const double* Wt, int steps, int64_t paths, long long* order,
-                             unsigned long long* queue, cudaStream_t stream);
+                             unsigned long long* queue, cudaStream_t stream, int64_t first = 0);
 // The Magnus engine from the records Wt, with the paths ordered by decreasing
 // estimated cost and handed out by a queue when that pays off (order_buf:
 // paths entries, queue: one counter; both scratch; null: static assignment).
+// queue2 (a second counter, may be null) allows the split solve (engine_split).
 msk_status launch_magnus_queued(msk_ctx* ctx, int steps, int64_t paths, int precision, const double* Wt, void* out,
                                 uint32_t* status, cudaStream_t stream, long long* order_buf,
-                                unsigned long long* queue);
+                                unsigned long long* queue, unsigned long long* queue2 = nullptr);
+// Split solve (engine.cu): the resident engine's clusters fill what they can of the
+// device and the streamed engine runs, as their programmatic dependent, on the SMs
+// they leave free.  engine_split gives the number n_s of paths of a `paths`-path
+// solve that go to the streamed engine (the last n_s indices; 0: no split) and the
+// free SMs; launch_engine_split runs it with two path orders and queue counters.
+msk_status engine_split(msk_ctx* ctx, int precision, int64_t paths, int64_t* n_s, int64_t* free_sms);
+msk_status launch_engine_split(msk_ctx* ctx, int steps, int64_t paths, int64_t n_s, int64_t free_sms, int precision,
+                               const double* Wt, void* out, uint32_t* status, cudaStream_t stream,
+                               long long* order_buf, unsigned long long* queue, unsigned long long* queue2);
 // Fill the Euler table of `steps` steps: em_d[2n] = alpha(t_n) dt, em_d[2n+1] = sigma(t_n), em_f the same in float.
 msk_status launch_em_table(msk_ctx* ctx, int steps, double* em_d, float* em_f, cudaStream_t stream);
 msk_status launch_engine_ex(msk_ctx* ctx, bool euler, int steps, int64_t paths, int precision,
@@ -153,9 +165,15 @@ msk_status launch_omega_jobs(msk_ctx* ctx, int order, int64_t njobs, int precisi
 // HBM (its output slot and two per-CTA term grids of library scratch), for grids
 // whose state does not stay on chip.
 bool stream_engine_available(int d, int precision);
+// qlen: entries of order the queue hands out (0: paths); grid_cap > 0: at most that
+// many CTAs; dependent: launched as the programmatic dependent of the kernel before
+// it on the stream (the split solve).
 msk_status launch_engine_stream(msk_ctx* ctx, int steps, int64_t paths, int precision, const double* Wt, void* out,
                                 uint32_t* status, cudaStream_t stream, const long long* order,
-                                unsigned long long* queue);
+                                unsigned long long* queue, int64_t qlen = 0, int64_t grid_cap = 0,
+                                bool dependent = false);
+// The streamed engine's term grids for `grid` CTAs (allocated before a split solve's launches).
+msk_status ensure_stream_scratch(msk_ctx* ctx, int precision, int64_t grid);
 bool resident_engine_available(int d, int precision);
 // whether the Magnus solves of this context run the streamed engine (msk_set_engine)
 bool engine_is_streamed(const msk_ctx* ctx, int precision);

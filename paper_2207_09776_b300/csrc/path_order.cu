@@ -28,8 +28,10 @@ __device__ __forceinline__ int order_bucket(const double* Wt, int steps, int64_t
   return kOrderBuckets - 1 - ci;   // costliest first
 }
 
+// Paths first .. first + paths - 1 (Wt points at path first's records).
 __global__ void __launch_bounds__(kOrderThreads) path_order_kernel(const double* Wt, int steps, int64_t paths,
-                                                                   long long* order, unsigned long long* queue) {
+                                                                   int64_t first, long long* order,
+                                                                   unsigned long long* queue) {
   __shared__ int cnt[kOrderBuckets];
   __shared__ int wsum[kOrderThreads / 32];
   __shared__ unsigned short cache[kOrderCache];
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(kOrderThreads) path_order_kernel(const double*
   __syncthreads();
   for (int64_t p = tid; p < paths; p += kOrderThreads) {
     const int pos = atomicAdd(&cnt[p < kOrderCache ? (int)cache[p] : order_bucket(Wt, steps, p)], 1);
-    order[pos] = p;
+    order[pos] = first + p;
   }
   if (tid == 0) *queue = 0ull;
 }
@@ -85,18 +87,27 @@ __global__ void __launch_bounds__(kOrderThreads) path_order_kernel(const double*
 }  // namespace
 
 msk_status launch_path_order(msk_ctx* ctx, const double* Wt, int steps, int64_t paths, long long* order,
-                             unsigned long long* queue, cudaStream_t stream) {
-  if (paths > (int64_t)INT32_MAX) return msk_fail(ctx, MSK_ERR_ARG, "too many paths for the path queue");
-  path_order_kernel<<<1, kOrderThreads, 0, stream>>>(Wt, steps, paths, order, queue);
+                             unsigned long long* queue, cudaStream_t stream, int64_t first) {
+  if (first + paths > (int64_t)INT32_MAX) return msk_fail(ctx, MSK_ERR_ARG, "too many paths for the path queue");
+  path_order_kernel<<<1, kOrderThreads, 0, stream>>>(Wt + (size_t)first * steps * MSK_NWT, steps, paths, first,
+                                                     order, queue);
   return msk_cuda(ctx, cudaGetLastError(), "path order");
 }
 
 msk_status launch_magnus_queued(msk_ctx* ctx, int steps, int64_t paths, int precision, const double* Wt, void* out,
                                 uint32_t* status, cudaStream_t stream, long long* order_buf,
-                                unsigned long long* queue) {
+                                unsigned long long* queue, unsigned long long* queue2) {
   EngineSnap x;
   // the queue pays off once every CTA solves several paths of unequal cost
   if (order_buf && queue && paths > 2 * (int64_t)ctx->num_sms) {
+    if (queue2 && out) {
+      int64_t n_s = 0, free_sms = 0;
+      msk_status st = engine_split(ctx, precision, paths, &n_s, &free_sms);
+      if (st != MSK_OK) return st;
+      if (n_s > 0)
+        return launch_engine_split(ctx, steps, paths, n_s, free_sms, precision, Wt, out, status, stream, order_buf,
+                                   queue, queue2);
+    }
     msk_status st = launch_path_order(ctx, Wt, steps, paths, order_buf, queue, stream);
     if (st != MSK_OK) return st;
     x.order = order_buf;

@@ -1,7 +1,8 @@
 """GPU parity of the streamed engine (each path's state in HBM, several Taylor terms
 per sweep): against the CPU oracle at 256^2 and 512^2 in double and float, against
-the resident engine on many paths (cost-ordered queue), and the 512^2 precision
-study of the large-grid configuration (float vs double, relative L2 per path)."""
+the resident engine on many paths (cost-ordered queue), the split solve (both engines
+at once, each path from one of them), and the 512^2 precision study of the large-grid
+configuration (float vs double, relative L2 per path)."""
 import numpy as np
 import pytest
 
@@ -94,6 +95,56 @@ def test_streamed_equals_resident_on_many_paths(d, precision, tol):
     s.close()
 
 
+@pytest.mark.parametrize("d,precision,mode", [(512, msk.MSK_F32, msk.MSK_ENGINE_AUTO),
+                                               (512, msk.MSK_F32, msk.MSK_ENGINE_SPLIT),
+                                               (256, msk.MSK_F32, msk.MSK_ENGINE_SPLIT),
+                                               (256, msk.MSK_F64, msk.MSK_ENGINE_SPLIT)])
+def test_split_solve_takes_each_path_from_one_engine(d, precision, mode):
+    """The split solve (resident clusters plus the streamed engine on the SMs they leave
+    free, launched as their programmatic dependent): every path equals, bit for bit, the
+    solution of the engine that took it, with its status word; the streamed share is a
+    non-empty block of the last path indices; with the work counter the two engines'
+    applications add up."""
+    base = BATCH_GRIDS[2] if d == 256 else LARGE_512[0]
+    w = base.with_(paths=320 if d == 256 else 300, T=0.2, n_fine=512)
+    s = msk.Solver(w)
+    P = w.paths
+    runs = {}
+    for name, m in (("resident", msk.MSK_ENGINE_RESIDENT), ("streamed", msk.MSK_ENGINE_STREAMED), ("split", mode)):
+        msk.msk_set_engine(s.ctx, m)
+        msk.msk_work_counter(s.ctx, reset=True)
+        u, st = s.magnus(2, 4, precision=precision, status=True)
+        torch.cuda.synchronize()
+        runs[name] = (u[:P].clone(), st[:P].clone(), msk.msk_work_counter(s.ctx, reset=True))
+    (ur, sr, wr), (us, ss, ws), (ux, sx, wx) = runs["resident"], runs["streamed"], runs["split"]
+    same_r = (ux == ur).reshape(P, -1).all(dim=1).cpu().numpy()
+    same_s = (ux == us).reshape(P, -1).all(dim=1).cpu().numpy()
+    assert bool((same_r | same_s).all())
+    n_s = int(P - np.argmax(~same_r)) if not same_r.all() else 0
+    assert 0 < n_s < P
+    assert same_r[: P - n_s].all() and same_s[P - n_s:].all()
+    assert torch.equal(sx, sr) and torch.equal(sx, ss)
+    assert min(wr, ws) <= wx <= max(wr, ws)
+    # the split result against the oracle on the last path (taken by the streamed engine)
+    if d == 256:
+        ref = omagnus.solve(w, 2, 4, [P - 1])
+        assert rel_l2(ux[P - 1:].cpu().numpy(), ref).max() <= (TOL32 if precision == msk.MSK_F32 else TOL64)
+    s.close()
+
+
+def test_split_below_the_queue_threshold_is_the_resident_solve():
+    """With at most two paths per SM there is no path queue and so no split: the split
+    mode gives the resident engine's result."""
+    w = LARGE_512[0].with_(paths=8, T=0.1, n_fine=128)
+    s = msk.Solver(w)
+    msk.msk_set_engine(s.ctx, msk.MSK_ENGINE_RESIDENT)
+    ur = s.magnus(2, 2, precision=msk.MSK_F32)
+    msk.msk_set_engine(s.ctx, msk.MSK_ENGINE_SPLIT)
+    ux = s.magnus(2, 2, precision=msk.MSK_F32)
+    assert torch.equal(ux, ur)
+    s.close()
+
+
 def test_large_grid_float_vs_double_per_path():
     """The 512^2 precision study (a = 1, sigma = 0.5, order 2, K = 32 to T = 1) on 48
     paths: float against double (both on the streamed engine, the only one holding double
@@ -114,17 +165,19 @@ def test_large_grid_float_vs_double_per_path():
 def test_engine_mode_is_validated():
     w = BATCH_GRIDS[2].with_(paths=1, n_fine=64)
     s = msk.Solver(w)
-    with pytest.raises(msk.MskError) as e:
-        msk.msk_set_engine(s.ctx, 7)
-    assert e.value.status == msk.MSK_ERR_ARG
+    for bad in (7, -1, 4):
+        with pytest.raises(msk.MskError) as e:
+            msk.msk_set_engine(s.ctx, bad)
+        assert e.value.status == msk.MSK_ERR_ARG
     s.close()
 
 
 def test_d512_full_size_on_a_sampled_path_both_engines():
     """The 512^2 configuration at full size as the bench runs it for sigma = 0.5 (1024 paths,
-    order 2, K = 64, 2^14 fine cells) on both engines (the bench times both; the automatic
-    choice is the resident one): every path finite and unflagged, the last path against the
-    oracle."""
+    order 2, K = 64, 2^14 fine cells) on the streamed engine and the automatic choice (the
+    split: resident clusters plus streamed CTAs on the free SMs, which take the last paths;
+    the resident engine alone runs in tests/test_gpu_parity.py): every path finite and
+    unflagged, the last path against the oracle."""
     w = LARGE_512[1]
     s = msk.Solver(w)
     ref = omagnus.solve(w, 2, 64, [w.paths - 1])
