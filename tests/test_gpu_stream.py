@@ -145,6 +145,20 @@ def test_split_below_the_queue_threshold_is_the_resident_solve():
     s.close()
 
 
+def test_host_output_solve_does_not_split():
+    """msk_solve_magnus_host keeps every path on the resident clusters (the streamed engine
+    would sweep its partial sums through the host-memory output): at 512^2 in float with
+    the path queue its result equals the resident engine's bit for bit."""
+    w = LARGE_512[0].with_(paths=300, T=0.2, n_fine=512)
+    s = msk.Solver(w)
+    msk.msk_set_engine(s.ctx, msk.MSK_ENGINE_RESIDENT)
+    ur = s.magnus(2, 4, precision=msk.MSK_F32)
+    msk.msk_set_engine(s.ctx, msk.MSK_ENGINE_AUTO)
+    uh = s.magnus_host(2, 4, precision=msk.MSK_F32)
+    assert torch.equal(uh, ur[: w.paths].cpu().view_as(uh))
+    s.close()
+
+
 def test_large_grid_float_vs_double_per_path():
     """The 512^2 precision study (a = 1, sigma = 0.5, order 2, K = 32 to T = 1) on 48
     paths: float against double (both on the streamed engine, the only one holding double
