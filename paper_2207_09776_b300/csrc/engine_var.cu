@@ -77,6 +77,9 @@ struct VarArgs {
   int n_out, u0_self;
   const void* gB;     // general coefficients: B stencil [9][d][d] and A stencil [5][d][d] (T)
   const void* gA;
+  // general coefficients, compact float form [9][d][d]: B's centre, odd and even x
+  // parts, odd and even v parts, cross term; A's centre, x and v parts (gen_stencil_kernel)
+  const float* gC;
   const double* em_d;  // Euler: alpha(t_n) dt, sigma(t_n) per step (double / float)
   const float* em_f;
   // Magnus: optional dynamic path queue (positions q = 0, 1, ... of an atomic
@@ -1681,6 +1684,64 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine2_kernel(const Va
     r.y = y;
     return r;
   };
+  // Compact float form (gen_stencil_kernel): nine coefficient pairs per point instead
+  // of fourteen, and each field's x and v differences and sums formed once for both
+  // stencils (the coefficient reads come from L2 in every pass; the arithmetic is cheap)
+  constexpr bool CMP = sizeof(T) == 4;
+  const P2* __restrict__ gCp = reinterpret_cast<const P2*>(a.gC);   // [9][d][d / 2] pairs
+  struct Df {
+    T ex, sx, nx, tx, cx;   // element x: u_E - u_W, u_E + u_W, u_N - u_S, u_N + u_S, cross
+    T ey, sy, ny, ty, cy;   // element y
+  };
+  auto diffs = [&](const Nb& f) -> Df {
+    Df D;
+    D.ex = f.c.y - f.cL;
+    D.sx = f.c.y + f.cL;
+    D.nx = f.n.x - f.m.x;
+    D.tx = f.n.x + f.m.x;
+    D.cx = (f.n.y - f.nL) - (f.m.y - f.mL);
+    D.ey = f.cR - f.c.x;
+    D.sy = f.cR + f.c.x;
+    D.ny = f.n.y - f.m.y;
+    D.ty = f.n.y + f.m.y;
+    D.cy = (f.nR - f.n.x) - (f.mR - f.m.x);
+    return D;
+  };
+  auto applyB9 = [&](const Nb& f, const Df& D, const P2* g) -> P2 {
+    T x = g[0].x * f.c.x;
+    x = fma(g[1].x, D.ex, x);
+    x = fma(g[2].x, D.sx, x);
+    x = fma(g[3].x, D.nx, x);
+    x = fma(g[4].x, D.tx, x);
+    x = fma(g[5].x, D.cx, x);
+    T y = g[0].y * f.c.y;
+    y = fma(g[1].y, D.ey, y);
+    y = fma(g[2].y, D.sy, y);
+    y = fma(g[3].y, D.ny, y);
+    y = fma(g[4].y, D.ty, y);
+    y = fma(g[5].y, D.cy, y);
+    P2 r;
+    r.x = x;
+    r.y = y;
+    return r;
+  };
+  auto applyA9 = [&](const Nb& f, const Df& D, const P2* g) -> P2 {
+    T x = g[6].x * f.c.x;
+    x = fma(g[7].x, D.ex, x);
+    x = fma(g[8].x, D.nx, x);
+    T y = g[6].y * f.c.y;
+    y = fma(g[7].y, D.ey, y);
+    y = fma(g[8].y, D.ny, y);
+    P2 r;
+    r.x = x;
+    r.y = y;
+    return r;
+  };
+  auto coefs9 = [&](int p, P2* g) {
+    const int g2 = ((r0 + p) * d + col) / 2;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[k] = __ldg(gCp + k * dd2 + g2);
+  };
   // the pair's coefficients at local row p
   auto coefs = [&](int p, P2* ga, P2* gb) {
     const int g2 = ((r0 + p) * d + col) / 2;
@@ -1694,10 +1755,21 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine2_kernel(const Va
   auto pass1 = [&](int b, int ra, int rb) {
     const T* t = sm + b * L.TS;
     for (int p = ra; p < rb; ++p) {
-      P2 ga[5], gb[9];
-      coefs(p, ga, gb);
-      const Nb f = load_nb(t, atT(0, p));
-      const P2 av = applyA2(f, ga), bv = applyB2(f, gb);
+      P2 av, bv;
+      if constexpr (CMP) {
+        P2 g[9];
+        coefs9(p, g);
+        const Nb f = load_nb(t, atT(0, p));
+        const Df D = diffs(f);
+        av = applyA9(f, D, g);
+        bv = applyB9(f, D, g);
+      } else {
+        P2 ga[5], gb[9];
+        coefs(p, ga, gb);
+        const Nb f = load_nb(t, atT(0, p));
+        av = applyA2(f, ga);
+        bv = applyB2(f, gb);
+      }
       st2v(Af + atA(p), av.x, av.y);
       st2v(Bf + atA(p), bv.x, bv.y);
     }
@@ -1706,10 +1778,28 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine2_kernel(const Va
   auto pass2 = [&](int b, int ra, int rb, T wB, T wA, T wAA, T wBA, T wBAA, T wBAB) {
     const T* t = sm + b * L.TS;
     for (int p = ra; p < rb; ++p) {
-      P2 ga[5], gb[9];
-      coefs(p, ga, gb);
-      const Nb fa = load_nb(Af, atA(p)), fb = load_nb(Bf, atA(p));
-      const P2 aa = applyA2(fa, ga), ab = applyA2(fb, ga), ba = applyB2(fa, gb), bb = applyB2(fb, gb);
+      P2 aa, ab, ba, bb;
+      Nb fa, fb;
+      if constexpr (CMP) {
+        P2 g[9];
+        coefs9(p, g);
+        fa = load_nb(Af, atA(p));
+        fb = load_nb(Bf, atA(p));
+        const Df Da = diffs(fa), Db = diffs(fb);
+        aa = applyA9(fa, Da, g);
+        ab = applyA9(fb, Db, g);
+        ba = applyB9(fa, Da, g);
+        bb = applyB9(fb, Db, g);
+      } else {
+        P2 ga[5], gb[9];
+        coefs(p, ga, gb);
+        fa = load_nb(Af, atA(p));
+        fb = load_nb(Bf, atA(p));
+        aa = applyA2(fa, ga);
+        ab = applyA2(fb, ga);
+        ba = applyB2(fa, gb);
+        bb = applyB2(fb, gb);
+      }
       const P2 tc = ld2v(t + atT(0, p));
       const T Px = fma(wB, tc.x, fma(wBA, fa.c.x, fma(wBAA, aa.x, wBAB * fma(T(2), ab.x, -ba.x))));
       const T Py = fma(wB, tc.y, fma(wBA, fa.c.y, fma(wBAA, aa.y, wBAB * fma(T(2), ab.y, -ba.y))));
@@ -1723,10 +1813,20 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine2_kernel(const Va
   auto pass3 = [&](int b, T sc, T scmu, T& mn, T& ma) {
     const T* t = sm + b * L.TS;
     for (int p = p0; p < p0 + nrows; ++p) {
-      P2 ga[5], gb[9];
-      coefs(p, ga, gb);
-      const Nb fp = load_nb(Pf, atP(p)), fq = load_nb(Qf, atP(p));
-      const P2 bp = applyB2(fp, gb), aq = applyA2(fq, ga);
+      P2 bp, aq;
+      if constexpr (CMP) {
+        P2 g[9];
+        coefs9(p, g);
+        const Nb fp = load_nb(Pf, atP(p)), fq = load_nb(Qf, atP(p));
+        bp = applyB9(fp, diffs(fp), g);
+        aq = applyA9(fq, diffs(fq), g);
+      } else {
+        P2 ga[5], gb[9];
+        coefs(p, ga, gb);
+        const Nb fp = load_nb(Pf, atP(p)), fq = load_nb(Qf, atP(p));
+        bp = applyB2(fp, gb);
+        aq = applyA2(fq, ga);
+      }
       const P2 tc = ld2v(t + atT(0, p));
       const T tx = fma(sc, bp.x + aq.x, -scmu * tc.x), ty = fma(sc, bp.y + aq.y, -scmu * tc.y);
       storeT2(b ^ 1, p, tx, ty);
@@ -1874,6 +1974,11 @@ __global__ void __launch_bounds__(kVarMaxThreads, 1) gen_engine2_kernel(const Va
 //      v+-1: +-f^v/(2dv) + g^vv/(2dv^2), (x+-1, v+-1): +-g^xv/(4 dx dv) (sign of the product)
 //   A: centre sigma, x+-1: +-sigma^x/(2dx), v+-1: +-sigma^v/(2dv)
 // in the order C, E (x+1), W, N (v+1), S, NE, NW, SE, SW (B) and C, E, W, N, S (A).
+// g32 also holds, after those 14 fields, the compact float form of the pair engine:
+//   B u = H u_C + X1 (u_E - u_W) + X2 (u_E + u_W) + V1 (u_N - u_S) + V2 (u_N + u_S)
+//         + XV ((u_NE - u_NW) - (u_SE - u_SW)),     A u = S u_C + SX (u_E - u_W) + SV (u_N - u_S)
+// with H = the centre above, X1 = f^x/(2dx), X2 = g^xx/(2dx^2), V1 = f^v/(2dv), V2 = g^vv/(2dv^2),
+// XV = g^xv/(4 dx dv), S = sigma, SX = sigma^x/(2dx), SV = sigma^v/(2dv): nine values per point.
 __global__ void gen_stencil_kernel(int d, double dx, double dv, const double* c, double* g64, float* g32) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int dd = d * d;
@@ -1888,6 +1993,8 @@ __global__ void gen_stencil_kernel(int d, double dx, double dv, const double* c,
     g64[(size_t)k * dd + e] = v[k];
     g32[(size_t)k * dd + e] = (float)v[k];
   }
+  const double cv[9] = {v[0], fx * ix, ixx, fv * iv, ivv, xv, s, sx * ix, sv * iv};
+  for (int k = 0; k < 9; ++k) g32[(size_t)(14 + k) * dd + e] = (float)cv[k];
 }
 
 // ------------------------------------------------------------------ operator norms
@@ -2364,6 +2471,7 @@ msk_status launch_engine_var(msk_ctx* ctx, bool euler, int steps, int64_t paths,
     const size_t dd = (size_t)ctx->d * ctx->d;
     a.gB = precision == MSK_F32 ? (const void*)ctx->gen32 : (const void*)ctx->gen64;
     a.gA = precision == MSK_F32 ? (const void*)(ctx->gen32 + 9 * dd) : (const void*)(ctx->gen64 + 9 * dd);
+    a.gC = ctx->gen32 + 14 * dd;
     if (precision == MSK_F32)
       return euler ? launch_var_typed<float, true, kModeGen>(ctx, a, paths, stream)
                    : launch_var_typed<float, false, kModeGen>(ctx, a, paths, stream);
@@ -2435,7 +2543,7 @@ extern "C" msk_status msk_set_general_coefficients(msk_ctx* ctx, const double* c
     if (!isfinite(coef_host[e])) return msk_fail(ctx, MSK_ERR_NONFINITE, "non-finite coefficient value");
   if (!ctx->gen64) {
     st = msk_cuda(ctx, cudaMalloc(&ctx->gen64, 14 * dd * sizeof(double)), "stencil field allocation");
-    if (st == MSK_OK) st = msk_cuda(ctx, cudaMalloc(&ctx->gen32, 14 * dd * sizeof(float)), "stencil field allocation");
+    if (st == MSK_OK) st = msk_cuda(ctx, cudaMalloc(&ctx->gen32, 23 * dd * sizeof(float)), "stencil field allocation");
     if (st != MSK_OK) return st;
   }
   st = alloc_var_tab(ctx);
