@@ -160,10 +160,11 @@ msk_status msk_fma_throughput(int device, int precision, double* tflops_out, voi
  *                        the last n_s paths on the SMs the clusters leave free, both
  *                        at once; n_s = a whole number of paths per free SM, from
  *                        the two engines' measured rates.  Only msk_solve_magnus and
- *                        msk_magnus_from_weights with more than two paths per SM split
- *                        (msk_solve_magnus_host does not: the streamed engine would
- *                        sweep the host-memory output over the bus); elsewhere this
- *                        mode acts as MSK_ENGINE_AUTO.  Every
+ *                        msk_magnus_from_weights with more than two paths per SM and
+ *                        an output in device memory split (not msk_solve_magnus_host,
+ *                        nor any output in mapped host memory: the streamed engine
+ *                        would sweep it over the bus); elsewhere this mode acts as
+ *                        MSK_ENGINE_AUTO.  Every
  *                        path's result equals, bit for bit, the one of the engine that
  *                        took it, and which engine takes a path depends only on the
  *                        path count and the device's SM count.

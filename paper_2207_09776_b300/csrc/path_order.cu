@@ -94,13 +94,25 @@ msk_status launch_path_order(msk_ctx* ctx, const double* Wt, int steps, int64_t 
   return msk_cuda(ctx, cudaGetLastError(), "path order");
 }
 
+// Whether p is page-locked host memory mapped into the device: the split solve's
+// streamed share keeps its partial sums in the output, which it would then sweep
+// over the bus for every group of Taylor terms.
+static bool host_memory(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
 msk_status launch_magnus_queued(msk_ctx* ctx, int steps, int64_t paths, int precision, const double* Wt, void* out,
                                 uint32_t* status, cudaStream_t stream, long long* order_buf,
                                 unsigned long long* queue, unsigned long long* queue2) {
   EngineSnap x;
   // the queue pays off once every CTA solves several paths of unequal cost
   if (order_buf && queue && paths > 2 * (int64_t)ctx->num_sms) {
-    if (queue2 && out) {
+    if (queue2 && out && !host_memory(out)) {
       int64_t n_s = 0, free_sms = 0;
       msk_status st = engine_split(ctx, precision, paths, &n_s, &free_sms);
       if (st != MSK_OK) return st;
