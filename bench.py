@@ -1741,7 +1741,7 @@ def run_paper_var(a):
             e1.record(stream)
             torch.cuda.synchronize()
             extra[nm] = {"paths_per_s": P / (e0.elapsed_time(e1) / 1e3)}
-        if d == 100:
+        if d in (100, 200):
             # the same problem through the general-coefficient path (nine-point B, five-point
             # A with per-point coefficients): the cost of generality, and agreement
             coef = general_coefficients(w)
