@@ -147,7 +147,7 @@ msk_status msk_fma_throughput(int device, int precision, double* tflops_out, voi
  * time-dependent coefficients):
  *   MSK_ENGINE_AUTO      the resident engine wherever it holds the grid, the streamed
  *                        engine where only it does (double at d = 512); in float at
- *                        d = 512 the split below (default)
+ *                        d = 256 and 512 the split below (default)
  *   MSK_ENGINE_RESIDENT  each path's state in shared memory (a cluster of up to 16
  *                        CTAs; d = 32 .. 512 in float, 32 .. 256 in double)
  *   MSK_ENGINE_STREAMED  each path's state in HBM, swept by one CTA per path with

@@ -204,7 +204,8 @@ bool engine_is_streamed(const msk_ctx* ctx, int precision) {
   if (ctx->xprof || ctx->gen) return false;
   if (ctx->engine_mode == MSK_ENGINE_STREAMED) return true;
   if (ctx->engine_mode == MSK_ENGINE_RESIDENT) return false;
-  // automatic (and the split mode wherever it does not split): the resident engine
+  // automatic (and the split mode, or the automatic split in float at 256^2 and 512^2,
+  // wherever the solve does not split): the resident engine
   // wherever it holds the grid (at 512^2 in float its 16-CTA clusters of 256 threads
   // measured as fast as streaming or faster, with termination per Taylor term instead
   // of per sweep), the streamed engine where only it does (double at 512^2)
@@ -223,7 +224,7 @@ msk_status engine_split(msk_ctx* ctx, int precision, int64_t paths, int64_t* n_s
   const int d = ctx->d;
   const bool both = resident_engine_available(d, precision) && stream_engine_available(d, precision);
   const bool want = ctx->engine_mode == MSK_ENGINE_SPLIT ||
-                    (ctx->engine_mode == MSK_ENGINE_AUTO && d == 512 && precision == MSK_F32);
+                    (ctx->engine_mode == MSK_ENGINE_AUTO && precision == MSK_F32 && (d == 512 || d == 256));
   if (!both || !want) return MSK_OK;
   int64_t used = 0;
   msk_status st = resident_sms(ctx, precision, &used);

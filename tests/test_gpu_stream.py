@@ -97,6 +97,7 @@ def test_streamed_equals_resident_on_many_paths(d, precision, tol):
 
 @pytest.mark.parametrize("d,precision,mode", [(512, msk.MSK_F32, msk.MSK_ENGINE_AUTO),
                                                (512, msk.MSK_F32, msk.MSK_ENGINE_SPLIT),
+                                               (256, msk.MSK_F32, msk.MSK_ENGINE_AUTO),
                                                (256, msk.MSK_F32, msk.MSK_ENGINE_SPLIT),
                                                (256, msk.MSK_F64, msk.MSK_ENGINE_SPLIT)])
 def test_split_solve_takes_each_path_from_one_engine(d, precision, mode):
