@@ -309,6 +309,9 @@ def test_dynamic_path_queue_matches_static_assignment(d, precision, paths):
     bit) to the static assignment used for small path counts."""
     w = LANGEVIN_TRIG_128.with_(d=d, paths=paths, n_fine=1024)
     s = solver(w)
+    # the resident engine alone (at 256^2 in float the automatic choice splits a queued
+    # solve with the streamed engine, which takes the last paths; tests/test_gpu_stream.py)
+    msk.msk_set_engine(s.ctx, msk.MSK_ENGINE_RESIDENT)
     full = s.magnus(3, 8, precision=precision).cpu().numpy()        # queued
     parts = []
     cuts = [0, paths // 3, 2 * paths // 3, paths]
