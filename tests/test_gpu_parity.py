@@ -472,7 +472,7 @@ def test_d256_cluster_slabs_match_the_oracle(precision, tol):
 def test_d512_sixteen_cta_clusters_match_the_oracle():
     w = LARGE_512[1].with_(paths=1, T=0.05, n_fine=64)
     s = solver(w)
-    msk.msk_set_engine(s.ctx, msk.MSK_ENGINE_RESIDENT)   # (also the automatic choice in float)
+    msk.msk_set_engine(s.ctx, msk.MSK_ENGINE_RESIDENT)   # (what the automatic choice runs for one path)
     u = s.magnus(2, 1, precision=msk.MSK_F32)
     ref = _oracle_magnus(w, 2, 1, [0])
     assert rel_l2(u.cpu().numpy(), ref).max() <= TOL32
