@@ -94,3 +94,33 @@ def test_create_without_a_device_reports_a_cuda_error(lib):
     g = msk.msk_grid(32, 32, -5, 5, -5, 5)
     assert lib.msk_create(ctypes.byref(h), ctypes.byref(g), 0) in (msk.MSK_ERR_CUDA, msk.MSK_ERR_OOM)
     assert h.value is None
+
+
+def test_header_constants_match_the_binding():
+    """Every numeric constant of include/msk.h (the #defines and the enum members, with
+    C's implicit numbering) that the binding exports has the header's value, and every
+    #define is exported: the binding passes these integers straight through the ABI."""
+    text = re.sub(r"/\*.*?\*/", " ", open(HEADER).read(), flags=re.S)
+    values = {}
+    for name, val in re.findall(r"#define\s+(MSK_\w+)\s+(-?\d+)u?\b", text):
+        values[name] = int(val)
+    defines = set(values)
+    for body in re.findall(r"enum\s*\w*\s*\{([^}]*)\}", text):
+        nxt = 0
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            if "=" in item:
+                name, val = (s.strip() for s in item.split("="))
+                nxt = int(val)
+            else:
+                name = item
+            values[name] = nxt
+            nxt += 1
+    assert values["MSK_ENGINE_SPLIT"] == 3 and values["MSK_OP_BX"] == 0 and values["MSK_ERR_UNSUPPORTED"] == 6
+    for name, val in values.items():
+        if name in defines:
+            assert hasattr(msk, name), name
+        if hasattr(msk, name):
+            assert getattr(msk, name) == val, (name, getattr(msk, name), val)
